@@ -1,0 +1,388 @@
+/*
+ * Plain FP64 CPU oracle for the adaptive-force-update gravity path
+ * (Grudic 2020, "Accelerating self-gravitating hydrodynamics simulations
+ * with adaptive force updates", Section 2 and Section 3).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark do.  It shares no source, header, table or helper with
+ * the CUDA library; both sides are written from the paper independently.
+ *
+ * Everything here is the plain definition, written out:
+ *   - force evaluation: O(n_tgt * N) direct summation over all sources j != i
+ *     of the softened acceleration, its time derivative (jerk, Eq. 4) and its
+ *     position derivative (the tidal tensor of Section 3), each sum
+ *     Neumaier-compensated; the tidal timestep of Eq. (tidaltimestep);
+ *   - the force-update counter (Eq. 3) and update condition
+ *     (Eq. updatecondition) on power-of-two time bins (Section 3);
+ *   - compaction of the due set in ascending index order;
+ *   - the first-order jerk predictor (Eq. jerkupdate) in closed form;
+ *   - the adjoint (reverse-mode) sums for a loss on a and on the potential
+ *     energy (not in the paper; derived from Eq. 4 and the tidal tensor).
+ *
+ * Readings where the paper is silent (all listed with reasons in the design
+ * notes of the repository):
+ *   - softening: cubic-spline (M4) density kernel of compact support radius
+ *     h, W(r,h) = 8/(pi h^3) w(r/h); the force is exactly Newtonian for
+ *     r >= h.  f(r) = M(<r)/(m r^3), g(r) = f'(r)/r, phi the potential kernel
+ *     (Phi_i = -G sum m_j phi(r_ij)), all derived by integrating W.
+ *   - the self term j == i is excluded by index, not by distance;
+ *   - T is d a / d x_i (negative semi-definite at a point mass' far field);
+ *     stored as xx, yy, zz, xy, xz, yz;
+ *   - time is counted in integer ticks of dt_min = dt_max * 2^-k_max;
+ *   - every floating-point step of selection and binning is a single
+ *     correctly rounded IEEE operation (built with -ffp-contract=off).
+ *
+ * All functions return 0 on success and a negative value on bad arguments.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------- */
+/* Softened kernel functions (cubic spline of support h).                      */
+/* f = M(<r)/(m r^3), g = f'(r)/r, phi: potential kernel, phi = 1/r for r>=h.  */
+/* Obtained by integrating W: M(<r)/m = 4 pi int_0^r s^2 W ds and              */
+/* phi(r) = int_r^inf s f(s) ds.  The Newtonian limit is f = r^-3, g = -3r^-5. */
+/* ------------------------------------------------------------------------- */
+void oracle_kernel(double r, double h, double *f, double *g, double *phi)
+{
+    if (r >= h) {
+        double r2 = r * r;
+        *f = 1.0 / (r2 * r);
+        *g = -3.0 / (r2 * r2 * r);
+        *phi = 1.0 / r;
+        return;
+    }
+    double u = r / h;
+    double h2 = h * h;
+    double h3 = h2 * h;
+    double h5 = h3 * h2;
+    if (u < 0.5) {
+        double u2 = u * u;
+        *f = (32.0 / 3.0 + u2 * (-192.0 / 5.0 + 32.0 * u)) / h3;
+        *g = (-384.0 / 5.0 + 96.0 * u) / h5;
+        *phi = (14.0 / 5.0 + u2 * (-16.0 / 3.0 + u2 * (48.0 / 5.0 - 32.0 / 5.0 * u))) / h;
+    } else {
+        double u2 = u * u;
+        double u3 = u2 * u;
+        double u5 = u3 * u2;
+        *f = (64.0 / 3.0 + u * (-48.0 + u * (192.0 / 5.0 - 32.0 / 3.0 * u)) - 1.0 / (15.0 * u3)) / h3;
+        *g = (-48.0 / u + 384.0 / 5.0 - 32.0 * u + 1.0 / (5.0 * u5)) / h5;
+        *phi = (16.0 / 5.0 - 1.0 / (15.0 * u) + u2 * (-32.0 / 3.0 + u * (16.0 + u * (-48.0 / 5.0 + 32.0 / 15.0 * u)))) / h;
+    }
+}
+
+/* Neumaier-compensated running sum. */
+typedef struct { double s, c; } nsum;
+
+static inline void nadd(nsum *a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x))
+        a->c += (a->s - t) + x;
+    else
+        a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static inline double nval(const nsum *a) { return a->s + a->c; }
+
+/* Tidal timestep, Eq. (tidaltimestep): sqrt(eta) * (||T||_F^2 / 6)^(-1/4).
+ * ||T||_F^2 summed in the fixed order xx, yy, zz, then the off-diagonals
+ * counted twice.  +inf when T vanishes. */
+double oracle_tidal_dt(const double *t6, double eta)
+{
+    double s = t6[0] * t6[0];
+    s = s + t6[1] * t6[1];
+    s = s + t6[2] * t6[2];
+    s = s + 2.0 * (t6[3] * t6[3]);
+    s = s + 2.0 * (t6[4] * t6[4]);
+    s = s + 2.0 * (t6[5] * t6[5]);
+    if (s == 0.0) return INFINITY;
+    return sqrt(eta) / sqrt(sqrt(s / 6.0));
+}
+
+static void set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/*
+ * Force evaluation at n_tgt targets (idx[t], or t itself when idx is NULL)
+ * against all n_src sources, j != i.  Outputs are per target slot t:
+ *   acc[3t..]   a_i   = G sum_j m_j f(r) d
+ *   jerk[3t..]  j_i   = G sum_j m_j [ f(r) v_ji + g(r) (d . v_ji) d ]     (Eq. 4)
+ *   tidal[6t..] T_i   = -G sum_j m_j [ f(r) I + g(r) d d^T ]    (d a_i / d x_i)
+ *   pot[t]      Phi_i = -G sum_j m_j phi(r)                       (nullable)
+ *   dt_grav[t]  sqrt(eta) (||T_i||^2/6)^(-1/4)                    (nullable)
+ * with d = x_j - x_i, v_ji = v_j - v_i, r = |d|.
+ */
+int oracle_eval(int64_t n_src, const double *pos, const double *vel, const double *mass,
+                int64_t n_tgt, const int32_t *idx, double G, double h, double eta,
+                double *acc, double *jerk, double *tidal, double *pot, double *dt_grav,
+                int nthreads)
+{
+    if (n_src < 0 || n_tgt < 0 || !(h > 0.0)) return -1;
+    if (n_tgt > 0 && (!pos || !vel || !mass || !acc || !jerk || !tidal)) return -1;
+    set_threads(nthreads);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(|: bad)
+    for (int64_t t = 0; t < n_tgt; ++t) {
+        int64_t i = idx ? (int64_t)idx[t] : t;
+        if (i < 0 || i >= n_src) { bad = 1; continue; }
+        nsum a[3], jk[3], tt[6], ph;
+        memset(a, 0, sizeof a);
+        memset(jk, 0, sizeof jk);
+        memset(tt, 0, sizeof tt);
+        memset(&ph, 0, sizeof ph);
+        const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+        const double ui = vel[3 * i], vi = vel[3 * i + 1], wi = vel[3 * i + 2];
+        for (int64_t j = 0; j < n_src; ++j) {
+            if (j == i) continue;
+            double d[3] = {pos[3 * j] - xi, pos[3 * j + 1] - yi, pos[3 * j + 2] - zi};
+            double v[3] = {vel[3 * j] - ui, vel[3 * j + 1] - vi, vel[3 * j + 2] - wi};
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double f, g, phi;
+            oracle_kernel(r, h, &f, &g, &phi);
+            double m = mass[j];
+            double dv = d[0] * v[0] + d[1] * v[1] + d[2] * v[2];
+            for (int c = 0; c < 3; ++c) {
+                nadd(&a[c], m * f * d[c]);
+                nadd(&jk[c], m * (f * v[c] + g * dv * d[c]));
+            }
+            /* T_ab = -m (f delta_ab + g d_a d_b) */
+            nadd(&tt[0], -m * (f + g * d[0] * d[0]));
+            nadd(&tt[1], -m * (f + g * d[1] * d[1]));
+            nadd(&tt[2], -m * (f + g * d[2] * d[2]));
+            nadd(&tt[3], -m * (g * d[0] * d[1]));
+            nadd(&tt[4], -m * (g * d[0] * d[2]));
+            nadd(&tt[5], -m * (g * d[1] * d[2]));
+            nadd(&ph, -m * phi);
+        }
+        double t6[6];
+        for (int c = 0; c < 3; ++c) {
+            acc[3 * t + c] = G * nval(&a[c]);
+            jerk[3 * t + c] = G * nval(&jk[c]);
+        }
+        for (int c = 0; c < 6; ++c) {
+            t6[c] = G * nval(&tt[c]);
+            tidal[6 * t + c] = t6[c];
+        }
+        if (pot) pot[t] = G * nval(&ph);
+        if (dt_grav) dt_grav[t] = oracle_tidal_dt(t6, eta);
+    }
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Time bins, counter and update condition.                                   */
+/* ------------------------------------------------------------------------- */
+
+/* An element of bin k (0 <= k <= k_max) takes steps of 2^(k_max-k) ticks and
+ * is active at every tick that is a multiple of its step (Section 3: the
+ * hierarchical power-of-two block timesteps). */
+static int is_active(int64_t tick, int32_t k_max, int32_t k)
+{
+    int64_t step = (int64_t)1 << (k_max - k);
+    return (tick % step) == 0;
+}
+
+/*
+ * Counter update (Eq. 3) and update condition (Eq. updatecondition).
+ * For every element active at `tick`: T_f += its step (in ticks); it is due
+ * when T_f * dt_min >= q_f * dt_grav (two correctly rounded products and a
+ * compare); a due element's counter is reset to 0, because its force is
+ * re-evaluated in this substep.  Inactive elements keep their counter and get
+ * active = due = 0.  dt_grav = 0 marks "never evaluated" and is always due.
+ */
+int oracle_select_due(int64_t n, int64_t tick, int32_t k_max, const int8_t *bin,
+                      int64_t *tf_ticks, const double *dt_grav, double q_f, double dt_min,
+                      uint8_t *active, uint8_t *due)
+{
+    if (n < 0 || k_max < 0 || k_max > 62 || tick < 0) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t k = bin[i];
+        if (k < 0 || k > k_max) return -1;
+        if (!is_active(tick, k_max, k)) {
+            active[i] = 0;
+            due[i] = 0;
+            continue;
+        }
+        active[i] = 1;
+        tf_ticks[i] += (int64_t)1 << (k_max - k);
+        double elapsed = (double)tf_ticks[i] * dt_min;
+        double need = q_f * dt_grav[i];
+        if (elapsed >= need) {
+            due[i] = 1;
+            tf_ticks[i] = 0;
+        } else {
+            due[i] = 0;
+        }
+    }
+    return 0;
+}
+
+/* Indices i with flags[i] != 0, ascending; *count = their number. */
+int oracle_compact(int64_t n, const uint8_t *flags, int32_t *idx, int32_t *count)
+{
+    if (n < 0 || n > INT32_MAX) return -1;
+    int32_t c = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (flags[i]) idx[c++] = (int32_t)i;
+    *count = c;
+    return 0;
+}
+
+/*
+ * Jerk predictor (Eq. jerkupdate) in closed form: for active, not-due
+ * elements a_out = a_last + j_last * tau with tau = T_f * dt_min the time since
+ * the last evaluation (the paper's incremental form summed exactly); active due
+ * elements get a_out = a_last (just re-evaluated); inactive ones are untouched.
+ */
+int oracle_predict(int64_t n, const uint8_t *active, const uint8_t *due, const double *a_last,
+                   const double *j_last, const int64_t *tf_ticks, double dt_min, double *a_out)
+{
+    if (n < 0) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!active[i]) continue;
+        if (due[i]) {
+            for (int c = 0; c < 3; ++c) a_out[3 * i + c] = a_last[3 * i + c];
+            continue;
+        }
+        double tau = (double)tf_ticks[i] * dt_min;
+        for (int c = 0; c < 3; ++c) {
+            double inc = j_last[3 * i + c] * tau;
+            a_out[3 * i + c] = a_last[3 * i + c] + inc;
+        }
+    }
+    return 0;
+}
+
+/*
+ * Bin assignment for elements active at `tick`: dt_i = min(dt_grav, dt_hydro)
+ * (Section 2); the target bin is the smallest k in [0, k_max] whose step
+ * dt_max 2^-k does not exceed dt_i (comparisons are exact: only exponents and
+ * mantissas are compared); a step may only grow at a tick that is a multiple
+ * of the new step, so the bin is raised to the smallest k aligned with `tick`.
+ * dt_hydro may be NULL (no limit).  NaN or non-positive dt_i -> k_max.
+ */
+static int32_t target_bin(double dt_i, double dt_max, int32_t k_max)
+{
+    if (!(dt_i > 0.0)) return k_max;          /* 0, negative or NaN */
+    if (isinf(dt_i)) return 0;
+    int ei, em;
+    double mi = frexp(dt_i, &ei);
+    double mm = frexp(dt_max, &em);
+    /* dt_max 2^-k <= dt_i  <=>  mm 2^(em-k) <= mi 2^ei */
+    int64_t k = (int64_t)em - (int64_t)ei;
+    if (mm > mi) k += 1;
+    if (k < 0) k = 0;
+    if (k > k_max) k = k_max;
+    return (int32_t)k;
+}
+
+int oracle_assign_bins(int64_t n, int64_t tick, int32_t k_max, double dt_max,
+                       const uint8_t *active, const double *dt_grav, const double *dt_hydro,
+                       int8_t *bin)
+{
+    if (n < 0 || k_max < 0 || k_max > 62 || tick < 0 || !(dt_max > 0.0)) return -1;
+    int32_t k_align = 0;
+    if (tick != 0) {
+        int32_t tz = 0;
+        while (((tick >> tz) & 1) == 0) ++tz;
+        k_align = k_max - tz;
+        if (k_align < 0) k_align = 0;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (!active[i]) continue;
+        double dt = dt_grav[i];
+        if (dt_hydro && dt_hydro[i] < dt) dt = dt_hydro[i];
+        if (dt_hydro && isnan(dt_hydro[i])) dt = dt_hydro[i];
+        int32_t k = target_bin(dt, dt_max, k_max);
+        if (k < k_align) k = k_align;
+        bin[i] = (int8_t)k;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of the force evaluation at all n elements.                         */
+/* ------------------------------------------------------------------------- */
+/*
+ * For a loss L(a, W) with a_bar = dL/da (n x 3, nullable = 0) and
+ * w_bar = dL/dW, W = 1/2 sum_i m_i Phi_i the potential energy:
+ *   pos_bar_k  = T_k a_bar_k + G m_k sum_{i!=k} [ f a_bar_i + g d (d . a_bar_i) ]
+ *                - w_bar m_k a_k
+ *   mass_bar_k = -G sum_{i!=k} f (d . a_bar_i) + w_bar Phi_k
+ * with d = x_i - x_k.  acc, tidal and pot are the forward results at all n
+ * elements (pot needed only when w_bar != 0, acc only when w_bar != 0).
+ */
+int oracle_backward(int64_t n, const double *pos, const double *mass, const double *a_bar,
+                    double w_bar, const double *acc, const double *tidal, const double *pot,
+                    double G, double h, double *pos_bar, double *mass_bar, int nthreads)
+{
+    if (n < 0 || !(h > 0.0)) return -1;
+    if (w_bar != 0.0 && (!acc || !pot)) return -1;
+    if (a_bar && !tidal) return -1;
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < n; ++k) {
+        nsum xb[3], mb;
+        memset(xb, 0, sizeof xb);
+        memset(&mb, 0, sizeof mb);
+        if (a_bar) {
+            const double xk = pos[3 * k], yk = pos[3 * k + 1], zk = pos[3 * k + 2];
+            for (int64_t i = 0; i < n; ++i) {
+                if (i == k) continue;
+                double d[3] = {pos[3 * i] - xk, pos[3 * i + 1] - yk, pos[3 * i + 2] - zk};
+                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                double f, g, phi;
+                oracle_kernel(r, h, &f, &g, &phi);
+                const double *ab = a_bar + 3 * i;
+                double da = d[0] * ab[0] + d[1] * ab[1] + d[2] * ab[2];
+                for (int c = 0; c < 3; ++c) nadd(&xb[c], f * ab[c] + g * d[c] * da);
+                nadd(&mb, -f * da);
+            }
+        }
+        double px[3] = {0.0, 0.0, 0.0};
+        double pm = 0.0;
+        if (a_bar) {
+            const double *t6 = tidal + 6 * k;
+            const double *ak = a_bar + 3 * k;
+            /* symmetric T from xx, yy, zz, xy, xz, yz */
+            double ta[3];
+            ta[0] = t6[0] * ak[0] + t6[3] * ak[1] + t6[4] * ak[2];
+            ta[1] = t6[3] * ak[0] + t6[1] * ak[1] + t6[5] * ak[2];
+            ta[2] = t6[4] * ak[0] + t6[5] * ak[1] + t6[2] * ak[2];
+            for (int c = 0; c < 3; ++c) px[c] = ta[c] + G * mass[k] * nval(&xb[c]);
+            pm = G * nval(&mb);
+        }
+        if (w_bar != 0.0) {
+            for (int c = 0; c < 3; ++c) px[c] -= w_bar * mass[k] * acc[3 * k + c];
+            pm += w_bar * pot[k];
+        }
+        for (int c = 0; c < 3; ++c) pos_bar[3 * k + c] = px[c];
+        mass_bar[k] = pm;
+    }
+    return 0;
+}

@@ -1,0 +1,71 @@
+"""Mutation test of the oracle's pins (no GPU).
+
+Each case copies the oracle's C source, plants one plausible mistake (a
+dropped term, a wrong sign, index or coefficient, an off-by-one comparison),
+compiles the copy and requires at least one pin to fail on it.  The planted
+mistakes live only in temporary copies; the oracle itself is not changed.
+"""
+import os
+
+import pytest
+
+import oracle_pins as P
+from oracle import oracle as O
+
+MUTANTS = {
+    "far_g_sign": ("*g = -3.0 / (r2 * r2 * r);", "*g = 3.0 / (r2 * r2 * r);"),
+    "inner_f_coeff": ("*f = (32.0 / 3.0 + u2 * (-192.0 / 5.0 + 32.0 * u)) / h3;",
+                      "*f = (32.0 / 3.0 + u2 * (-192.0 / 5.0 + 30.0 * u)) / h3;"),
+    "outer_g_term": ("*g = (-48.0 / u + 384.0 / 5.0 - 32.0 * u + 1.0 / (5.0 * u5)) / h5;",
+                     "*g = (-48.0 / u + 384.0 / 5.0 - 32.0 * u) / h5;"),
+    "outer_phi_coeff": ("*phi = (16.0 / 5.0 - 1.0 / (15.0 * u)",
+                        "*phi = (16.0 / 5.0 - 1.0 / (5.0 * u)"),
+    "self_term_kept": ("if (j == i) continue;", ";"),
+    "jerk_sign": ("nadd(&jk[c], m * (f * v[c] + g * dv * d[c]));",
+                  "nadd(&jk[c], m * (f * v[c] - g * dv * d[c]));"),
+    "jerk_dropped_term": ("nadd(&jk[c], m * (f * v[c] + g * dv * d[c]));",
+                          "nadd(&jk[c], m * (f * v[c]));"),
+    "tidal_index": ("nadd(&tt[4], -m * (g * d[0] * d[2]));", "nadd(&tt[4], -m * (g * d[0] * d[1]));"),
+    "tidal_sign": ("nadd(&tt[1], -m * (f + g * d[1] * d[1]));", "nadd(&tt[1], m * (f + g * d[1] * d[1]));"),
+    "d_transposed": ("double d[3] = {pos[3 * j] - xi,", "double d[3] = {xi - pos[3 * j],"),
+    "vel_index": ("double v[3] = {vel[3 * j] - ui, vel[3 * j + 1] - vi,",
+                  "double v[3] = {vel[3 * j] - ui, vel[3 * j + 1] - ui,"),
+    "pot_sign": ("nadd(&ph, -m * phi);", "nadd(&ph, m * phi);"),
+    "G_dropped": ("jerk[3 * t + c] = G * nval(&jk[c]);", "jerk[3 * t + c] = nval(&jk[c]);"),
+    "dt_offdiag_once": ("s = s + 2.0 * (t6[3] * t6[3]);", "s = s + (t6[3] * t6[3]);"),
+    "dt_norm_6": ("return sqrt(eta) / sqrt(sqrt(s / 6.0));", "return sqrt(eta) / sqrt(sqrt(s / 3.0));"),
+    "due_strict": ("if (elapsed >= need) {", "if (elapsed > need) {"),
+    "no_reset": ("            tf_ticks[i] = 0;\n", "\n"),
+    "counter_one_tick": ("tf_ticks[i] += (int64_t)1 << (k_max - k);", "tf_ticks[i] += 1;"),
+    "active_wrong_step": ("int64_t step = (int64_t)1 << (k_max - k);", "int64_t step = (int64_t)1 << k;"),
+    "compact_off_by_one": ("if (flags[i]) idx[c++] = (int32_t)i;", "if (flags[i]) idx[c++] = (int32_t)i + 1;"),
+    "predict_half": ("double inc = j_last[3 * i + c] * tau;", "double inc = j_last[3 * i + c] * tau * 0.5;"),
+    "predict_due_too": ("        if (due[i]) {\n            for (int c = 0; c < 3; ++c) a_out[3 * i + c] = a_last[3 * i + c];\n            continue;\n        }\n", ""),
+    "bin_round_up": ("if (mm > mi) k += 1;", "if (mm >= mi) k += 1;"),
+    "bin_no_align": ("if (k < k_align) k = k_align;", ";"),
+    "bin_hydro_ignored": ("if (dt_hydro && dt_hydro[i] < dt) dt = dt_hydro[i];", ";"),
+    "adj_mass_sign": ("nadd(&mb, -f * da);", "nadd(&mb, f * da);"),
+    "adj_g_term": ("nadd(&xb[c], f * ab[c] + g * d[c] * da);", "nadd(&xb[c], f * ab[c]);"),
+    "adj_tidal_transposed": ("ta[0] = t6[0] * ak[0] + t6[3] * ak[1] + t6[4] * ak[2];",
+                             "ta[0] = t6[0] * ak[0] + t6[4] * ak[1] + t6[3] * ak[2];"),
+    "adj_w_sign": ("px[c] -= w_bar * mass[k] * acc[3 * k + c];", "px[c] += w_bar * mass[k] * acc[3 * k + c];"),
+    "adj_pot_dropped": ("pm += w_bar * pot[k];", ";"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(O._SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique/present: {name}"
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    lib = O.load(O.build(force=True, src=str(path), out=str(tmp_path / "libmutant.so")))
+    caught = []
+    for pin in P.ALL_PINS:
+        try:
+            pin(lib)
+        except (AssertionError, ValueError, FloatingPointError):
+            caught.append(pin.__name__)
+            break
+    assert caught, f"mutant {name} passed every pin"
