@@ -1,0 +1,496 @@
+"""Benchmark of the adaptive-force-update hot path on one GB300.
+
+Workload: turbulent cloud, N = 2^20 equal-mass elements in a uniform sphere
+(R = 1, G = M = 1), k^-4 Gaussian random velocities at virial parameter 2,
+cubic-spline softening h = 2e-3 (synthetic stand-in for the paper's
+STARFORGE cloud, whose initial conditions are not public).
+
+One step = one pass of the whole path at tick t:
+  grav_select_due -> grav_compact_active -> grav_eval_active (mixed
+  precision, FP32 pair arithmetic) -> grav_predict -> grav_assign_bins.
+A fraction f of the elements sits in the finest time bin (active every tick,
+hydro-limited: dt_hydro = dt_min) and the rest in the coarsest bin (inactive
+at the ticks timed); q_f = 0, so every active element is due.  The headline
+uses f = 1 (all 2^20 elements evaluated against all 2^20 sources per step).
+
+Metric: acceleration + jerk + tidal-tensor interactions per second, counted
+as n_due * N per evaluation.  Printed as ONE JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_DEFAULT = 1 << 20
+H = 2e-3
+K_MAX = 6
+DT_MAX = 2.0**-4
+FLOPS_PER_INTERACTION = 56      # FP32 flops of the Newtonian pair body (FFMA = 2), MUFU not counted
+WORKLOAD = "turbulent_cloud_N1048576_h2e-3"
+METRIC = "acc+jerk+tidal interactions/s at N=2^20 (mixed precision)"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--fraction", type=float, default=1.0)
+    ap.add_argument("--tile-config", type=int, default=-1)
+    ap.add_argument("--no-extras", action="store_true", help="headline only (no sweeps, FP64, CPU)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (N > 1: independent replicas, one per GPU)
+# ---------------------------------------------------------------------------
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda() else "gloo"
+        dist.init_process_group(backend)
+    return rank, local, ws
+
+
+def _cuda():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{self.gpu}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# the path
+# ---------------------------------------------------------------------------
+
+class Path:
+    """Device state of one replica and one pass of the hot path."""
+
+    def __init__(self, n, fraction, device, tile_config=-1):
+        import torch
+
+        from paper_2010_13792_gb300 import grav, ics
+        self.torch, self.grav = torch, grav
+        self.n, self.dev = n, device
+        pos, vel, mass = ics.turbulent_cloud(n, seed=ics.BASE_SEED + 2)
+        self.host = {"pos": pos, "vel": vel, "mass": mass}
+        fine = ics.active_subset(n, fraction, ics.BASE_SEED + 3)
+        bins = np.zeros(n, np.int8)
+        bins[fine] = K_MAX
+        self.n_due_expected = fine.size
+        self.dt_min = DT_MAX * 2.0**-K_MAX
+        dt_hydro = np.full(n, self.dt_min)
+        f64 = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device)
+        self.pos, self.vel, self.mass = f64(pos), f64(vel), f64(mass)
+        self.bins = torch.as_tensor(bins, device=device)
+        self.dt_hydro = f64(dt_hydro)
+        self.tf = torch.zeros(n, dtype=torch.int64, device=device)
+        self.dt_grav = torch.zeros(n, dtype=torch.float64, device=device)
+        self.active = torch.zeros(n, dtype=torch.uint8, device=device)
+        self.due = torch.zeros(n, dtype=torch.uint8, device=device)
+        self.idx = torch.zeros(n, dtype=torch.int32, device=device)
+        self.count = torch.zeros(1, dtype=torch.int32, device=device)
+        self.acc = torch.zeros(n, 3, dtype=torch.float64, device=device)
+        self.jerk = torch.zeros(n, 3, dtype=torch.float64, device=device)
+        self.tidal = torch.zeros(n, 6, dtype=torch.float64, device=device)
+        self.a_out = torch.zeros(n, 3, dtype=torch.float64, device=device)
+        self.params = grav.params(h=H, precision=grav.MIXED, tile_config=tile_config)
+        self.ws_compact = grav.Workspace()
+        self.ws_eval = grav.Workspace()
+        self.launches_per_step = 9   # select 1, compact 3, pack 1, eval 1, reduce 1, predict 1, bins 1
+
+    def step(self, tick, ev=None):
+        """One pass of the path at `tick` (odd ticks: only the fine bin is active)."""
+        g = self.grav
+        g.select_due(tick, K_MAX, self.bins, self.tf, self.dt_grav, 0.0, self.dt_min, self.active,
+                     self.due)
+        g.compact_active(self.due, self.idx, self.count, workspace=self.ws_compact)
+        if ev is not None:
+            ev[0].record()
+        g.eval_active(self.params, self.pos, self.vel, self.mass, self.idx, self.count, self.n,
+                      self.acc, self.jerk, self.tidal, None, self.dt_grav,
+                      workspace=self.ws_eval)
+        if ev is not None:
+            ev[1].record()
+        g.predict(self.active, self.due, self.acc, self.jerk, self.tf, self.dt_min, self.a_out)
+        g.assign_bins(tick, K_MAX, DT_MAX, self.active, self.dt_grav, self.dt_hydro, self.bins)
+
+
+def l2_flush(buf):
+    buf.zero_()
+
+
+def run_ours(args, rank, local, ws):
+    import torch
+
+    from paper_2010_13792_gb300 import grav
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    path = Path(args.n, args.fraction, dev, args.tile_config)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    n_due = path.n_due_expected
+    tick = 1
+    for _ in range(max(args.warmup, 0)):
+        path.step(tick)
+        tick += 2
+    torch.cuda.synchronize()
+    got = int(path.count.item())
+    if got != n_due:
+        raise RuntimeError(f"due count {got} != expected {n_due}")
+
+    # ---- timed region: K steps, L2 flushed between steps ----
+    ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    ev_eval = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            l2_flush(flush)
+            ev_step[k][0].record()
+            path.step(tick, ev_eval[k])
+            ev_step[k][1].record()
+            tick += 2
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    barrier(ws)
+    step_ms = [a.elapsed_time(b) for a, b in ev_step]
+    eval_ms = [a.elapsed_time(b) for a, b in ev_eval]
+    t_total = max_over_ranks(sum(step_ms) * 1e-3, ws, dev)
+    interactions = float(n_due) * args.n
+    total_units = sum_over_ranks(interactions * args.steps, ws, dev)
+    value = total_units / t_total
+    clocks = clk.summary()
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-mixed",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": args.n, "active_fraction": args.fraction,
+                   "n_due_per_step": n_due, "h": H, "sources": args.n,
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "tile_config": grav.tile_configs(grav.MIXED)[
+                       args.tile_config if args.tile_config >= 0 else 0]},
+        "gpu_launches": path.launches_per_step * args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak32 = sms * 128 * 2 * 2070e6 / 1e12       # FP32 lanes x FMA x max SM clock
+    eval_s = statistics.mean(eval_ms) * 1e-3
+    achieved = FLOPS_PER_INTERACTION * interactions / eval_s / 1e12
+    result["roofline"] = {
+        "bound": "alu", "kernel": "eval_mixed_kernel (grav_eval_active: pack + direct sum)",
+        "achieved": achieved, "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32,
+        "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+        "flops_per_interaction": FLOPS_PER_INTERACTION, "traffic": None,
+        "eval_ms_mean": 1e3 * eval_s,
+    }
+
+    if rank == 0 and not args.no_extras:
+        result["extras"] = extras(args, path, dev, sms, peak32, flush)
+        result["e2e"] = e2e(args, path, dev, flush)
+        result["cpu_baseline"] = cpu_baseline(path, args.cpu_seconds)
+    elif rank == 0:
+        result["e2e"] = e2e(args, path, dev, flush)
+    return result
+
+
+def _time_eval(path, params, idx, cnt, n_idx, reps, flush):
+    import torch
+    from paper_2010_13792_gb300 import grav
+    ws = grav.Workspace()
+    grav.eval_active(params, path.pos, path.vel, path.mass, idx, cnt, n_idx, path.acc, path.jerk,
+                     path.tidal, None, path.dt_grav, workspace=ws)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        grav.eval_active(params, path.pos, path.vel, path.mass, idx, cnt, n_idx, path.acc,
+                         path.jerk, path.tidal, None, path.dt_grav, workspace=ws)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    return statistics.median(ts)
+
+
+def extras(args, path, dev, sms, peak32, flush):
+    """Active-fraction sweep (mixed), the FP64 GPU path, the predictor's
+    bandwidth and the measured FMA peaks."""
+    import torch
+
+    from paper_2010_13792_gb300 import grav, ics
+    out = {}
+    n = args.n
+    sweep = {}
+    for frac in (0.01, 0.1):
+        idx_np = ics.active_subset(n, frac, ics.BASE_SEED + 5)
+        idx = torch.as_tensor(idx_np, device=dev)
+        cnt = torch.tensor([idx_np.size], dtype=torch.int32, device=dev)
+        t = _time_eval(path, path.params, idx, cnt, idx_np.size, 3, flush)
+        sweep[str(frac)] = {"interactions_per_s": idx_np.size * n / t, "eval_ms": 1e3 * t}
+    out["mixed_fraction_sweep"] = sweep
+    # FP64 path on the 1% active set (all N sources)
+    idx_np = ics.active_subset(n, 0.01, ics.BASE_SEED + 5)
+    idx = torch.as_tensor(idx_np, device=dev)
+    cnt = torch.tensor([idx_np.size], dtype=torch.int32, device=dev)
+    p64 = grav.params(h=H, precision=grav.F64)
+    t64 = _time_eval(path, p64, idx, cnt, idx_np.size, 2, flush)
+    ips64 = idx_np.size * n / t64
+    out["fp64_path"] = {"interactions_per_s": ips64, "active_fraction": 0.01, "eval_ms": 1e3 * t64}
+    # predictor (HBM-bound): all elements active, none due
+    ones = torch.ones(n, dtype=torch.uint8, device=dev)
+    zeros = torch.zeros(n, dtype=torch.uint8, device=dev)
+    ts = []
+    for _ in range(5):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        grav.predict(ones, zeros, path.acc, path.jerk, path.tf, path.dt_min, path.a_out)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    tp = statistics.median(ts)
+    bytes_pred = n * (1 + 1 + 8 + 24 + 24 + 24)
+    out["predict"] = {"bytes_per_element": 82, "GB_per_s": bytes_pred / tp / 1e9, "us": tp * 1e6}
+    try:
+        f32 = grav.measure_fma_peak(grav.MIXED, 0.5)
+        f64 = grav.measure_fma_peak(grav.F64, 0.5)
+        out["measured_fma_peak_tflops"] = {"fp32": f32 / 1e12, "fp64": f64 / 1e12}
+    except grav.GravError as e:
+        out["measured_fma_peak_tflops"] = {"error": str(e)}
+    return out
+
+
+def e2e(args, path, dev, flush):
+    """The same step through the C ABI with inputs in pinned HOST memory:
+    host->device copies of the step's inputs and device->host copies of its
+    results are inside the timed region."""
+    import torch
+    host_in = {
+        "pos": torch.as_tensor(path.host["pos"]).pin_memory(),
+        "vel": torch.as_tensor(path.host["vel"]).pin_memory(),
+        "mass": torch.as_tensor(path.host["mass"]).pin_memory(),
+        "tf": path.tf.cpu().pin_memory(),
+        "dt_grav": path.dt_grav.cpu().pin_memory(),
+        "bins": path.bins.cpu().pin_memory(),
+        "dt_hydro": path.dt_hydro.cpu().pin_memory(),
+    }
+    dev_in = {"pos": path.pos, "vel": path.vel, "mass": path.mass, "tf": path.tf,
+              "dt_grav": path.dt_grav, "bins": path.bins, "dt_hydro": path.dt_hydro}
+    host_out = {"acc": torch.empty_like(path.acc, device="cpu").pin_memory(),
+                "jerk": torch.empty_like(path.jerk, device="cpu").pin_memory(),
+                "tidal": torch.empty_like(path.tidal, device="cpu").pin_memory(),
+                "dt_grav": torch.empty_like(path.dt_grav, device="cpu").pin_memory(),
+                "a_out": torch.empty_like(path.a_out, device="cpu").pin_memory()}
+    dev_out = {"acc": path.acc, "jerk": path.jerk, "tidal": path.tidal, "dt_grav": path.dt_grav,
+               "a_out": path.a_out}
+    h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+    d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+    steps = max(1, min(args.steps, 3))
+    tick = 10001
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for k, t in host_in.items():
+            dev_in[k].copy_(t, non_blocking=True)
+        path.step(tick)
+        for k, t in host_out.items():
+            t.copy_(dev_out[k], non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+        tick += 2
+    t = statistics.mean(ts)
+    return {"value": path.n_due_expected * path.n / t, "unit": "interactions/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+def cpu_baseline(path, seconds):
+    """The FP64 oracle as it stands, on this host's cores, on a strided target
+    sample of the same workload against all N sources."""
+    from oracle import oracle as O
+    n = path.n
+    pos, vel, mass = path.host["pos"], path.host["vel"], path.host["mass"]
+    threads = O.max_threads()
+    k = 64
+    t = 0.0
+    while True:
+        idx = np.arange(0, n, max(1, n // k), dtype=np.int32)[:k]
+        t0 = time.perf_counter()
+        O.eval_active(pos, vel, mass, idx, h=H, want_pot=False)
+        t = time.perf_counter() - t0
+        if t >= 0.3 * seconds or k >= n:
+            break
+        k = int(min(n, k * max(2.0, min(16.0, 0.5 * seconds / max(t, 1e-3)))))
+    return {"value": idx.size * n / t, "unit": "interactions/s", "cores": threads,
+            "kind": "oracle", "sample": f"{idx.size} strided targets x {n} sources, FP64, "
+            f"{t:.1f} s", "seconds": t}
+
+
+def run_reference(args, rank, ws):
+    """Reference arm: the FP64 oracle on the host cores, same workload and
+    metric; each step a bounded strided target sample against all N sources."""
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    from paper_2010_13792_gb300 import ics
+    n = args.n
+    pos, vel, mass = ics.turbulent_cloud(n, seed=ics.BASE_SEED + 2)
+    threads = O.max_threads()
+    k = max(threads * 4, 32)
+    idx = np.arange(0, n, max(1, n // k), dtype=np.int32)[:k]
+    for _ in range(max(args.warmup, 0)):
+        O.eval_active(pos, vel, mass, idx[: max(threads, 1)], h=H, want_pot=False)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.eval_active(pos, vel, mass, idx, h=H, want_pot=False)
+        ts.append(time.perf_counter() - t0)
+    t = sum(ts)
+    value = idx.size * n * args.steps / t
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "sample_targets_per_step": int(idx.size)},
+        "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": threads,
+                         "kind": "oracle", "sample": f"{idx.size} strided targets x {n} sources per step"},
+        "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, local, ws = dist_setup()
+    if args.impl == "reference":
+        res = run_reference(args, rank, ws)
+    else:
+        res = run_ours(args, rank, local, ws)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * grav.h -- C ABI of libgrav, the GB300 (sm_103a) implementation of the
+ * data-parallel hot path of adaptive force updates (Grudic 2020, "Accelerating
+ * self-gravitating hydrodynamics simulations with adaptive force updates",
+ * Sections 2 and 3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Array pointers are CUDA DEVICE pointers owned by the caller.  The library
+ *    never allocates device memory: calls that need scratch space take a
+ *    caller-provided `workspace` of at least the size the matching
+ *    `*_workspace_bytes` query returns (256-byte aligned).
+ *  - Every compute call is asynchronous on `stream` (a cudaStream_t passed as
+ *    void*; NULL is the legacy default stream) and returns an int status:
+ *    GRAV_OK on success, a negative GRAV_E* code otherwise.  Host-side argument
+ *    checks happen before anything is launched; a call that returns an error
+ *    has launched nothing unless the code is GRAV_ECUDA.
+ *  - Conditions that can only be seen on the device (non-finite inputs,
+ *    out-of-range indices or bins, a bounded wait that gave up) are OR-ed as
+ *    GRAV_FLAG_* bits into the optional device word `flags_dev` (nullable);
+ *    the caller reads it when it wants to.  No exception, abort or trap
+ *    crosses this boundary and no kernel spins without an iteration bound.
+ *  - grav_last_error_string() describes the last failing call of the calling
+ *    host thread.
+ *  - Layouts: positions, velocities, accelerations and jerks are [n][3]
+ *    row-major FP64; the tidal tensor is [n][6] FP64 in the order
+ *    xx, yy, zz, xy, xz, yz; masses, potentials and timesteps are [n] FP64;
+ *    flags are one byte per element (0 = false, non-zero = true).
+ *
+ * Notation: element i's position x_i, velocity v_i, mass m_i; d = x_j - x_i,
+ * v_ji = v_j - v_i, r = |d|; the softened kernel is the cubic spline of
+ * compact support radius h, entering through f(r) = M(<r)/(m r^3) and
+ * g(r) = f'(r)/r (f = r^-3 and g = -3 r^-5 for r >= h).
+ */
+#ifndef GRAV_H
+#define GRAV_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GRAV_API __attribute__((visibility("default")))
+#else
+#define GRAV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define GRAV_OK          0
+#define GRAV_EINVAL     -1   /* bad argument (null pointer, size, alignment, parameter) */
+#define GRAV_ECUDA      -2   /* a CUDA runtime call or kernel launch failed */
+#define GRAV_ENONFINITE -3   /* reserved: non-finite input (reported via GRAV_FLAG_NONFINITE) */
+#define GRAV_ETIMEOUT   -4   /* reserved: bounded device wait expired (GRAV_FLAG_TIMEOUT) */
+#define GRAV_ENOMEM     -5   /* workspace smaller than the matching *_workspace_bytes */
+
+/* Device flag bits OR-ed into *flags_dev. */
+#define GRAV_FLAG_NONFINITE 1  /* a position, velocity, mass or a_bar was NaN or Inf */
+#define GRAV_FLAG_TIMEOUT   2  /* a bounded wait on a shared-memory copy gave up */
+#define GRAV_FLAG_BADINDEX  4  /* a target index outside [0, n_src), or a bin outside [0, k_max] */
+
+/* Arithmetic of the force sums. */
+#define GRAV_F64   0  /* all pair arithmetic and sums in FP64 */
+#define GRAV_MIXED 1  /* FP64 positions offset to FP32 per source tile, FP32 pair
+                         arithmetic, compensated FP32 tile sums, FP64 final sums */
+
+typedef struct grav_params {
+    double G;            /* gravitational constant (> 0) */
+    double h;            /* softening support radius (> 0); Newtonian beyond h */
+    double eta;          /* tidal-timestep tolerance of Eq. (tidaltimestep) (> 0), e.g. 0.01 */
+    int32_t precision;   /* GRAV_F64 or GRAV_MIXED */
+    int32_t want_pot;    /* non-zero: also evaluate the potential Phi_i */
+    int32_t tile_config; /* -1 = library default, else an index < grav_tile_config_count(precision) */
+    int32_t max_split;   /* upper bound on source splits per target block; 0 = default */
+} grav_params;
+
+/* Describes one tile configuration (for the autotuner). */
+typedef struct grav_tile_info {
+    int32_t threads;          /* threads per CTA */
+    int32_t targets_per_thread;
+    int32_t sources_per_tile; /* S: sources staged per shared-memory tile */
+    int32_t targets_per_block;/* threads * targets_per_thread */
+} grav_tile_info;
+
+GRAV_API const char *grav_last_error_string(void);
+GRAV_API const char *grav_version(void);
+GRAV_API int32_t grav_tile_config_count(int32_t precision);
+GRAV_API int grav_tile_config(int32_t precision, int32_t index, grav_tile_info *out);
+
+/* ------------------------------------------------------------------------ */
+/* Selection: Eq. (3), Eq. (updatecondition) and Section 3's power-of-two     */
+/* block timesteps.  Time is counted in integer ticks of dt_min; an element   */
+/* of bin k (0 <= k <= k_max <= 62) takes steps of 2^(k_max-k) ticks and is   */
+/* active at ticks that are multiples of its step.                            */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * grav_select_due -- Eq. (3) and Eq. (updatecondition).
+ * For each element i active at `tick` (>= 0): tf_ticks[i] += 2^(k_max-bin[i]);
+ * due_out[i] = (tf_ticks[i]*dt_min >= q_f*dt_grav[i]) evaluated as two
+ * correctly rounded FP64 products and a compare (bit-identical on any IEEE
+ * machine); a due element's counter is reset to 0 because its force is
+ * re-evaluated in this substep.  active_out/due_out get 1/0; inactive elements
+ * keep their counter and get 0/0.  dt_grav[i] == 0 means "never evaluated"
+ * and is always due.  A bin outside [0, k_max] makes the element inactive and
+ * sets GRAV_FLAG_BADINDEX.
+ *   n         number of elements (>= 0)
+ *   bin       int8[n]  (in)
+ *   tf_ticks  int64[n] (in/out) ticks since the last force evaluation
+ *   dt_grav   f64[n]   (in) tidal timestep from each element's last evaluation
+ *   q_f       update tolerance (>= 0); dt_min > 0 the tick length
+ *   active_out, due_out  uint8[n] (out)
+ */
+GRAV_API int grav_select_due(int64_t n, int64_t tick, int32_t k_max, const int8_t *bin,
+                    int64_t *tf_ticks, const double *dt_grav, double q_f, double dt_min,
+                    uint8_t *active_out, uint8_t *due_out, int32_t *flags_dev, void *stream);
+
+/*
+ * grav_compact_active -- the due set as an index list (follows from
+ * Eq. (updatecondition): only due elements are evaluated).
+ * idx_out[0..c) = the indices i with flags[i] != 0, ascending; *count_dev = c
+ * written on the device (no host synchronisation).  idx_out has room for n
+ * entries; entries past c are left unchanged.  n <= INT32_MAX.
+ * workspace: >= grav_compact_workspace_bytes(n) bytes.
+ */
+GRAV_API int64_t grav_compact_workspace_bytes(int64_t n);
+GRAV_API int grav_compact_active(int64_t n, const uint8_t *flags, int32_t *idx_out, int32_t *count_dev,
+                        void *workspace, int64_t workspace_bytes, void *stream);
+
+/*
+ * grav_predict -- the first-order jerk predictor, Eq. (jerkupdate), in closed
+ * form: for active, not-due elements
+ *     a_out[i] = a_last[i] + j_last[i] * (tf_ticks[i] * dt_min)
+ * (one correctly rounded product for the elapsed time, then a product and a
+ * sum per component, no fused multiply-add); for active due elements
+ * a_out[i] = a_last[i]; inactive elements are not written.  The paper's
+ * incremental update g += j dt_i summed over the steps since the last
+ * evaluation equals this closed form in exact arithmetic.
+ * a_out may alias neither a_last nor j_last.
+ */
+GRAV_API int grav_predict(int64_t n, const uint8_t *active, const uint8_t *due, const double *a_last,
+                 const double *j_last, const int64_t *tf_ticks, double dt_min, double *a_out,
+                 void *stream);
+
+/*
+ * grav_assign_bins -- Section 2's dt_i = min(dt_grav_i, dt_hydro_i) placed on
+ * Section 3's power-of-two bins, for elements active at `tick`.
+ * The target bin is the smallest k in [0, k_max] with dt_max * 2^-k <= dt_i
+ * (exact comparison of mantissas and exponents; dt_i = +inf -> 0; dt_i <= 0 or
+ * NaN -> k_max); a step may only grow at a tick that is a multiple of the new
+ * step, so the bin is raised to the smallest k aligned with `tick`.
+ * dt_hydro is nullable (no limit).  Inactive elements keep their bin.
+ */
+GRAV_API int grav_assign_bins(int64_t n, int64_t tick, int32_t k_max, double dt_max, const uint8_t *active,
+                     const double *dt_grav, const double *dt_hydro, int8_t *bin, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Force evaluation: Eq. (4), Section 3's tidal tensor and tidal timestep.    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * grav_eval_active -- direct summation over all n_src sources j != i of
+ *   a_i   = G sum_j m_j f(r) d                                      (g of the paper)
+ *   j_i   = G sum_j m_j [ f(r) v_ji + g(r) (d . v_ji) d ]          (Eq. 4, softened)
+ *   T_i   = -G sum_j m_j [ f(r) I + g(r) d d^T ]   = d a_i / d x_i (Section 3)
+ *   Phi_i = -G sum_j m_j phi(r)                                     (if want_pot)
+ *   dt_grav_i = sqrt(eta) (||T_i||_F^2 / 6)^(-1/4)            (Eq. tidaltimestep)
+ * at the targets i = idx[0..c), c = *n_idx_dev (device word, e.g. from
+ * grav_compact_active) or n_idx_max when n_idx_dev is NULL; idx NULL means
+ * targets 0..n_src-1 (then n_idx_max must equal n_src).  Results are
+ * scattered to row i of acc [n_src][3], jerk [n_src][3], tidal [n_src][6],
+ * pot [n_src] (nullable unless want_pot) and dt_grav [n_src] (nullable); rows
+ * of non-targets are not written.  The self term j == i is excluded by index.
+ * c must not exceed n_idx_max (the launch is sized for n_idx_max).
+ * workspace: >= grav_eval_workspace_bytes(p, n_src, n_idx_max) bytes.
+ */
+GRAV_API int64_t grav_eval_workspace_bytes(const grav_params *p, int64_t n_src, int64_t n_idx_max);
+GRAV_API int grav_eval_active(const grav_params *p, int64_t n_src, const double *pos, const double *vel,
+                     const double *mass, const int32_t *idx, const int32_t *n_idx_dev,
+                     int64_t n_idx_max, double *acc, double *jerk, double *tidal, double *pot,
+                     double *dt_grav, int32_t *flags_dev, void *workspace,
+                     int64_t workspace_bytes, void *stream);
+
+/*
+ * grav_eval_backward -- adjoint of grav_eval_active over all n elements as
+ * targets (the paper has no adjoint; derived from Eq. 4 and the tidal tensor).
+ * For a loss L(a, W) with a_bar = dL/da ([n][3], nullable = 0) and
+ * w_bar = dL/dW, W = 1/2 sum_i m_i Phi_i the potential energy:
+ *   pos_bar_k  = T_k a_bar_k + G m_k sum_{i!=k} [ f a_bar_i + g d (d . a_bar_i) ]
+ *                - w_bar m_k a_k
+ *   mass_bar_k = -G sum_{i!=k} f (d . a_bar_i) + w_bar Phi_k,   d = x_i - x_k.
+ * acc, tidal and pot are the forward results at all n elements (acc and pot
+ * are read only when w_bar != 0, tidal only when a_bar is given).  Pair terms
+ * are recomputed, never stored.  pos_bar [n][3] and mass_bar [n] are written.
+ * workspace: >= grav_backward_workspace_bytes(p, n) bytes.
+ */
+GRAV_API int64_t grav_backward_workspace_bytes(const grav_params *p, int64_t n);
+GRAV_API int grav_eval_backward(const grav_params *p, int64_t n, const double *pos, const double *mass,
+                       const double *a_bar, double w_bar, const double *acc, const double *tidal,
+                       const double *pot, double *pos_bar, double *mass_bar, int32_t *flags_dev,
+                       void *workspace, int64_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement helper (not part of the method).                               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * grav_measure_fma_peak -- times a register-resident FMA throughput kernel
+ * (FP32 when precision == GRAV_MIXED, FP64 when GRAV_F64) on the current
+ * device with CUDA events and returns the achieved FLOP/s (FMA = 2 flops).
+ * Synchronises the stream.  Used to state the CUDA-core peak that the force
+ * kernels are measured against.
+ */
+GRAV_API int grav_measure_fma_peak(int32_t precision, double seconds_target, double *flops_per_s,
+                          void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAV_H */

@@ -1,0 +1,474 @@
+// K7: adjoint of the force evaluation (reverse mode), all n elements targets.
+//
+// For a loss L(a, W) with a_bar = dL/da and w_bar = dL/dW (W = 1/2 sum m Phi):
+//   pos_bar_k  = T_k a_bar_k + G m_k sum_{i!=k} [ f a_bar_i + g d (d . a_bar_i) ]
+//                - w_bar m_k a_k
+//   mass_bar_k = -G sum_{i!=k} f (d . a_bar_i) + w_bar Phi_k,      d = x_i - x_k,
+// obtained by differentiating a_i = G sum_j m_j f(r) d (Eq. 4's acceleration)
+// with respect to x_k and m_k; T_k = d a_k / d x_k is the forward tidal tensor.
+// The paper has no adjoint.  The kernel is the forward direct sum with the
+// source attribute a_bar_i in place of (v_i, m_i): per pair it accumulates
+//   X1 += f a_bar_i,   X2 += g' (d . a_bar_i) d,   MB += f (d . a_bar_i)
+// with g' = -g/3, recomputing every pair term instead of storing any, and the
+// epilogue forms pos_bar = T a_bar + G m (X1 - 3 X2) - w_bar m a.
+#include <cmath>
+#include <mutex>
+
+#include "grav_eval.cuh"
+
+namespace grav {
+namespace {
+
+constexpr int kNB = 7;
+enum { X10 = 0, X20 = 3, MBS = 6 };
+
+struct BwdArgs {
+    int64_t n;
+    const TileGeom *geo;
+    const void *src;
+    int32_t n_tiles;
+    int32_t max_split;
+    int32_t grid;
+    int32_t pad0;
+    double *part;
+    int64_t part_cap_rows;
+    const double *pos, *mass, *a_bar;
+    double w_bar;
+    const double *acc, *tidal, *pot;
+    double G, h;
+    float h2f_up, hinvf;
+    double *pos_bar, *mass_bar;
+    int32_t *flags;
+};
+
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T x);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrt_sfu(x); }
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ T sqrt_t(T x) { return sqrt(x); }
+
+template <typename T>
+struct Src;
+template <>
+struct Src<float> { using type = float4; };
+template <>
+struct Src<double> { using type = D4; };
+
+template <typename T, int KT, int S, bool NEAR>
+__device__ __forceinline__ void bwd_loop(const typename Src<T>::type *__restrict__ sp,
+                                         const typename Src<T>::type *__restrict__ sa,
+                                         const T tx[KT][3], const int64_t tk[KT], int64_t jbase,
+                                         T h2, T hinv, T acc[KT][kNB])
+{
+    const T hinv3 = hinv * hinv * hinv;
+    const T hinv5 = hinv3 * hinv * hinv;
+#pragma unroll 4
+    for (int j = 0; j < S; ++j) {
+        const auto p = sp[j];
+        const auto ab = sa[j];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            T dx = p.x - tx[q][0], dy = p.y - tx[q][1], dz = p.z - tx[q][2];
+            T r2 = dx * dx + dy * dy + dz * dz;
+            T ri = rsqrt_t<T>(r2);
+            T ri2 = ri * ri;
+            T f = ri * ri2;
+            T gp = f * ri2;
+            if (NEAR && r2 < h2) {
+                T F, Gp, P;
+                spline_kernel<T>(sqrt_t<T>(r2) * hinv, F, Gp, P);
+                f = F * hinv3;
+                gp = Gp * hinv5;
+                if (jbase + j == tk[q]) {
+                    f = T(0);
+                    gp = T(0);
+                }
+            }
+            T da = dx * ab.x + dy * ab.y + dz * ab.z;
+            acc[q][X10 + 0] += f * ab.x;
+            acc[q][X10 + 1] += f * ab.y;
+            acc[q][X10 + 2] += f * ab.z;
+            T gd = gp * da;
+            acc[q][X20 + 0] += gd * dx;
+            acc[q][X20 + 1] += gd * dy;
+            acc[q][X20 + 2] += gd * dz;
+            acc[q][MBS] += f * da;
+        }
+    }
+}
+
+__device__ __forceinline__ void bwd_write(const BwdArgs &a, int64_t k, const double s[kNB])
+{
+    const double m = a.mass[k];
+    double px[3] = {0.0, 0.0, 0.0};
+    double pm = 0.0;
+    if (a.a_bar) {
+        const double *t6 = a.tidal + 6 * k;
+        const double *ak = a.a_bar + 3 * k;
+        px[0] = t6[0] * ak[0] + t6[3] * ak[1] + t6[4] * ak[2];
+        px[1] = t6[3] * ak[0] + t6[1] * ak[1] + t6[5] * ak[2];
+        px[2] = t6[4] * ak[0] + t6[5] * ak[1] + t6[2] * ak[2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) px[c] += a.G * m * (s[X10 + c] - 3.0 * s[X20 + c]);
+        pm = -a.G * s[MBS];
+    }
+    if (a.w_bar != 0.0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) px[c] -= a.w_bar * m * a.acc[3 * k + c];
+        pm += a.w_bar * a.pot[k];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.pos_bar[3 * k + c] = px[c];
+    a.mass_bar[k] = pm;
+}
+
+template <typename T, int NT, int KT, int S, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+backward_kernel(const BwdArgs a)
+{
+    using E = typename Src<T>::type;
+    constexpr bool MIXED = sizeof(T) == 4;
+    constexpr int BT = NT * KT;
+    constexpr int NSTAGE = 2;
+    constexpr uint32_t kTileBytes = S * 2 * sizeof(E);
+    __shared__ __align__(128) E stage[NSTAGE][2 * S];
+    __shared__ __align__(8) uint64_t bar[NSTAGE];
+    __shared__ float blo[3], bhi[3];
+    __shared__ int abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    uint32_t parity = 0, pending = 0;
+
+    const int64_t n_tb = (a.n + BT - 1) / BT;
+    const int split = choose_split(n_tb, a.n_tiles, a.grid, a.max_split, a.part_cap_rows, BT);
+    const int64_t items = n_tb * split;
+    const int64_t rows = n_tb * BT;
+    const E *src = static_cast<const E *>(a.src);
+    const T h2 = MIXED ? (T)a.h2f_up : (T)(a.h * a.h);
+    const T hinv = MIXED ? (T)a.hinvf : (T)(1.0 / a.h);
+
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t tb = item / split;
+        const int sp = (int)(item - tb * split);
+        const int t_begin = (int)((int64_t)sp * a.n_tiles / split);
+        const int t_end = (int)((int64_t)(sp + 1) * a.n_tiles / split);
+
+        double xk[KT][3];
+        int64_t tk[KT];
+        float lo[3], hi[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = __int_as_float(0x7f800000);
+            hi[c] = -__int_as_float(0x7f800000);
+        }
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const int64_t k = tb * BT + (int64_t)q * NT + threadIdx.x;
+            tk[q] = k < a.n ? k : -1;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xk[q][c] = tk[q] >= 0 ? a.pos[3 * k + c] : 0.0;
+                if (tk[q] >= 0) {
+                    lo[c] = fminf(lo[c], __double2float_rd(xk[q][c]));
+                    hi[c] = fmaxf(hi[c], __double2float_ru(xk[q][c]));
+                }
+            }
+        }
+        block_bbox<NT>(lo, hi, blo, bhi);
+        const float blo_r[3] = {blo[0], blo[1], blo[2]};
+        const float bhi_r[3] = {bhi[0], bhi[1], bhi[2]};
+
+        T shi[KT][kNB], slo[KT][kNB];
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+#pragma unroll
+            for (int c = 0; c < kNB; ++c) {
+                shi[q][c] = T(0);
+                slo[q][c] = T(0);
+            }
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < NSTAGE; ++s) {
+                int t = t_begin + s;
+                if (t < t_end) {
+                    tma_load_1d(stage[s], src + (int64_t)t * 2 * S, kTileBytes, &bar[s]);
+                    pending |= 1u << s;
+                }
+            }
+        }
+        for (int t = t_begin; t < t_end; ++t) {
+            const int s = (t - t_begin) % NSTAGE;
+            const TileGeom g = a.geo[t];
+            const bool near = tile_is_near(blo_r, bhi_r, g, a.h2f_up);
+            T tx[KT][3];
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (MIXED)
+                        tx[q][c] = (T)__double2float_rn(__dsub_rn(xk[q][c], g.c[c]));
+                    else
+                        tx[q][c] = (T)xk[q][c];
+                }
+            const bool got = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, a.flags);
+            if (got)
+                parity ^= 1u << s;
+            else
+                atomicExch(&abort_flag, 1);
+            T acc[KT][kNB];
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+#pragma unroll
+                for (int c = 0; c < kNB; ++c) acc[q][c] = T(0);
+            if (!near)
+                bwd_loop<T, KT, S, false>(stage[s], stage[s] + S, tx, tk, (int64_t)t * S, h2, hinv, acc);
+            else
+                bwd_loop<T, KT, S, true>(stage[s], stage[s] + S, tx, tk, (int64_t)t * S, h2, hinv, acc);
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+#pragma unroll
+                for (int c = 0; c < kNB; ++c) two_sum_acc(shi[q][c], slo[q][c], acc[q][c]);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (got) pending &= ~(1u << s);
+                if (t + NSTAGE < t_end && !abort_flag) {
+                    tma_load_1d(stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes, &bar[s]);
+                    pending |= 1u << s;
+                }
+            }
+            if (abort_flag) break;
+        }
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            double sum[kNB];
+#pragma unroll
+            for (int c = 0; c < kNB; ++c) sum[c] = (double)shi[q][c] + (double)slo[q][c];
+            const int64_t slot = tb * BT + (int64_t)q * NT + threadIdx.x;
+            if (split == 1) {
+                if (tk[q] >= 0) bwd_write(a, tk[q], sum);
+            } else {
+#pragma unroll
+                for (int c = 0; c < kNB; ++c) a.part[((int64_t)sp * kNB + c) * rows + slot] = sum[c];
+            }
+        }
+        if (abort_flag) break;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && pending) {
+        for (int s = 0; s < NSTAGE; ++s)
+            if (pending & (1u << s)) mbar_wait_bounded(&bar[s], (parity >> s) & 1u, a.flags);
+    }
+}
+
+__global__ void __launch_bounds__(256) backward_reduce_kernel(const BwdArgs a, int32_t BT)
+{
+    const int64_t n_tb = (a.n + BT - 1) / BT;
+    const int split = choose_split(n_tb, a.n_tiles, a.grid, a.max_split, a.part_cap_rows, BT);
+    if (split <= 1) return;
+    const int64_t rows = n_tb * BT;
+    const int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (k >= a.n) return;
+    double hi[kNB], lo[kNB];
+#pragma unroll
+    for (int c = 0; c < kNB; ++c) {
+        hi[c] = 0.0;
+        lo[c] = 0.0;
+    }
+    for (int sp = 0; sp < split; ++sp)
+#pragma unroll
+        for (int c = 0; c < kNB; ++c) two_sum_acc(hi[c], lo[c], a.part[((int64_t)sp * kNB + c) * rows + k]);
+    double sum[kNB];
+#pragma unroll
+    for (int c = 0; c < kNB; ++c) sum[c] = hi[c] + lo[c];
+    bwd_write(a, k, sum);
+}
+
+// a_bar == NULL: only the potential-energy terms, elementwise.
+__global__ void __launch_bounds__(256) backward_pot_only_kernel(const BwdArgs a)
+{
+    const int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (k >= a.n) return;
+    double zero[kNB] = {0, 0, 0, 0, 0, 0, 0};
+    bwd_write(a, k, zero);
+}
+
+// Fixed tile shapes of the adjoint.
+constexpr int kBwdNTf = 128, kBwdKTf = 2, kBwdSf = 256, kBwdMinBf = 3;
+constexpr int kBwdNTd = 128, kBwdKTd = 1, kBwdSd = 128, kBwdMinBd = 2;
+
+struct BwdLayout {
+    int64_t n_tiles, geo_off, src_off, part_off, total, part_cap_rows;
+    int32_t max_split, S, BT;
+};
+
+int bwd_layout(const grav_params *p, int64_t n, BwdLayout *L)
+{
+    int sms = 0;
+    int rc = device_sm_count(&sms);
+    if (rc) return rc;
+    const bool mixed = p->precision == GRAV_MIXED;
+    L->S = mixed ? kBwdSf : kBwdSd;
+    L->BT = mixed ? kBwdNTf * kBwdKTf : kBwdNTd * kBwdKTd;
+    const int64_t elem = mixed ? 16 : 32;
+    L->max_split = p->max_split > 0 ? p->max_split : kDefaultMaxSplit;
+    L->n_tiles = (n + L->S - 1) / L->S;
+    L->geo_off = 0;
+    L->src_off = round_up(L->n_tiles * (int64_t)sizeof(TileGeom), 256);
+    L->part_off = L->src_off + round_up(L->n_tiles * 2 * L->S * elem, 256);
+    const int64_t n_tb = (n + L->BT - 1) / L->BT;
+    int64_t blocks = 0;
+    if (L->max_split > 1 && L->n_tiles > 1) blocks = std::min<int64_t>(n_tb * L->max_split, 16LL * sms);
+    L->part_cap_rows = blocks * L->BT;
+    L->total = std::max<int64_t>(256, L->part_off + round_up(L->part_cap_rows * kNB * 8, 256));
+    return GRAV_OK;
+}
+
+int bwd_grid(bool mixed, int *grid)
+{
+    static std::mutex mu;
+    static int cache[64][2];
+    int dev = 0, sms = 0;
+    int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    rc = device_sm_count(&sms);
+    if (rc) return rc;
+    if (dev >= 64) return fail(GRAV_ECUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    int &slot = cache[dev][mixed ? 1 : 0];
+    if (slot == 0) {
+        int b = 0;
+        cudaError_t e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &b, backward_kernel<float, kBwdNTf, kBwdKTf, kBwdSf, kBwdMinBf>, kBwdNTf, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &b, backward_kernel<double, kBwdNTd, kBwdKTd, kBwdSd, kBwdMinBd>, kBwdNTd, 0);
+        rc = check_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        if (rc) return rc;
+        if (b < 1) return fail(GRAV_ECUDA, "adjoint kernel cannot be resident on an SM");
+        slot = b * sms;
+    }
+    *grid = slot;
+    return GRAV_OK;
+}
+
+int check_bwd_params(const grav_params *p, const char *who)
+{
+    if (!p) return fail(GRAV_EINVAL, "%s: null params", who);
+    if (!(p->G > 0.0) || !std::isfinite(p->G)) return fail(GRAV_EINVAL, "%s: G must be finite and > 0", who);
+    if (!(p->h > 0.0) || !std::isfinite(p->h)) return fail(GRAV_EINVAL, "%s: h must be finite and > 0", who);
+    if (p->precision != GRAV_F64 && p->precision != GRAV_MIXED)
+        return fail(GRAV_EINVAL, "%s: precision must be GRAV_F64 or GRAV_MIXED", who);
+    if (p->max_split < 0) return fail(GRAV_EINVAL, "%s: max_split < 0", who);
+    return GRAV_OK;
+}
+
+}  // namespace
+}  // namespace grav
+
+using namespace grav;
+
+extern "C" int64_t grav_backward_workspace_bytes(const grav_params *p, int64_t n)
+{
+    int rc = check_bwd_params(p, "grav_backward_workspace_bytes");
+    if (rc) return rc;
+    if (n < 0 || n > INT32_MAX) return fail(GRAV_EINVAL, "grav_backward_workspace_bytes: n outside [0, 2^31)");
+    BwdLayout L;
+    rc = bwd_layout(p, n, &L);
+    if (rc) return rc;
+    return L.total;
+}
+
+extern "C" int grav_eval_backward(const grav_params *p, int64_t n, const double *pos,
+                                  const double *mass, const double *a_bar, double w_bar,
+                                  const double *acc, const double *tidal, const double *pot,
+                                  double *pos_bar, double *mass_bar, int32_t *flags_dev,
+                                  void *workspace, int64_t workspace_bytes, void *stream)
+{
+    static const char *who = "grav_eval_backward";
+    int rc = check_bwd_params(p, who);
+    if (rc) return rc;
+    if (n < 0 || n > INT32_MAX) return fail(GRAV_EINVAL, "%s: n outside [0, 2^31)", who);
+    if (!std::isfinite(w_bar)) return fail(GRAV_EINVAL, "%s: w_bar not finite", who);
+    if (n == 0) return GRAV_OK;
+    if (!pos || !mass || !pos_bar || !mass_bar) return fail(GRAV_EINVAL, "%s: null array", who);
+    if (a_bar && !tidal) return fail(GRAV_EINVAL, "%s: a_bar given but tidal is NULL", who);
+    if (w_bar != 0.0 && (!acc || !pot)) return fail(GRAV_EINVAL, "%s: w_bar != 0 needs acc and pot", who);
+    const bool mixed = p->precision == GRAV_MIXED;
+    BwdLayout L;
+    rc = bwd_layout(p, n, &L);
+    if (rc) return rc;
+    if (a_bar) {
+        if (!workspace) return fail(GRAV_EINVAL, "%s: null workspace", who);
+        if (!aligned(workspace, 256)) return fail(GRAV_EINVAL, "%s: workspace not 256-byte aligned", who);
+        if (workspace_bytes < L.total)
+            return fail(GRAV_ENOMEM, "%s: workspace of %lld bytes < %lld", who, (long long)workspace_bytes,
+                        (long long)L.total);
+    }
+    int grid = 0;
+    rc = bwd_grid(mixed, &grid);
+    if (rc) return rc;
+    char *ws = static_cast<char *>(workspace);
+    BwdArgs a;
+    a.n = n;
+    a.geo = reinterpret_cast<const TileGeom *>(ws + L.geo_off);
+    a.src = ws + L.src_off;
+    a.n_tiles = (int32_t)L.n_tiles;
+    a.max_split = L.max_split;
+    a.grid = grid;
+    a.pad0 = 0;
+    a.part = reinterpret_cast<double *>(ws + L.part_off);
+    a.part_cap_rows = L.part_cap_rows;
+    a.pos = pos;
+    a.mass = mass;
+    a.a_bar = a_bar;
+    a.w_bar = w_bar;
+    a.acc = acc;
+    a.tidal = tidal;
+    a.pot = pot;
+    a.G = p->G;
+    a.h = p->h;
+    double h2 = p->h * p->h;
+    float h2f = (float)h2;
+    if ((double)h2f < h2) h2f = std::nextafter(h2f, INFINITY);
+    a.h2f_up = h2f;
+    a.hinvf = (float)(1.0 / p->h);
+    a.pos_bar = pos_bar;
+    a.mass_bar = mass_bar;
+    a.flags = flags_dev;
+    cudaStream_t st = as_stream(stream);
+    const unsigned eblocks = (unsigned)((n + 255) / 256);
+    if (!a_bar) {
+        backward_pot_only_kernel<<<eblocks, 256, 0, st>>>(a);
+        return check_launch("grav_eval_backward/pot");
+    }
+    // Pack (x, a_bar) tiles: the forward packer with a_bar in the velocity
+    // slot and no mass.
+    if (mixed)
+        pack_tiles_kernel<kBwdSf, true><<<(unsigned)L.n_tiles, kBwdSf, 0, st>>>(
+            n, pos, a_bar, nullptr, const_cast<TileGeom *>(a.geo), const_cast<void *>(a.src), flags_dev);
+    else
+        pack_tiles_kernel<kBwdSd, false><<<(unsigned)L.n_tiles, kBwdSd, 0, st>>>(
+            n, pos, a_bar, nullptr, const_cast<TileGeom *>(a.geo), const_cast<void *>(a.src), flags_dev);
+    rc = check_launch("grav_eval_backward/pack");
+    if (rc) return rc;
+    if (mixed)
+        backward_kernel<float, kBwdNTf, kBwdKTf, kBwdSf, kBwdMinBf><<<grid, kBwdNTf, 0, st>>>(a);
+    else
+        backward_kernel<double, kBwdNTd, kBwdKTd, kBwdSd, kBwdMinBd><<<grid, kBwdNTd, 0, st>>>(a);
+    rc = check_launch("grav_eval_backward/sum");
+    if (rc) return rc;
+    const int64_t n_tb = (n + L.BT - 1) / L.BT;
+    if (L.part_cap_rows > 0 &&
+        choose_split(n_tb, a.n_tiles, grid, a.max_split, a.part_cap_rows, L.BT) > 1) {
+        backward_reduce_kernel<<<eblocks, 256, 0, st>>>(a, L.BT);
+        rc = check_launch("grav_eval_backward/reduce");
+    }
+    return rc;
+}

@@ -1,0 +1,894 @@
+// Force evaluation kernels of libgrav (Grudic 2020, Eq. 4 and Section 3).
+//
+// Direct summation, target-blocked: a CTA owns a block of BT = NT*KT targets
+// (KT per thread, in registers) and streams source tiles of S elements through
+// shared memory with 1-D TMA bulk copies (cp.async.bulk + mbarrier, double
+// buffered).  Every thread evaluates each staged source against its KT
+// targets with the SFU reciprocal square root; all lanes read the same source
+// (shared-memory broadcast).  This is CUDA-core work, not a contraction: no
+// tensor cores.
+//
+// Per pair the kernel accumulates, with d = x_j - x_i and v = v_j - v_i,
+//   A  += m f d          J1 += m f v         J2 += m g' (d.v) d
+//   F  += m f            Tp += m g' d d^T    P  += m phi   (optional)
+// where g' = -g/3 (= r^-5 beyond the softening).  The epilogue forms
+//   a = G A,  j = G (J1 - 3 J2),  T = -G (F I - 3 Tp),  Phi = -G P,
+// and the tidal timestep of Eq. (tidaltimestep) in FP64.
+//
+// Tiles whose bounding box lies at least h from the target block's bounding
+// box take the Newtonian loop (exact there: the cubic spline has compact
+// support); the others take the softened loop, which also excludes the self
+// pair by index.  Mixed precision: positions are FP64; each source tile stores
+// FP32 offsets from its FP64 bounding-box centre, each target's offset to that
+// centre is formed in FP64 and rounded once, pair arithmetic and per-tile sums
+// are FP32, tile sums are carried across tiles as compensated FP32 pairs
+// (TwoSum) and the final per-target result is FP64.
+//
+// Work items are (target block, source chunk).  A fixed grid of CTAs takes
+// items round-robin; when the target set is small the sources are split into
+// chunks so that every SM has work, and the chunk partials are reduced by a
+// second kernel in a fixed order (deterministic results).
+#pragma once
+
+#include "grav_common.cuh"
+
+namespace grav {
+
+constexpr int kNC = 16;            // accumulators without the potential
+constexpr int kNCPot = 17;         // with the potential
+constexpr int kDefaultMaxSplit = 64;
+
+// Accumulator slots.
+enum { A0 = 0, J10 = 3, J20 = 6, FSUM = 9, TXX = 10, TYY, TZZ, TXY, TXZ, TYZ, PSUM = 16 };
+
+struct __align__(16) TileGeom {
+    double c[3];    // FP64 bounding-box centre (offset origin of the mixed path)
+    float lo[3];    // bounding box, rounded outward to FP32
+    float hi[3];
+    int32_t count;  // real sources in the tile
+    int32_t pad[3];
+};
+static_assert(sizeof(TileGeom) == 64, "TileGeom layout");
+
+struct __align__(16) D4 {
+    double x, y, z, w;
+};
+
+struct EvalArgs {
+    int64_t n_src;
+    const int32_t *idx;        // nullable: targets are 0..n_idx_max-1
+    const int32_t *n_idx_dev;  // nullable: count is n_idx_max
+    int64_t n_idx_max;
+    const TileGeom *geo;
+    const void *src;           // packed tiles
+    int32_t n_tiles;
+    int32_t max_split;
+    int32_t grid;              // CTAs of the persistent launch (split policy input)
+    int32_t pad0;
+    double *part;              // split partials
+    int64_t part_cap_rows;     // partial rows available (each row NC doubles)
+    const double *pos;
+    const double *vel;
+    double G, h, sqrt_eta;
+    float hf, h2f_up, hinvf, pad1;
+    double *acc, *jerk, *tidal, *pot, *dt_grav;
+    int32_t *flags;
+};
+
+// Number of source chunks per target block.  Shared by the host, the eval
+// kernel and the reduction kernel, so it must depend only on its arguments.
+__host__ __device__ inline int choose_split(int64_t n_tb, int32_t n_tiles, int32_t grid,
+                                            int32_t max_split, int64_t part_cap_rows, int32_t BT)
+{
+    if (n_tb <= 0 || max_split <= 1 || n_tiles <= 1 || grid <= 0) return 1;
+    if (n_tb >= 4LL * grid) return 1;
+    int64_t s_max = max_split < n_tiles ? max_split : n_tiles;
+    int64_t cap = part_cap_rows / (n_tb * (int64_t)BT);
+    if (cap < s_max) s_max = cap;
+    if (s_max <= 1) return 1;
+    int64_t best = 1, best_items = n_tb, best_slots = ((n_tb + grid - 1) / grid) * grid;
+    for (int64_t s = 1; s <= s_max; ++s) {
+        int64_t items = n_tb * s;
+        int64_t slots = ((items + grid - 1) / grid) * grid;
+        if (items >= grid && 10 * items >= 9 * slots) return (int)s;
+        if (items * best_slots > best_items * slots) {
+            best = s;
+            best_items = items;
+            best_slots = slots;
+        }
+    }
+    return (int)best;
+}
+
+__device__ __forceinline__ int64_t active_count(const EvalArgs &a)
+{
+    int64_t n = a.n_idx_max;
+    if (a.n_idx_dev) {
+        int64_t c = *a.n_idx_dev;
+        if (c < 0) c = 0;
+        if (c < n) n = c;
+    }
+    return n;
+}
+
+// Final FP64 outputs of one target from its accumulated sums.
+template <bool POT>
+__device__ __forceinline__ void write_target(const EvalArgs &a, int64_t i, const double s[kNCPot])
+{
+    const double G = a.G;
+    double t6[6];
+    t6[0] = -G * (s[FSUM] - 3.0 * s[TXX]);
+    t6[1] = -G * (s[FSUM] - 3.0 * s[TYY]);
+    t6[2] = -G * (s[FSUM] - 3.0 * s[TZZ]);
+    t6[3] = 3.0 * G * s[TXY];
+    t6[4] = 3.0 * G * s[TXZ];
+    t6[5] = 3.0 * G * s[TYZ];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a.acc[3 * i + c] = G * s[A0 + c];
+        a.jerk[3 * i + c] = G * (s[J10 + c] - 3.0 * s[J20 + c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) a.tidal[6 * i + c] = t6[c];
+    if (POT) a.pot[i] = -G * s[PSUM];
+    if (a.dt_grav) a.dt_grav[i] = tidal_dt(t6, a.sqrt_eta);
+}
+
+// Is the source tile within h of the target block (conservative: any doubt
+// means "near")?  blo/bhi is the target block's outward-rounded bbox.
+__device__ __forceinline__ bool tile_is_near(const float blo[3], const float bhi[3],
+                                             const TileGeom &g, float h2_up)
+{
+    float d2 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float gap = fmaxf(0.0f, fmaxf(__fsub_rd(g.lo[c], bhi[c]), __fsub_rd(blo[c], g.hi[c])));
+        d2 = __fmaf_rd(gap, gap, d2);
+    }
+    return !(d2 >= h2_up);
+}
+
+// Block reduction of the targets' outward bounding box into shared blo/bhi.
+template <int NT>
+__device__ __forceinline__ void block_bbox(float lo[3], float hi[3], float *blo, float *bhi)
+{
+    __shared__ float wlo[3][NT / 32], whi[3][NT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+        if (lane == 0) {
+            wlo[c][wid] = lo[c];
+            whi[c][wid] = hi[c];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        float l = wlo[threadIdx.x][0], h = whi[threadIdx.x][0];
+        for (int w = 1; w < NT / 32; ++w) {
+            l = fminf(l, wlo[threadIdx.x][w]);
+            h = fmaxf(h, whi[threadIdx.x][w]);
+        }
+        blo[threadIdx.x] = l;
+        bhi[threadIdx.x] = h;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Tile packing (K3)
+// ---------------------------------------------------------------------------
+
+// Block-wide FP64 min/max over S threads.
+template <int S>
+__device__ __forceinline__ void block_minmax_d(double lo[3], double hi[3], double *slo, double *shi)
+{
+    __shared__ double wlo[3][S / 32], whi[3][S / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fmin(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmax(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+        if (lane == 0) {
+            wlo[c][wid] = lo[c];
+            whi[c][wid] = hi[c];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double l = wlo[threadIdx.x][0], h = whi[threadIdx.x][0];
+        for (int w = 1; w < S / 32; ++w) {
+            l = fmin(l, wlo[threadIdx.x][w]);
+            h = fmax(h, whi[threadIdx.x][w]);
+        }
+        slo[threadIdx.x] = l;
+        shi[threadIdx.x] = h;
+    }
+    __syncthreads();
+}
+
+// One CTA of S threads per tile.  MIXED: tile = [S x float4 (offset, m)]
+// [S x float4 (v, 0)]; F64: tile = [S x D4 (x, m)][S x D4 (v, 0)].  Padding
+// sources have zero mass and sit far away, so they contribute exactly 0.
+template <int S, bool MIXED>
+__global__ void __launch_bounds__(S)
+pack_tiles_kernel(int64_t n_src, const double *__restrict__ pos, const double *__restrict__ vel,
+                  const double *__restrict__ mass, TileGeom *__restrict__ geo, void *__restrict__ src,
+                  int32_t *flags)
+{
+    __shared__ double slo[3], shi[3];
+    const int t = blockIdx.x, j = threadIdx.x;
+    const int64_t gj = (int64_t)t * S + j;
+    const bool ok = gj < n_src;
+    double x[3] = {0, 0, 0}, v[3] = {0, 0, 0}, m = 0.0;
+    if (ok) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            x[c] = pos[3 * gj + c];
+            v[c] = vel[3 * gj + c];
+        }
+        m = mass ? mass[gj] : 0.0;
+        if (!(finite3(x[0], x[1], x[2]) && finite3(v[0], v[1], v[2]) && isfinite(m)))
+            flag_or(flags, GRAV_FLAG_NONFINITE);
+    }
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    double lo[3], hi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = ok ? x[c] : inf;
+        hi[c] = ok ? x[c] : -inf;
+    }
+    block_minmax_d<S>(lo, hi, slo, shi);
+    double cc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) cc[c] = __dmul_rn(0.5, __dadd_rn(slo[c], shi[c]));
+    if (MIXED) {
+        float4 *tile = static_cast<float4 *>(src) + (int64_t)t * 2 * S;
+        float4 pm, pv;
+        if (ok) {
+            pm = make_float4(__double2float_rn(__dsub_rn(x[0], cc[0])),
+                             __double2float_rn(__dsub_rn(x[1], cc[1])),
+                             __double2float_rn(__dsub_rn(x[2], cc[2])), __double2float_rn(m));
+            pv = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]),
+                             __double2float_rn(v[2]), 0.0f);
+        } else {
+            pm = make_float4(1.0e18f, 0.0f, 0.0f, 0.0f);
+            pv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+        tile[j] = pm;
+        tile[S + j] = pv;
+    } else {
+        D4 *tile = static_cast<D4 *>(src) + (int64_t)t * 2 * S;
+        D4 pm, pv;
+        if (ok) {
+            pm = D4{x[0], x[1], x[2], m};
+            pv = D4{v[0], v[1], v[2], 0.0};
+        } else {
+            pm = D4{1.0e150, 0.0, 0.0, 0.0};
+            pv = D4{0.0, 0.0, 0.0, 0.0};
+        }
+        tile[j] = pm;
+        tile[S + j] = pv;
+    }
+    if (j == 0) {
+        TileGeom g;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            g.c[c] = cc[c];
+            g.lo[c] = __double2float_rd(slo[c]);
+            g.hi[c] = __double2float_ru(shi[c]);
+        }
+        int64_t cnt = n_src - (int64_t)t * S;
+        g.count = (int32_t)(cnt < S ? cnt : S);
+        g.pad[0] = g.pad[1] = g.pad[2] = 0;
+        geo[t] = g;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cubic-spline kernel inside the support, u = r/h in [0, 1):
+//   F  = h^3 f        (f = M(<r)/(m r^3))
+//   Gp = -h^5 g / 3   (g = f'(r)/r; Gp -> u^-5 at u = 1, matching g' = r^-5)
+//   P  = h phi        (potential kernel, 2.8 at u = 0, 1 at u = 1)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void spline_kernel(T u, T &F, T &Gp, T &P)
+{
+    const T u2 = u * u;
+    if (u < T(0.5)) {
+        F = T(32.0 / 3.0) + u2 * (T(-192.0 / 5.0) + T(32.0) * u);
+        Gp = T(128.0 / 5.0) - T(32.0) * u;
+        P = T(14.0 / 5.0) + u2 * (T(-16.0 / 3.0) + u2 * (T(48.0 / 5.0) - T(32.0 / 5.0) * u));
+    } else {
+        const T ui = T(1) / u;
+        const T ui3 = ui * ui * ui;
+        F = T(64.0 / 3.0) + u * (T(-48.0) + u * (T(192.0 / 5.0) - T(32.0 / 3.0) * u)) -
+            ui3 * T(1.0 / 15.0);
+        Gp = T(16.0) * ui - T(128.0 / 5.0) + T(32.0 / 3.0) * u - ui3 * ui * ui * T(1.0 / 15.0);
+        P = T(16.0 / 5.0) - ui * T(1.0 / 15.0) +
+            u2 * (T(-32.0 / 3.0) + u * (T(16.0) + u * (T(-48.0 / 5.0) + T(32.0 / 15.0) * u)));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pair loops, mixed precision
+// ---------------------------------------------------------------------------
+
+template <int KT, bool POT>
+__device__ __forceinline__ void accumulate_f(float acc[KT][kNCPot], int q, float dx, float dy,
+                                             float dz, float ux, float uy, float uz, float mf,
+                                             float mg, float mp)
+{
+    acc[q][A0 + 0] = fmaf(mf, dx, acc[q][A0 + 0]);
+    acc[q][A0 + 1] = fmaf(mf, dy, acc[q][A0 + 1]);
+    acc[q][A0 + 2] = fmaf(mf, dz, acc[q][A0 + 2]);
+    acc[q][FSUM] += mf;
+    float dv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+    acc[q][J10 + 0] = fmaf(mf, ux, acc[q][J10 + 0]);
+    acc[q][J10 + 1] = fmaf(mf, uy, acc[q][J10 + 1]);
+    acc[q][J10 + 2] = fmaf(mf, uz, acc[q][J10 + 2]);
+    float gx = mg * dx, gy = mg * dy, gz = mg * dz;
+    acc[q][TXX] = fmaf(gx, dx, acc[q][TXX]);
+    acc[q][TYY] = fmaf(gy, dy, acc[q][TYY]);
+    acc[q][TZZ] = fmaf(gz, dz, acc[q][TZZ]);
+    acc[q][TXY] = fmaf(gx, dy, acc[q][TXY]);
+    acc[q][TXZ] = fmaf(gx, dz, acc[q][TXZ]);
+    acc[q][TYZ] = fmaf(gy, dz, acc[q][TYZ]);
+    acc[q][J20 + 0] = fmaf(gx, dv, acc[q][J20 + 0]);
+    acc[q][J20 + 1] = fmaf(gy, dv, acc[q][J20 + 1]);
+    acc[q][J20 + 2] = fmaf(gz, dv, acc[q][J20 + 2]);
+    if (POT) acc[q][PSUM] += mp;
+}
+
+// Newtonian loop: every pair is at least h apart and none is a self pair.
+template <int KT, int S, bool POT>
+__device__ __forceinline__ void far_loop_f(const float4 *__restrict__ sp,
+                                           const float4 *__restrict__ sv, const float tx[KT][3],
+                                           const float tv[KT][3], float acc[KT][kNCPot])
+{
+#pragma unroll 8
+    for (int j = 0; j < S; ++j) {
+        const float4 p = sp[j];
+        const float4 v = sv[j];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            float dx = p.x - tx[q][0], dy = p.y - tx[q][1], dz = p.z - tx[q][2];
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float ri = rsqrt_sfu(r2);
+            float ri2 = ri * ri;
+            float mp = p.w * ri;
+            float mf = mp * ri2;
+            float mg = mf * ri2;
+            accumulate_f<KT, POT>(acc, q, dx, dy, dz, v.x - tv[q][0], v.y - tv[q][1],
+                                  v.z - tv[q][2], mf, mg, mp);
+        }
+    }
+}
+
+// Softened loop: cubic-spline kernel inside h, self pair excluded by index.
+template <int KT, int S, bool POT>
+__device__ __forceinline__ void near_loop_f(const float4 *__restrict__ sp,
+                                            const float4 *__restrict__ sv, const float tx[KT][3],
+                                            const float tv[KT][3], const int64_t ti[KT],
+                                            int64_t jbase, float h2, float hinv,
+                                            float acc[KT][kNCPot])
+{
+    const float hinv3 = hinv * hinv * hinv;
+    const float hinv5 = hinv3 * hinv * hinv;
+#pragma unroll 2
+    for (int j = 0; j < S; ++j) {
+        const float4 p = sp[j];
+        const float4 v = sv[j];
+        const int64_t jg = jbase + j;
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            float dx = p.x - tx[q][0], dy = p.y - tx[q][1], dz = p.z - tx[q][2];
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float ri = rsqrt_sfu(r2);
+            float ri2 = ri * ri;
+            float mp = p.w * ri;
+            float mf = mp * ri2;
+            float mg = mf * ri2;
+            if (r2 < h2) {
+                float F, Gp, P;
+                spline_kernel<float>(sqrtf(r2) * hinv, F, Gp, P);
+                mf = p.w * F * hinv3;
+                mg = p.w * Gp * hinv5;
+                mp = p.w * P * hinv;
+                if (jg == ti[q]) {
+                    mf = 0.0f;
+                    mg = 0.0f;
+                    mp = 0.0f;
+                }
+            }
+            accumulate_f<KT, POT>(acc, q, dx, dy, dz, v.x - tv[q][0], v.y - tv[q][1],
+                                  v.z - tv[q][2], mf, mg, mp);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pair loops, FP64
+// ---------------------------------------------------------------------------
+
+template <bool POT>
+__device__ __forceinline__ void accumulate_d(double acc[kNCPot], double dx, double dy, double dz,
+                                             double ux, double uy, double uz, double mf, double mg,
+                                             double mp)
+{
+    acc[A0 + 0] = fma(mf, dx, acc[A0 + 0]);
+    acc[A0 + 1] = fma(mf, dy, acc[A0 + 1]);
+    acc[A0 + 2] = fma(mf, dz, acc[A0 + 2]);
+    acc[FSUM] += mf;
+    double dv = fma(dx, ux, fma(dy, uy, dz * uz));
+    acc[J10 + 0] = fma(mf, ux, acc[J10 + 0]);
+    acc[J10 + 1] = fma(mf, uy, acc[J10 + 1]);
+    acc[J10 + 2] = fma(mf, uz, acc[J10 + 2]);
+    double gx = mg * dx, gy = mg * dy, gz = mg * dz;
+    acc[TXX] = fma(gx, dx, acc[TXX]);
+    acc[TYY] = fma(gy, dy, acc[TYY]);
+    acc[TZZ] = fma(gz, dz, acc[TZZ]);
+    acc[TXY] = fma(gx, dy, acc[TXY]);
+    acc[TXZ] = fma(gx, dz, acc[TXZ]);
+    acc[TYZ] = fma(gy, dz, acc[TYZ]);
+    acc[J20 + 0] = fma(gx, dv, acc[J20 + 0]);
+    acc[J20 + 1] = fma(gy, dv, acc[J20 + 1]);
+    acc[J20 + 2] = fma(gz, dv, acc[J20 + 2]);
+    if (POT) acc[PSUM] += mp;
+}
+
+template <int S, bool POT, bool NEAR>
+__device__ __forceinline__ void loop_d(const D4 *__restrict__ sp, const D4 *__restrict__ sv,
+                                       const double xi[3], const double vi[3], int64_t ti,
+                                       int64_t jbase, double h2, double hinv,
+                                       double acc[kNCPot])
+{
+    const double hinv3 = hinv * hinv * hinv;
+    const double hinv5 = hinv3 * hinv * hinv;
+#pragma unroll 4
+    for (int j = 0; j < S; ++j) {
+        const D4 p = sp[j];
+        const D4 v = sv[j];
+        double dx = p.x - xi[0], dy = p.y - xi[1], dz = p.z - xi[2];
+        double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        double ri = rsqrt(r2);
+        double ri2 = ri * ri;
+        double mp = p.w * ri;
+        double mf = mp * ri2;
+        double mg = mf * ri2;
+        if (NEAR && r2 < h2) {
+            double F, Gp, P;
+            spline_kernel<double>(sqrt(r2) * hinv, F, Gp, P);
+            mf = p.w * F * hinv3;
+            mg = p.w * Gp * hinv5;
+            mp = p.w * P * hinv;
+            if (jbase + j == ti) {
+                mf = 0.0;
+                mg = 0.0;
+                mp = 0.0;
+            }
+        }
+        accumulate_d<POT>(acc, dx, dy, dz, v.x - vi[0], v.y - vi[1], v.z - vi[2], mf, mg, mp);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shared pieces of both eval kernels
+// ---------------------------------------------------------------------------
+
+// Writes one target's chunk partial (FP64) into column `slot` of the split's
+// partial block: part[(sp*NC + c) * rows + slot].
+template <int NC>
+__device__ __forceinline__ void write_partial(const EvalArgs &a, int sp, int64_t rows, int64_t slot,
+                                              const double s[kNCPot])
+{
+#pragma unroll
+    for (int c = 0; c < NC; ++c) a.part[((int64_t)sp * NC + c) * rows + slot] = s[c];
+}
+
+// ---------------------------------------------------------------------------
+// K5: mixed-precision eval kernel
+// ---------------------------------------------------------------------------
+
+template <int NT, int KT, int S, int MINB, bool POT>
+__global__ void __launch_bounds__(NT, MINB)
+eval_mixed_kernel(const EvalArgs a)
+{
+    constexpr int BT = NT * KT;
+    constexpr int NSTAGE = 2;
+    constexpr int NC = POT ? kNCPot : kNC;
+    constexpr uint32_t kTileBytes = S * 2 * sizeof(float4);
+    __shared__ __align__(128) float4 stage[NSTAGE][2 * S];
+    __shared__ __align__(8) uint64_t bar[NSTAGE];
+    __shared__ float blo[3], bhi[3];
+    __shared__ int abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    uint32_t parity = 0;             // bit s: parity of stage s's next completion
+    uint32_t pending = 0;            // thread 0 only: bit s set while a copy is in flight
+
+    const int64_t n_act = active_count(a);
+    const int64_t n_tb = (n_act + BT - 1) / BT;
+    const int split = choose_split(n_tb, a.n_tiles, a.grid, a.max_split, a.part_cap_rows, BT);
+    const int64_t items = n_tb * split;
+    const int64_t rows = n_tb * BT;
+    const float4 *src = static_cast<const float4 *>(a.src);
+
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t tb = item / split;
+        const int sp = (int)(item - tb * split);
+        const int t_begin = (int)((int64_t)sp * a.n_tiles / split);
+        const int t_end = (int)((int64_t)(sp + 1) * a.n_tiles / split);
+
+        // ---- targets of this block (KT per thread, strided by NT) ----
+        double xi[KT][3];
+        float tv[KT][3];
+        int64_t ti[KT];
+        float lo[3], hi[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = __int_as_float(0x7f800000);
+            hi[c] = -__int_as_float(0x7f800000);
+        }
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const int64_t slot = tb * BT + (int64_t)q * NT + threadIdx.x;
+            int64_t i = -1;
+            if (slot < n_act) {
+                i = a.idx ? (int64_t)a.idx[slot] : slot;
+                if (i < 0 || i >= a.n_src) {
+                    flag_or(a.flags, GRAV_FLAG_BADINDEX);
+                    i = -1;
+                }
+            }
+            ti[q] = i;
+            if (i >= 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    xi[q][c] = a.pos[3 * i + c];
+                    tv[q][c] = __double2float_rn(a.vel[3 * i + c]);
+                    lo[c] = fminf(lo[c], __double2float_rd(xi[q][c]));
+                    hi[c] = fmaxf(hi[c], __double2float_ru(xi[q][c]));
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    xi[q][c] = 0.0;
+                    tv[q][c] = 0.0f;
+                }
+            }
+        }
+        block_bbox<NT>(lo, hi, blo, bhi);
+        const float blo_r[3] = {blo[0], blo[1], blo[2]};
+        const float bhi_r[3] = {bhi[0], bhi[1], bhi[2]};
+
+        float shi[KT][kNCPot], slo[KT][kNCPot];
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+#pragma unroll
+            for (int c = 0; c < kNCPot; ++c) {
+                shi[q][c] = 0.0f;
+                slo[q][c] = 0.0f;
+            }
+
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < NSTAGE; ++s) {
+                int t = t_begin + s;
+                if (t < t_end) {
+                    tma_load_1d(stage[s], src + (int64_t)t * 2 * S, kTileBytes, &bar[s]);
+                    pending |= 1u << s;
+                }
+            }
+        }
+
+        // offsets of the targets to the first tile's centre (FP64, rounded once)
+        float tx[KT][3], tx_next[KT][3];
+        TileGeom g = a.geo[t_begin];
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tx[q][c] = __double2float_rn(__dsub_rn(xi[q][c], g.c[c]));
+
+        for (int t = t_begin; t < t_end; ++t) {
+            const int s = (t - t_begin) % NSTAGE;
+            const bool near = tile_is_near(blo_r, bhi_r, g, a.h2f_up);
+            // next tile's geometry and offsets, computed ahead (FP64 latency)
+            TileGeom gn = g;
+            if (t + 1 < t_end) {
+                gn = a.geo[t + 1];
+#pragma unroll
+                for (int q = 0; q < KT; ++q)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        tx_next[q][c] = __double2float_rn(__dsub_rn(xi[q][c], gn.c[c]));
+            }
+            const bool got = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, a.flags);
+            if (got)
+                parity ^= 1u << s;
+            else
+                atomicExch(&abort_flag, 1);
+
+            float acc[KT][kNCPot];
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+#pragma unroll
+                for (int c = 0; c < kNCPot; ++c) acc[q][c] = 0.0f;
+            const float4 *sp_ = stage[s];
+            const float4 *sv_ = stage[s] + S;
+            if (!near)
+                far_loop_f<KT, S, POT>(sp_, sv_, tx, tv, acc);
+            else
+                near_loop_f<KT, S, POT>(sp_, sv_, tx, tv, ti, (int64_t)t * S, a.h2f_up, a.hinvf,
+                                        acc);
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) two_sum_acc(shi[q][c], slo[q][c], acc[q][c]);
+
+            __syncthreads();                       // all reads of stage s are done
+            if (threadIdx.x == 0) {
+                if (got) pending &= ~(1u << s);
+                if (t + NSTAGE < t_end && !abort_flag) {
+                    tma_load_1d(stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes, &bar[s]);
+                    pending |= 1u << s;
+                }
+            }
+            if (abort_flag) break;
+            g = gn;
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) tx[q][c] = tx_next[q][c];
+        }
+
+        // ---- results ----
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            double sum[kNCPot];
+#pragma unroll
+            for (int c = 0; c < kNCPot; ++c) sum[c] = (double)shi[q][c] + (double)slo[q][c];
+            const int64_t slot = tb * BT + (int64_t)q * NT + threadIdx.x;
+            if (split == 1) {
+                if (ti[q] >= 0) write_target<POT>(a, ti[q], sum);
+            } else {
+                write_partial<NC>(a, sp, rows, slot, sum);
+            }
+        }
+        if (abort_flag) break;
+        __syncthreads();
+    }
+    // Never leave a copy in flight into shared memory (only after a timeout).
+    if (threadIdx.x == 0 && pending) {
+        for (int s = 0; s < NSTAGE; ++s)
+            if (pending & (1u << s)) mbar_wait_bounded(&bar[s], (parity >> s) & 1u, a.flags);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4: FP64 eval kernel (one target per thread)
+// ---------------------------------------------------------------------------
+
+template <int NT, int S, bool POT>
+__global__ void __launch_bounds__(NT, 2)
+eval_f64_kernel(const EvalArgs a)
+{
+    constexpr int BT = NT;
+    constexpr int NSTAGE = 2;
+    constexpr int NC = POT ? kNCPot : kNC;
+    constexpr uint32_t kTileBytes = S * 2 * sizeof(D4);
+    __shared__ __align__(128) D4 stage[NSTAGE][2 * S];
+    __shared__ __align__(8) uint64_t bar[NSTAGE];
+    __shared__ float blo[3], bhi[3];
+    __shared__ int abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    uint32_t parity = 0, pending = 0;
+
+    const int64_t n_act = active_count(a);
+    const int64_t n_tb = (n_act + BT - 1) / BT;
+    const int split = choose_split(n_tb, a.n_tiles, a.grid, a.max_split, a.part_cap_rows, BT);
+    const int64_t items = n_tb * split;
+    const int64_t rows = n_tb * BT;
+    const D4 *src = static_cast<const D4 *>(a.src);
+    const double h2 = a.h * a.h;
+    const double hinv = 1.0 / a.h;
+
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t tb = item / split;
+        const int sp = (int)(item - tb * split);
+        const int t_begin = (int)((int64_t)sp * a.n_tiles / split);
+        const int t_end = (int)((int64_t)(sp + 1) * a.n_tiles / split);
+
+        const int64_t slot = tb * BT + threadIdx.x;
+        int64_t i = -1;
+        if (slot < n_act) {
+            i = a.idx ? (int64_t)a.idx[slot] : slot;
+            if (i < 0 || i >= a.n_src) {
+                flag_or(a.flags, GRAV_FLAG_BADINDEX);
+                i = -1;
+            }
+        }
+        double xi[3] = {0, 0, 0}, vi[3] = {0, 0, 0};
+        float lo[3], hi[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = __int_as_float(0x7f800000);
+            hi[c] = -__int_as_float(0x7f800000);
+            if (i >= 0) {
+                xi[c] = a.pos[3 * i + c];
+                vi[c] = a.vel[3 * i + c];
+                lo[c] = __double2float_rd(xi[c]);
+                hi[c] = __double2float_ru(xi[c]);
+            }
+        }
+        block_bbox<NT>(lo, hi, blo, bhi);
+        const float blo_r[3] = {blo[0], blo[1], blo[2]};
+        const float bhi_r[3] = {bhi[0], bhi[1], bhi[2]};
+
+        double shi[kNCPot], slo[kNCPot];
+#pragma unroll
+        for (int c = 0; c < kNCPot; ++c) {
+            shi[c] = 0.0;
+            slo[c] = 0.0;
+        }
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < NSTAGE; ++s) {
+                int t = t_begin + s;
+                if (t < t_end) {
+                    tma_load_1d(stage[s], src + (int64_t)t * 2 * S, kTileBytes, &bar[s]);
+                    pending |= 1u << s;
+                }
+            }
+        }
+        for (int t = t_begin; t < t_end; ++t) {
+            const int s = (t - t_begin) % NSTAGE;
+            const TileGeom g = a.geo[t];
+            const bool near = tile_is_near(blo_r, bhi_r, g, a.h2f_up);
+            const bool got = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, a.flags);
+            if (got)
+                parity ^= 1u << s;
+            else
+                atomicExch(&abort_flag, 1);
+            double acc[kNCPot];
+#pragma unroll
+            for (int c = 0; c < kNCPot; ++c) acc[c] = 0.0;
+            if (!near)
+                loop_d<S, POT, false>(stage[s], stage[s] + S, xi, vi, i, (int64_t)t * S, h2, hinv, acc);
+            else
+                loop_d<S, POT, true>(stage[s], stage[s] + S, xi, vi, i, (int64_t)t * S, h2, hinv, acc);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) two_sum_acc(shi[c], slo[c], acc[c]);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (got) pending &= ~(1u << s);
+                if (t + NSTAGE < t_end && !abort_flag) {
+                    tma_load_1d(stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes, &bar[s]);
+                    pending |= 1u << s;
+                }
+            }
+            if (abort_flag) break;
+        }
+        double sum[kNCPot];
+#pragma unroll
+        for (int c = 0; c < kNCPot; ++c) sum[c] = shi[c] + slo[c];
+        if (split == 1) {
+            if (i >= 0) write_target<POT>(a, i, sum);
+        } else {
+            write_partial<NC>(a, sp, rows, slot, sum);
+        }
+        if (abort_flag) break;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && pending) {
+        for (int s = 0; s < NSTAGE; ++s)
+            if (pending & (1u << s)) mbar_wait_bounded(&bar[s], (parity >> s) & 1u, a.flags);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K9: deterministic reduction of the chunk partials (fixed chunk order)
+// ---------------------------------------------------------------------------
+
+template <bool POT>
+__global__ void __launch_bounds__(256)
+reduce_partials_kernel(const EvalArgs a, int32_t BT)
+{
+    constexpr int NC = POT ? kNCPot : kNC;
+    const int64_t n_act = active_count(a);
+    const int64_t n_tb = (n_act + BT - 1) / BT;
+    const int split = choose_split(n_tb, a.n_tiles, a.grid, a.max_split, a.part_cap_rows, BT);
+    if (split <= 1) return;
+    const int64_t rows = n_tb * BT;
+    const int64_t slot = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (slot >= n_act) return;
+    int64_t i = a.idx ? (int64_t)a.idx[slot] : slot;
+    if (i < 0 || i >= a.n_src) return;
+    double hi[kNCPot], lo[kNCPot];
+#pragma unroll
+    for (int c = 0; c < kNCPot; ++c) {
+        hi[c] = 0.0;
+        lo[c] = 0.0;
+    }
+    for (int sp = 0; sp < split; ++sp) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            two_sum_acc(hi[c], lo[c], a.part[((int64_t)sp * NC + c) * rows + slot]);
+    }
+    double sum[kNCPot];
+#pragma unroll
+    for (int c = 0; c < kNCPot; ++c) sum[c] = hi[c] + lo[c];
+    write_target<POT>(a, i, sum);
+}
+
+// ---------------------------------------------------------------------------
+// Launch table
+// ---------------------------------------------------------------------------
+
+typedef void (*eval_launch_fn)(const EvalArgs &, int grid, cudaStream_t);
+typedef int (*occupancy_fn)(int *blocks_per_sm);
+typedef void (*pack_launch_fn)(int64_t n_src, const double *, const double *, const double *,
+                               TileGeom *, void *, int32_t *, int n_tiles, cudaStream_t);
+
+struct EvalConfig {
+    int32_t precision;
+    int32_t threads, kt, s;
+    eval_launch_fn launch[2];      // [want_pot]
+    occupancy_fn occupancy[2];
+    pack_launch_fn pack;
+};
+
+template <int NT, int KT, int S, int MINB, bool POT>
+void launch_mixed(const EvalArgs &a, int grid, cudaStream_t st)
+{
+    eval_mixed_kernel<NT, KT, S, MINB, POT><<<grid, NT, 0, st>>>(a);
+}
+
+template <int NT, int KT, int S, int MINB, bool POT>
+int occupancy_mixed(int *b)
+{
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        b, eval_mixed_kernel<NT, KT, S, MINB, POT>, NT, 0);
+}
+
+template <int NT, int S, bool POT>
+void launch_f64(const EvalArgs &a, int grid, cudaStream_t st)
+{
+    eval_f64_kernel<NT, S, POT><<<grid, NT, 0, st>>>(a);
+}
+
+template <int NT, int S, bool POT>
+int occupancy_f64(int *b)
+{
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_kernel<NT, S, POT>, NT, 0);
+}
+
+template <int S, bool MIXED>
+void launch_pack(int64_t n_src, const double *pos, const double *vel, const double *mass,
+                 TileGeom *geo, void *src, int32_t *flags, int n_tiles, cudaStream_t st)
+{
+    pack_tiles_kernel<S, MIXED><<<n_tiles, S, 0, st>>>(n_src, pos, vel, mass, geo, src, flags);
+}
+
+// Defined in the per-precision translation units.
+const EvalConfig *mixed_configs(int *count);
+const EvalConfig *f64_configs(int *count);
+void launch_reduce(const EvalArgs &a, int32_t BT, bool pot, int blocks, cudaStream_t st);
+
+}  // namespace grav

@@ -1,0 +1,30 @@
+// Instantiations of the FP64 force kernel (K4) and of the split reduction (K9).
+#include "grav_eval.cuh"
+
+namespace grav {
+
+#define GRAV_F64_CFG(NT, S)                                                                   \
+    {GRAV_F64, NT, 1, S, {launch_f64<NT, S, false>, launch_f64<NT, S, true>},                 \
+     {occupancy_f64<NT, S, false>, occupancy_f64<NT, S, true>}, launch_pack<S, false>}
+
+static const EvalConfig kF64Configs[] = {
+    GRAV_F64_CFG(128, 128),
+    GRAV_F64_CFG(64, 128),
+    GRAV_F64_CFG(256, 64),
+};
+
+const EvalConfig *f64_configs(int *count)
+{
+    *count = (int)(sizeof(kF64Configs) / sizeof(kF64Configs[0]));
+    return kF64Configs;
+}
+
+void launch_reduce(const EvalArgs &a, int32_t BT, bool pot, int blocks, cudaStream_t st)
+{
+    if (pot)
+        reduce_partials_kernel<true><<<blocks, 256, 0, st>>>(a, BT);
+    else
+        reduce_partials_kernel<false><<<blocks, 256, 0, st>>>(a, BT);
+}
+
+}  // namespace grav

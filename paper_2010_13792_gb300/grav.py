@@ -1,0 +1,314 @@
+"""Python binding of libgrav's C ABI (``include/grav.h``).
+
+Argument marshalling only: every function checks dtypes, devices, shapes and
+contiguity of PyTorch CUDA tensors, passes their device pointers and the
+current CUDA stream to the library, and raises :class:`GravError` with the
+library's error text on a non-zero status.  All arithmetic of the path runs
+in libgrav's kernels.  There is no fallback: if the library is missing or was
+not built, :func:`lib` raises.
+
+Names follow the C ABI: ``select_due``, ``compact_active``, ``eval_active``,
+``predict``, ``assign_bins``, ``eval_backward``, ``measure_fma_peak``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+GRAV_OK = 0
+GRAV_EINVAL = -1
+GRAV_ECUDA = -2
+GRAV_ENONFINITE = -3
+GRAV_ETIMEOUT = -4
+GRAV_ENOMEM = -5
+
+FLAG_NONFINITE = 1
+FLAG_TIMEOUT = 2
+FLAG_BADINDEX = 4
+
+F64 = 0
+MIXED = 1
+
+_c_i64 = ctypes.c_int64
+_c_i32 = ctypes.c_int32
+_c_dbl = ctypes.c_double
+_c_ptr = ctypes.c_void_p
+
+
+class GravError(RuntimeError):
+    """A libgrav call returned a non-zero status."""
+
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: status {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("G", _c_dbl), ("h", _c_dbl), ("eta", _c_dbl), ("precision", _c_i32),
+                ("want_pot", _c_i32), ("tile_config", _c_i32), ("max_split", _c_i32)]
+
+
+class TileInfo(ctypes.Structure):
+    _fields_ = [("threads", _c_i32), ("targets_per_thread", _c_i32), ("sources_per_tile", _c_i32),
+                ("targets_per_block", _c_i32)]
+
+
+def params(*, G: float = 1.0, h: float, eta: float = 0.01, precision: int = MIXED,
+           want_pot: bool = False, tile_config: int = -1, max_split: int = 0) -> Params:
+    return Params(float(G), float(h), float(eta), int(precision), int(bool(want_pot)),
+                  int(tile_config), int(max_split))
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "grav_last_error_string": (ctypes.c_char_p, []),
+    "grav_version": (ctypes.c_char_p, []),
+    "grav_tile_config_count": (_c_i32, [_c_i32]),
+    "grav_tile_config": (ctypes.c_int, [_c_i32, _c_i32, ctypes.POINTER(TileInfo)]),
+    "grav_select_due": (ctypes.c_int, [_c_i64, _c_i64, _c_i32, _c_ptr, _c_ptr, _c_ptr, _c_dbl,
+                                       _c_dbl, _c_ptr, _c_ptr, _c_ptr, _c_ptr]),
+    "grav_compact_workspace_bytes": (_c_i64, [_c_i64]),
+    "grav_compact_active": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr]),
+    "grav_predict": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_dbl, _c_ptr,
+                                    _c_ptr]),
+    "grav_assign_bins": (ctypes.c_int, [_c_i64, _c_i64, _c_i32, _c_dbl, _c_ptr, _c_ptr, _c_ptr,
+                                        _c_ptr, _c_ptr]),
+    "grav_eval_workspace_bytes": (_c_i64, [ctypes.POINTER(Params), _c_i64, _c_i64]),
+    "grav_eval_active": (ctypes.c_int, [ctypes.POINTER(Params), _c_i64, _c_ptr, _c_ptr, _c_ptr,
+                                        _c_ptr, _c_ptr, _c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+                                        _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr]),
+    "grav_backward_workspace_bytes": (_c_i64, [ctypes.POINTER(Params), _c_i64]),
+    "grav_eval_backward": (ctypes.c_int, [ctypes.POINTER(Params), _c_i64, _c_ptr, _c_ptr, _c_ptr,
+                                          _c_dbl, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+                                          _c_ptr, _c_i64, _c_ptr]),
+    "grav_measure_fma_peak": (ctypes.c_int, [_c_i32, _c_dbl, ctypes.POINTER(_c_dbl), _c_ptr]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libgrav handle.  Raises if the library has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise GravError(GRAV_EINVAL, "libgrav",
+                            f"{path} does not exist: build it first "
+                            "(python -m paper_2010_13792_gb300.build)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def _err(where: str, rc: int):
+    if rc != GRAV_OK:
+        msg = lib().grav_last_error_string()
+        raise GravError(rc, where, msg.decode() if msg else "")
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, dtype, name, shape=None, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise GravError(GRAV_EINVAL, name, "tensor required")
+    if not isinstance(t, torch.Tensor):
+        raise GravError(GRAV_EINVAL, name, "expected a torch.Tensor")
+    if not t.is_cuda:
+        raise GravError(GRAV_EINVAL, name, "tensor must live on a CUDA device")
+    if t.dtype != dtype:
+        raise GravError(GRAV_EINVAL, name, f"dtype {t.dtype}, expected {dtype}")
+    if not t.is_contiguous():
+        raise GravError(GRAV_EINVAL, name, "tensor must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise GravError(GRAV_EINVAL, name, f"shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr()) if t.numel() else ctypes.c_void_p(0)
+
+
+def version() -> str:
+    return lib().grav_version().decode()
+
+
+def tile_configs(precision: int):
+    out = []
+    for i in range(lib().grav_tile_config_count(precision)):
+        ti = TileInfo()
+        _err("grav_tile_config", lib().grav_tile_config(precision, i, ctypes.byref(ti)))
+        out.append({"index": i, "threads": ti.threads, "targets_per_thread": ti.targets_per_thread,
+                    "sources_per_tile": ti.sources_per_tile, "targets_per_block": ti.targets_per_block})
+    return out
+
+
+class Workspace:
+    """Caller-owned device scratch (a torch uint8 buffer, 256-byte aligned)."""
+
+    def __init__(self, device=None):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes: int, device) -> torch.Tensor:
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes or self.buf.device != device:
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        return self.buf[off: off + nbytes]
+
+
+_default_ws = {}
+
+
+def _ws(ws, key, device):
+    if ws is not None:
+        return ws
+    w = _default_ws.get((key, device))
+    if w is None:
+        w = _default_ws[(key, device)] = Workspace()
+    return w
+
+
+# ---------------------------------------------------------------------------
+# Selection
+# ---------------------------------------------------------------------------
+
+
+def select_due(tick: int, k_max: int, bin_, tf_ticks, dt_grav, q_f: float, dt_min: float,
+               active_out, due_out, flags=None, stream=None):
+    n = bin_.numel()
+    rc = lib().grav_select_due(
+        n, int(tick), int(k_max), _ptr(bin_, torch.int8, "bin", (n,)),
+        _ptr(tf_ticks, torch.int64, "tf_ticks", (n,)), _ptr(dt_grav, torch.float64, "dt_grav", (n,)),
+        float(q_f), float(dt_min), _ptr(active_out, torch.uint8, "active_out", (n,)),
+        _ptr(due_out, torch.uint8, "due_out", (n,)),
+        _ptr(flags, torch.int32, "flags", (1,), allow_none=True), _stream(stream))
+    _err("grav_select_due", rc)
+
+
+def compact_workspace_bytes(n: int) -> int:
+    r = lib().grav_compact_workspace_bytes(int(n))
+    if r < 0:
+        _err("grav_compact_workspace_bytes", r)
+    return r
+
+
+def compact_active(flags_u8, idx_out, count_out, workspace: Workspace | None = None, stream=None):
+    n = flags_u8.numel()
+    dev = flags_u8.device
+    nb = compact_workspace_bytes(n)
+    buf = _ws(workspace, "compact", dev).get(nb, dev)
+    rc = lib().grav_compact_active(
+        n, _ptr(flags_u8, torch.uint8, "flags", (n,)), _ptr(idx_out, torch.int32, "idx_out", (n,)),
+        _ptr(count_out, torch.int32, "count_out", (1,)), ctypes.c_void_p(buf.data_ptr()), nb,
+        _stream(stream))
+    _err("grav_compact_active", rc)
+
+
+def predict(active, due, a_last, j_last, tf_ticks, dt_min: float, a_out, stream=None):
+    n = active.numel()
+    rc = lib().grav_predict(
+        n, _ptr(active, torch.uint8, "active", (n,)), _ptr(due, torch.uint8, "due", (n,)),
+        _ptr(a_last, torch.float64, "a_last", (n, 3)), _ptr(j_last, torch.float64, "j_last", (n, 3)),
+        _ptr(tf_ticks, torch.int64, "tf_ticks", (n,)), float(dt_min),
+        _ptr(a_out, torch.float64, "a_out", (n, 3)), _stream(stream))
+    _err("grav_predict", rc)
+
+
+def assign_bins(tick: int, k_max: int, dt_max: float, active, dt_grav, dt_hydro, bin_, stream=None):
+    n = active.numel()
+    rc = lib().grav_assign_bins(
+        n, int(tick), int(k_max), float(dt_max), _ptr(active, torch.uint8, "active", (n,)),
+        _ptr(dt_grav, torch.float64, "dt_grav", (n,)),
+        _ptr(dt_hydro, torch.float64, "dt_hydro", (n,), allow_none=True),
+        _ptr(bin_, torch.int8, "bin", (n,)), _stream(stream))
+    _err("grav_assign_bins", rc)
+
+
+# ---------------------------------------------------------------------------
+# Force evaluation
+# ---------------------------------------------------------------------------
+
+
+def eval_workspace_bytes(p: Params, n_src: int, n_idx_max: int) -> int:
+    r = lib().grav_eval_workspace_bytes(ctypes.byref(p), int(n_src), int(n_idx_max))
+    if r < 0:
+        _err("grav_eval_workspace_bytes", r)
+    return r
+
+
+def eval_active(p: Params, pos, vel, mass, idx, n_idx_dev, n_idx_max: int, acc, jerk, tidal,
+                pot=None, dt_grav=None, flags=None, workspace: Workspace | None = None,
+                stream=None):
+    """Direct-sum a, jerk, tidal tensor (and pot, dt_grav) scattered to rows idx."""
+    n = mass.numel()
+    dev = mass.device
+    nb = eval_workspace_bytes(p, n, n_idx_max)
+    buf = _ws(workspace, "eval", dev).get(nb, dev)
+    rc = lib().grav_eval_active(
+        ctypes.byref(p), n, _ptr(pos, torch.float64, "pos", (n, 3)),
+        _ptr(vel, torch.float64, "vel", (n, 3)), _ptr(mass, torch.float64, "mass", (n,)),
+        _ptr(idx, torch.int32, "idx", allow_none=True),
+        _ptr(n_idx_dev, torch.int32, "n_idx_dev", (1,), allow_none=True), int(n_idx_max),
+        _ptr(acc, torch.float64, "acc", (n, 3)), _ptr(jerk, torch.float64, "jerk", (n, 3)),
+        _ptr(tidal, torch.float64, "tidal", (n, 6)),
+        _ptr(pot, torch.float64, "pot", (n,), allow_none=True),
+        _ptr(dt_grav, torch.float64, "dt_grav", (n,), allow_none=True),
+        _ptr(flags, torch.int32, "flags", (1,), allow_none=True),
+        ctypes.c_void_p(buf.data_ptr()), nb, _stream(stream))
+    _err("grav_eval_active", rc)
+
+
+def backward_workspace_bytes(p: Params, n: int) -> int:
+    r = lib().grav_backward_workspace_bytes(ctypes.byref(p), int(n))
+    if r < 0:
+        _err("grav_backward_workspace_bytes", r)
+    return r
+
+
+def eval_backward(p: Params, pos, mass, a_bar, w_bar: float, acc, tidal, pot, pos_bar, mass_bar,
+                  flags=None, workspace: Workspace | None = None, stream=None):
+    n = mass.numel()
+    dev = mass.device
+    nb = backward_workspace_bytes(p, n)
+    buf = _ws(workspace, "backward", dev).get(nb, dev)
+    rc = lib().grav_eval_backward(
+        ctypes.byref(p), n, _ptr(pos, torch.float64, "pos", (n, 3)),
+        _ptr(mass, torch.float64, "mass", (n,)),
+        _ptr(a_bar, torch.float64, "a_bar", (n, 3), allow_none=True), float(w_bar),
+        _ptr(acc, torch.float64, "acc", (n, 3), allow_none=True),
+        _ptr(tidal, torch.float64, "tidal", (n, 6), allow_none=True),
+        _ptr(pot, torch.float64, "pot", (n,), allow_none=True),
+        _ptr(pos_bar, torch.float64, "pos_bar", (n, 3)),
+        _ptr(mass_bar, torch.float64, "mass_bar", (n,)),
+        _ptr(flags, torch.int32, "flags", (1,), allow_none=True),
+        ctypes.c_void_p(buf.data_ptr()), nb, _stream(stream))
+    _err("grav_eval_backward", rc)
+
+
+def measure_fma_peak(precision: int, seconds: float = 0.5, stream=None) -> float:
+    out = ctypes.c_double()
+    rc = lib().grav_measure_fma_peak(int(precision), float(seconds), ctypes.byref(out),
+                                     _stream(stream))
+    _err("grav_measure_fma_peak", rc)
+    return out.value

@@ -1,0 +1,214 @@
+"""GPU force evaluation against the FP64 oracle, element by element.
+
+FP64 path: <= 1e-12 relative per target on a, j, T and Phi.  Mixed path:
+median <= 1e-5 and max <= 1e-4 relative on |a|, max <= 1e-4 on j, T, Phi.
+Cases: the uniform sphere of N = 4096 (all active), ragged sizes spanning
+several tiles with a partial last tile and last target block, every tile
+configuration, the source-split path (few targets), device-resident counts,
+degenerate inputs (one element, two bodies, coincident elements, everything
+softened), device flags, and full-size Plummer and turbulent-cloud inputs
+compared on sampled targets.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2010_13792_gb300 import grav, ics
+
+from gpu_util import (DEV, T, assert_f64, assert_mixed, errors, run_eval)  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sphere4096():
+    pos, vel, mass = ics.uniform_sphere(4096, seed=ics.BASE_SEED + 0)
+    ref = O.eval_active(pos, vel, mass, h=0.01)
+    return pos, vel, mass, ref
+
+
+def test_f64_uniform_sphere_4096(sphere4096):
+    pos, vel, mass, ref = sphere4096
+    out = run_eval(pos, vel, mass, None, h=0.01, precision=grav.F64)
+    e = errors(out, ref, np.arange(4096))
+    assert_f64(e)
+    assert np.allclose(out["dt_grav"], ref["dt_grav"], rtol=1e-12, atol=0)
+
+
+def test_mixed_uniform_sphere_4096(sphere4096):
+    pos, vel, mass, ref = sphere4096
+    out = run_eval(pos, vel, mass, None, h=0.01, precision=grav.MIXED)
+    e = errors(out, ref, np.arange(4096))
+    assert_mixed(e)
+
+
+@pytest.mark.parametrize("cfg", range(5))
+def test_mixed_tile_configs(cfg):
+    n = 2500
+    pos, vel, mass = ics.plummer(n, seed=11)
+    idx = ics.active_subset(n, 0.37, 12)
+    ref = O.eval_active(pos, vel, mass, idx, h=0.02)
+    out = run_eval(pos, vel, mass, idx, h=0.02, precision=grav.MIXED, tile_config=cfg)
+    assert_mixed(errors(out, ref, idx))
+
+
+@pytest.mark.parametrize("cfg", range(3))
+def test_f64_tile_configs(cfg):
+    n = 1777
+    pos, vel, mass = ics.uniform_sphere(n, seed=13)
+    idx = ics.active_subset(n, 0.6, 14)
+    ref = O.eval_active(pos, vel, mass, idx, h=0.05)
+    out = run_eval(pos, vel, mass, idx, h=0.05, precision=grav.F64, tile_config=cfg)
+    assert_f64(errors(out, ref, idx))
+
+
+@pytest.mark.parametrize("precision", [grav.F64, grav.MIXED])
+@pytest.mark.parametrize("max_split", [0, 1, 3])
+def test_split_path(precision, max_split):
+    """Few targets against many sources: the sources are split into chunks
+    (unless max_split = 1) and the partials reduced in a fixed order."""
+    n = 30000
+    pos, vel, mass = ics.plummer(n, seed=15)
+    idx = ics.active_subset(n, 0.002, 16)
+    ref = O.eval_active(pos, vel, mass, idx, h=0.01)
+    out = run_eval(pos, vel, mass, idx, h=0.01, precision=precision, max_split=max_split)
+    e = errors(out, ref, idx)
+    (assert_f64 if precision == grav.F64 else assert_mixed)(e)
+
+
+@pytest.mark.parametrize("precision", [grav.F64, grav.MIXED])
+def test_rows_of_non_targets_untouched_and_host_count(precision):
+    n = 3001
+    pos, vel, mass = ics.uniform_sphere(n, seed=17)
+    idx = ics.active_subset(n, 0.1, 18)
+    a = run_eval(pos, vel, mass, idx, h=0.03, precision=precision, device_count=True)
+    b = run_eval(pos, vel, mass, idx, h=0.03, precision=precision, device_count=False)
+    others = np.setdiff1d(np.arange(n), idx)
+    for k in ("acc", "jerk", "tidal", "pot", "dt_grav"):
+        assert np.all(np.isnan(a[k][others]))
+        assert np.array_equal(a[k][idx], b[k][idx])       # deterministic
+
+
+@pytest.mark.parametrize("precision", [grav.F64, grav.MIXED])
+def test_deterministic(precision):
+    n = 20000
+    pos, vel, mass = ics.plummer(n, seed=19)
+    idx = ics.active_subset(n, 0.01, 20)
+    a = run_eval(pos, vel, mass, idx, h=0.01, precision=precision)
+    b = run_eval(pos, vel, mass, idx, h=0.01, precision=precision)
+    for k in ("acc", "jerk", "tidal"):
+        assert np.array_equal(a[k][idx], b[k][idx])
+
+
+@pytest.mark.parametrize("precision", [grav.F64, grav.MIXED])
+def test_degenerate_inputs(precision):
+    tol = 1e-12 if precision == grav.F64 else 1e-5
+    # one element: nothing to sum, T = 0 and dt_grav = +inf
+    out = run_eval(np.zeros((1, 3)), np.zeros((1, 3)), np.ones(1), None, h=0.1, precision=precision)
+    assert np.all(out["acc"] == 0) and np.all(out["tidal"] == 0)
+    assert np.isinf(out["dt_grav"][0])
+    # two bodies beyond h, and within h
+    for sep in (0.5, 0.03):
+        pos = np.array([[0.1, 0.2, 0.3], [0.1 + sep, 0.2, 0.3]])
+        vel = np.array([[0.0, 0.1, 0.0], [0.2, 0.0, 0.1]])
+        mass = np.array([0.7, 1.3])
+        ref = O.eval_active(pos, vel, mass, h=0.1)
+        out = run_eval(pos, vel, mass, None, h=0.1, precision=precision)
+        for k in ("acc", "jerk", "tidal", "pot"):
+            assert np.allclose(out[k], ref[k], rtol=tol, atol=tol * np.abs(ref[k]).max())
+    # coincident distinct elements and everything inside one softening length
+    g = ics.rng(21)
+    pos = g.normal(0, 0.01, (300, 3))
+    pos[1] = pos[0]
+    pos[7] = pos[3]
+    vel = g.normal(0, 1, (300, 3))
+    mass = g.uniform(0.5, 1.5, 300)
+    ref = O.eval_active(pos, vel, mass, h=0.5)
+    out = run_eval(pos, vel, mass, None, h=0.5, precision=precision)
+    e = errors(out, ref, np.arange(300))
+    if precision == grav.F64:
+        assert_f64(e)
+    else:
+        assert_mixed(e)
+
+
+def test_flags_nonfinite_and_bad_index():
+    n = 600
+    pos, vel, mass = ics.uniform_sphere(n, seed=23)
+    pos[17, 1] = np.nan
+    flags = torch.zeros(1, dtype=torch.int32, device=DEV)
+    run_eval(pos, vel, mass, None, h=0.05, precision=grav.MIXED, flags=flags)
+    assert int(flags.item()) & grav.FLAG_NONFINITE
+    pos[17, 1] = 0.0
+    idx = np.array([3, 5, n + 10, 7, -2], np.int32)
+    flags.zero_()
+    out = run_eval(pos, vel, mass, idx, h=0.05, precision=grav.F64, flags=flags)
+    assert int(flags.item()) & grav.FLAG_BADINDEX
+    ref = O.eval_active(pos, vel, mass, np.array([3, 5, 7], np.int32), h=0.05)
+    assert_f64(errors(out, ref, np.array([3, 5, 7])))
+
+
+def test_zero_targets_device_count():
+    n = 1000
+    pos, vel, mass = ics.uniform_sphere(n, seed=24)
+    idx = np.zeros(0, np.int32)
+    p = grav.params(h=0.05, precision=grav.MIXED, want_pot=False)
+    acc = torch.full((n, 3), 3.0, dtype=torch.float64, device=DEV)
+    jerk = acc.clone()
+    tid = torch.full((n, 6), 3.0, dtype=torch.float64, device=DEV)
+    it = torch.zeros(n, dtype=torch.int32, device=DEV)
+    cnt = torch.zeros(1, dtype=torch.int32, device=DEV)
+    grav.eval_active(p, T(pos), T(vel), T(mass), it, cnt, n, acc, jerk, tid)
+    torch.cuda.synchronize()
+    assert torch.all(acc == 3.0) and torch.all(tid == 3.0)
+    del idx
+
+
+# ---- full-size inputs, sampled targets ------------------------------------
+
+
+@pytest.fixture(scope="module")
+def plummer_2e17():
+    return ics.plummer(1 << 17, seed=ics.BASE_SEED + 1)
+
+
+@pytest.fixture(scope="module")
+def cloud_2e20():
+    return ics.turbulent_cloud(1 << 20, seed=ics.BASE_SEED + 2)
+
+
+def _sample(n, k, seed):
+    return np.sort(ics.rng(seed).choice(n, size=k, replace=False)).astype(np.int32)
+
+
+@pytest.mark.parametrize("precision", [grav.F64, grav.MIXED])
+def test_plummer_2e17_all_active_sampled(plummer_2e17, precision):
+    pos, vel, mass = plummer_2e17
+    n = mass.size
+    out = run_eval(pos, vel, mass, None, h=1e-3, precision=precision)
+    rows = _sample(n, 192, 31)
+    ref = O.eval_active(pos, vel, mass, rows, h=1e-3)
+    e = errors(out, ref, rows)
+    (assert_f64 if precision == grav.F64 else assert_mixed)(e)
+
+
+@pytest.mark.parametrize("fraction", [0.01, 0.1, 1.0])
+def test_cloud_2e20_mixed_sampled(cloud_2e20, fraction):
+    pos, vel, mass = cloud_2e20
+    n = mass.size
+    idx = ics.active_subset(n, fraction, 40 + int(fraction * 100))
+    out = run_eval(pos, vel, mass, idx, h=2e-3, precision=grav.MIXED)
+    rows = np.sort(ics.rng(41).choice(idx, size=160, replace=False)).astype(np.int32)
+    ref = O.eval_active(pos, vel, mass, rows, h=2e-3)
+    assert_mixed(errors(out, ref, rows))
+
+
+def test_cloud_2e20_f64_sampled(cloud_2e20):
+    pos, vel, mass = cloud_2e20
+    n = mass.size
+    idx = ics.active_subset(n, 0.01, 41)
+    out = run_eval(pos, vel, mass, idx, h=2e-3, precision=grav.F64)
+    rows = np.sort(ics.rng(42).choice(idx, size=96, replace=False)).astype(np.int32)
+    ref = O.eval_active(pos, vel, mass, rows, h=2e-3)
+    assert_f64(errors(out, ref, rows))
