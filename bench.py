@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--fraction", type=float, default=1.0)
     ap.add_argument("--tile-config", type=int, default=-1)
-    ap.add_argument("--no-extras", action="store_true", help="headline only (no sweeps, FP64, CPU)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline steps only (no sweeps, FP64 path, e2e, CPU baseline)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -303,8 +304,6 @@ def run_ours(args, rank, local, ws):
         result["extras"] = extras(args, path, dev, sms, peak32, flush)
         result["e2e"] = e2e(args, path, dev, flush)
         result["cpu_baseline"] = cpu_baseline(path, args.cpu_seconds)
-    elif rank == 0:
-        result["e2e"] = e2e(args, path, dev, flush)
     return result
 
 

@@ -339,14 +339,20 @@ int oracle_assign_bins(int64_t n, int64_t tick, int32_t k_max, double dt_max,
  */
 int oracle_backward(int64_t n, const double *pos, const double *mass, const double *a_bar,
                     double w_bar, const double *acc, const double *tidal, const double *pot,
-                    double G, double h, double *pos_bar, double *mass_bar, int nthreads)
+                    double G, double h, int64_t n_sel, const int32_t *sel, double *pos_bar,
+                    double *mass_bar, int nthreads)
 {
+    /* sel (nullable): compute only rows k = sel[0..n_sel) (outputs still
+     * indexed by k); NULL means every k in [0, n). */
     if (n < 0 || !(h > 0.0)) return -1;
     if (w_bar != 0.0 && (!acc || !pot)) return -1;
     if (a_bar && !tidal) return -1;
+    if (!sel) n_sel = n;
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t k = 0; k < n; ++k) {
+    for (int64_t s = 0; s < n_sel; ++s) {
+        int64_t k = sel ? (int64_t)sel[s] : s;
+        if (k < 0 || k >= n) continue;
         nsum xb[3], mb;
         memset(xb, 0, sizeof xb);
         memset(&mb, 0, sizeof mb);

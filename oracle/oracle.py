@@ -76,8 +76,8 @@ def load(path: str | None = None):
                                            ctypes.c_double, _u8p, _dp, _dp, _i8p]
         lib.oracle_assign_bins.restype = ctypes.c_int
         lib.oracle_backward.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double, _dp, _dp,
-                                        _dp, ctypes.c_double, ctypes.c_double, _dp, _dp,
-                                        ctypes.c_int]
+                                        _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                        _i32p, _dp, _dp, ctypes.c_int]
         lib.oracle_backward.restype = ctypes.c_int
         if path is None:
             _lib = lib
@@ -198,8 +198,9 @@ def assign_bins(tick, k_max, dt_max, active, dt_grav, dt_hydro, bin_, lib=None):
 
 
 def backward(pos, mass, a_bar, w_bar, acc, tidal, pot, *, G=1.0, h, nthreads: int = 0,
-             lib=None):
-    """Adjoint sums: returns (pos_bar [n,3], mass_bar [n])."""
+             lib=None, rows=None):
+    """Adjoint sums: returns (pos_bar [n,3], mass_bar [n]); with `rows` only
+    those rows are computed (the others are 0)."""
     pos = _c(pos, np.float64)
     mass = _c(mass, np.float64)
     n = mass.shape[0]
@@ -209,8 +210,10 @@ def backward(pos, mass, a_bar, w_bar, acc, tidal, pot, *, G=1.0, h, nthreads: in
     pot = None if pot is None else _c(pot, np.float64)
     pb = np.zeros((n, 3))
     mb = np.zeros(n)
+    sel = None if rows is None else _c(rows, np.int32)
     rc = (lib or load()).oracle_backward(n, _p(pos, _dp), _p(mass, _dp), _p(a_bar, _dp), float(w_bar),
                                 _p(acc, _dp), _p(tidal, _dp), _p(pot, _dp), float(G), float(h),
+                                0 if sel is None else sel.size, _p(sel, _i32p),
                                 _p(pb, _dp), _p(mb, _dp), int(nthreads))
     if rc != 0:
         raise ValueError("oracle_backward: bad arguments")
