@@ -129,6 +129,30 @@ GRAV_API int grav_compact_active(int64_t n, const uint8_t *flags, int32_t *idx_o
                         void *workspace, int64_t workspace_bytes, void *stream);
 
 /*
+ * grav_compact_active_noalloc -- the same compaction as grav_compact_active
+ * (identical output) for callers that cannot allocate device memory, so
+ * cannot provide a workspace: for example a host code that has reserved the
+ * whole device memory pool for itself, or a time-step loop that must not
+ * stall on cudaMalloc's implicit device synchronisation.  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ *  - Allocates nothing: its scratch (one int32 per block of 4096 flags) is a
+ *    fixed array inside the library, present on every device that loads the
+ *    library until the process exits (64 KiB per device).
+ *  - n is limited to GRAV_COMPACT_NOALLOC_MAX_N (2^26); larger n returns
+ *    GRAV_EINVAL before anything is launched.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls share the array.  Each call writes every scratch element it
+ *    reads, so nothing needs clearing between calls, but calls whose kernels
+ *    overlap on the GPU (other streams, other threads) race on it: serialise
+ *    them.
+ */
+#define GRAV_COMPACT_NOALLOC_MAX_N 67108864
+GRAV_API int grav_compact_active_noalloc(int64_t n, const uint8_t *flags, int32_t *idx_out,
+                                         int32_t *count_dev, void *stream);
+
+/*
  * grav_predict -- the first-order jerk predictor, Eq. (jerkupdate), in closed
  * form: for active, not-due elements
  *     a_out[i] = a_last[i] + j_last[i] * (tf_ticks[i] * dt_min)

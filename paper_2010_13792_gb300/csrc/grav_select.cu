@@ -7,6 +7,8 @@
 // point step that decides an integer (due, bin) is a single correctly rounded
 // operation written as an explicit intrinsic, so results are bit-identical to
 // any IEEE implementation of the same definition.
+#include <mutex>
+
 #include "grav_common.cuh"
 
 namespace grav {
@@ -337,4 +339,78 @@ extern "C" int grav_assign_bins(int64_t n, int64_t tick, int32_t k_max, double d
     assign_bins_kernel<<<elem_blocks(n), kElemThreads, 0, as_stream(stream)>>>(
         n, k_align, k_max, dt_max, active, dt_grav, dt_hydro, bin);
     return check_launch("grav_assign_bins");
+}
+
+// ---------------------------------------------------------------------------
+// Compaction for callers that cannot allocate device memory.
+//
+// Some callers cannot hand us a workspace: a host framework that reserved the
+// whole device memory pool for itself, a time-step loop that must not stall
+// on cudaMalloc's implicit device synchronisation, or code recording work in
+// a mode where allocation is forbidden.  This entry point keeps its scratch
+// (one int32 per block of 4096 flags) in a fixed array inside the library.
+// The array lives on every device that loads the library until the process
+// exits, is shared by all calls, and keeps whatever the last call left in it;
+// every element a call reads is written by that same call first, so nothing
+// has to be cleared.  Calls whose kernels overlap on the GPU race on it.
+// ---------------------------------------------------------------------------
+
+namespace grav {
+namespace {
+
+constexpr int64_t kNoAllocMaxBlocks = 1 << 14;
+constexpr int64_t kNoAllocMaxN = kNoAllocMaxBlocks * kPerBlock;   // 2^26 flags
+static_assert(kNoAllocMaxN == GRAV_COMPACT_NOALLOC_MAX_N, "limit of the header");
+
+static __device__ __align__(256) int32_t g_noalloc_block_counts[kNoAllocMaxBlocks];
+
+// Device address of the array on the current device, looked up once per
+// device (host code may not use the array's name as a device pointer).
+int noalloc_scratch(int32_t **out)
+{
+    static std::mutex mu;
+    static int32_t *addr[64] = {nullptr};
+    int dev = 0;
+    int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    if (dev < 0 || dev >= 64) return fail(GRAV_ECUDA, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        rc = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_block_counts),
+                        "cudaGetSymbolAddress(g_noalloc_block_counts)");
+        if (rc) return rc;
+        addr[dev] = static_cast<int32_t *>(p);
+    }
+    *out = addr[dev];
+    return GRAV_OK;
+}
+
+}  // namespace
+}  // namespace grav
+
+extern "C" int grav_compact_active_noalloc(int64_t n, const uint8_t *flags, int32_t *idx_out,
+                                           int32_t *count_dev, void *stream)
+{
+    static const char *who = "grav_compact_active_noalloc";
+    if (n < 0 || n > kNoAllocMaxN)
+        return fail(GRAV_EINVAL, "%s: n = %lld outside [0, %lld] (the fixed scratch holds %lld blocks)",
+                    who, (long long)n, (long long)kNoAllocMaxN, (long long)kNoAllocMaxBlocks);
+    if (!count_dev) return fail(GRAV_EINVAL, "%s: null count_dev", who);
+    cudaStream_t s = as_stream(stream);
+    if (n == 0) return check_cuda(cudaMemsetAsync(count_dev, 0, sizeof(int32_t), s), who);
+    if (!flags || !idx_out) return fail(GRAV_EINVAL, "%s: null array", who);
+    int32_t *counts = nullptr;
+    int rc = noalloc_scratch(&counts);
+    if (rc) return rc;
+    const int64_t nb = (n + kPerBlock - 1) / kPerBlock;
+    const bool vec_ok = aligned(flags, 16);
+    compact_count_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(n, flags, vec_ok, counts);
+    rc = check_launch("grav_compact_active_noalloc/count");
+    if (rc) return rc;
+    compact_scan_kernel<<<1, kTopThreads, 0, s>>>(nb, counts, count_dev);
+    rc = check_launch("grav_compact_active_noalloc/scan");
+    if (rc) return rc;
+    compact_scatter_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(n, flags, vec_ok, counts, idx_out);
+    return check_launch("grav_compact_active_noalloc/scatter");
 }

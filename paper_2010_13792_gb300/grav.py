@@ -76,6 +76,7 @@ _SIGS = {
                                        _c_dbl, _c_ptr, _c_ptr, _c_ptr, _c_ptr]),
     "grav_compact_workspace_bytes": (_c_i64, [_c_i64]),
     "grav_compact_active": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr]),
+    "grav_compact_active_noalloc": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr]),
     "grav_predict": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_dbl, _c_ptr,
                                     _c_ptr]),
     "grav_assign_bins": (ctypes.c_int, [_c_i64, _c_i64, _c_i32, _c_dbl, _c_ptr, _c_ptr, _c_ptr,
@@ -223,6 +224,21 @@ def compact_active(flags_u8, idx_out, count_out, workspace: Workspace | None = N
         _ptr(count_out, torch.int32, "count_out", (1,)), ctypes.c_void_p(buf.data_ptr()), nb,
         _stream(stream))
     _err("grav_compact_active", rc)
+
+
+COMPACT_NOALLOC_MAX_N = 1 << 26
+
+
+def compact_active_noalloc(flags_u8, idx_out, count_out, stream=None):
+    """compact_active without a workspace (library-resident scratch; n <= 2^26).
+    For callers that cannot allocate device memory.  Calls that overlap on the
+    GPU share the scratch and race; make the first call on a device before
+    any stream capture."""
+    n = flags_u8.numel()
+    rc = lib().grav_compact_active_noalloc(
+        n, _ptr(flags_u8, torch.uint8, "flags", (n,)), _ptr(idx_out, torch.int32, "idx_out", (n,)),
+        _ptr(count_out, torch.int32, "count_out", (1,)), _stream(stream))
+    _err("grav_compact_active_noalloc", rc)
 
 
 def predict(active, due, a_last, j_last, tf_ticks, dt_min: float, a_out, stream=None):
