@@ -229,9 +229,9 @@ backward_kernel(const BwdArgs a)
 #pragma unroll
                 for (int c = 0; c < kNB; ++c) acc[q][c] = T(0);
             if (!near)
-                bwd_loop<T, KT, S, false>(stage[s], stage[s] + S, tx, tk, (int64_t)t * S, h2, hinv, acc);
+                bwd_loop<T, KT, S, false>(stage[s], stage[s] + S, tx, tk, g.first, h2, hinv, acc);
             else
-                bwd_loop<T, KT, S, true>(stage[s], stage[s] + S, tx, tk, (int64_t)t * S, h2, hinv, acc);
+                bwd_loop<T, KT, S, true>(stage[s], stage[s] + S, tx, tk, g.first, h2, hinv, acc);
 #pragma unroll
             for (int q = 0; q < KT; ++q)
 #pragma unroll
@@ -451,10 +451,10 @@ extern "C" int grav_eval_backward(const grav_params *p, int64_t n, const double 
     // Pack (x, a_bar) tiles: the forward packer with a_bar in the velocity
     // slot and no mass.
     if (mixed)
-        pack_tiles_kernel<kBwdSf, true><<<(unsigned)L.n_tiles, kBwdSf, 0, st>>>(
+        pack_tiles_kernel<kBwdSf, true, false><<<(unsigned)L.n_tiles, kBwdSf, 0, st>>>(
             n, pos, a_bar, nullptr, const_cast<TileGeom *>(a.geo), const_cast<void *>(a.src), flags_dev);
     else
-        pack_tiles_kernel<kBwdSd, false><<<(unsigned)L.n_tiles, kBwdSd, 0, st>>>(
+        pack_tiles_kernel<kBwdSd, false, false><<<(unsigned)L.n_tiles, kBwdSd, 0, st>>>(
             n, pos, a_bar, nullptr, const_cast<TileGeom *>(a.geo), const_cast<void *>(a.src), flags_dev);
     rc = check_launch("grav_eval_backward/pack");
     if (rc) return rc;

@@ -1,28 +1,39 @@
 // Force evaluation kernels of libgrav (Grudic 2020, Eq. 4 and Section 3).
 //
 // Direct summation, target-blocked: a CTA owns a block of BT = NT*KT targets
-// (KT per thread, in registers) and streams source tiles of S elements through
-// shared memory with 1-D TMA bulk copies (cp.async.bulk + mbarrier, double
+// (KT per thread) and streams source tiles of S elements through shared
+// memory with 1-D TMA bulk copies (cp.async.bulk + mbarrier, double
 // buffered).  Every thread evaluates each staged source against its KT
 // targets with the SFU reciprocal square root; all lanes read the same source
 // (shared-memory broadcast).  This is CUDA-core work, not a contraction: no
 // tensor cores.
 //
-// Per pair the kernel accumulates, with d = x_j - x_i and v = v_j - v_i,
-//   A  += m f d          J1 += m f v         J2 += m g' (d.v) d
-//   F  += m f            Tp += m g' d d^T    P  += m phi   (optional)
-// where g' = -g/3 (= r^-5 beyond the softening).  The epilogue forms
+// Accumulated sums per target (d = x_j - x_i, g' = -g/3 = r^-5 beyond h):
+//   A  = sum m f d          Tp = sum m g' d d^T       P = sum m phi (optional)
+//   J1 = sum m f v          J2 = sum m g' (d.v) d
+// and the trace term F = sum m f.  The epilogue forms
 //   a = G A,  j = G (J1 - 3 J2),  T = -G (F I - 3 Tp),  Phi = -G P,
 // and the tidal timestep of Eq. (tidaltimestep) in FP64.
+//
+// Mixed precision (K5): positions are FP64; each source tile stores FP32
+// offsets from its FP64 bounding-box centre and FP32 velocities relative to
+// its velocity centre; each target's offset to the tile centre is formed in
+// FP64 and rounded once.  Two identities keep the pair body at 31 FP32
+// instructions + 1 MUFU:
+//   * beyond h, m f = m r^-3 = m r^-5 r^2, so F = trace(Tp) + E with
+//     E = sum (m f - m g' r^2) over softened pairs only;
+//   * v = v_j' - v_i' (both relative to the tile's velocity centre), so the
+//     per-tile sums J1 = sum m f v_j' - v_i' F_tile and
+//     J2 = sum m g' (d.v_j') d - Tp_tile v_i' take the target velocity out of
+//     the pair loop.
+// Per-tile sums are FP32; they are carried across tiles as compensated FP32
+// pairs (TwoSum), in registers or in shared memory, and the final per-target
+// result is FP64.  The FP64 path (K4) accumulates the plain sums in FP64.
 //
 // Tiles whose bounding box lies at least h from the target block's bounding
 // box take the Newtonian loop (exact there: the cubic spline has compact
 // support); the others take the softened loop, which also excludes the self
-// pair by index.  Mixed precision: positions are FP64; each source tile stores
-// FP32 offsets from its FP64 bounding-box centre, each target's offset to that
-// centre is formed in FP64 and rounded once, pair arithmetic and per-tile sums
-// are FP32, tile sums are carried across tiles as compensated FP32 pairs
-// (TwoSum) and the final per-target result is FP64.
+// pair by index.
 //
 // Work items are (target block, source chunk).  A fixed grid of CTAs takes
 // items round-robin; when the target set is small the sources are split into
@@ -38,15 +49,15 @@ constexpr int kNC = 16;            // accumulators without the potential
 constexpr int kNCPot = 17;         // with the potential
 constexpr int kDefaultMaxSplit = 64;
 
-// Accumulator slots.
-enum { A0 = 0, J10 = 3, J20 = 6, FSUM = 9, TXX = 10, TYY, TZZ, TXY, TXZ, TYZ, PSUM = 16 };
+// Accumulator slots.  Slot 9 holds F (FP64 path) or E (mixed path).
+enum { A0 = 0, J10 = 3, J20 = 6, FSUM = 9, ESUM = 9, TXX = 10, TYY, TZZ, TXY, TXZ, TYZ, PSUM = 16 };
 
 struct __align__(16) TileGeom {
-    double c[3];    // FP64 bounding-box centre (offset origin of the mixed path)
+    double c[3];    // FP64 bounding-box centre of the positions (offset origin, mixed path)
     float lo[3];    // bounding box, rounded outward to FP32
     float hi[3];
-    int32_t count;  // real sources in the tile
-    int32_t pad[3];
+    int32_t first;  // element index of the tile's first source
+    float cv[3];    // velocity centre (mixed path; 0 when velocities are stored as they are)
 };
 static_assert(sizeof(TileGeom) == 64, "TileGeom layout");
 
@@ -111,15 +122,17 @@ __device__ __forceinline__ int64_t active_count(const EvalArgs &a)
     return n;
 }
 
-// Final FP64 outputs of one target from its accumulated sums.
-template <bool POT>
+// Final FP64 outputs of one target from its accumulated sums.  ETRACE: slot 9
+// holds E and F = E + trace(Tp) (mixed path); otherwise slot 9 holds F.
+template <bool POT, bool ETRACE>
 __device__ __forceinline__ void write_target(const EvalArgs &a, int64_t i, const double s[kNCPot])
 {
     const double G = a.G;
+    const double F = ETRACE ? s[ESUM] + (s[TXX] + s[TYY] + s[TZZ]) : s[FSUM];
     double t6[6];
-    t6[0] = -G * (s[FSUM] - 3.0 * s[TXX]);
-    t6[1] = -G * (s[FSUM] - 3.0 * s[TYY]);
-    t6[2] = -G * (s[FSUM] - 3.0 * s[TZZ]);
+    t6[0] = -G * (F - 3.0 * s[TXX]);
+    t6[1] = -G * (F - 3.0 * s[TYY]);
+    t6[2] = -G * (F - 3.0 * s[TZZ]);
     t6[3] = 3.0 * G * s[TXY];
     t6[4] = 3.0 * G * s[TXZ];
     t6[5] = 3.0 * G * s[TYZ];
@@ -214,16 +227,18 @@ __device__ __forceinline__ void block_minmax_d(double lo[3], double hi[3], doubl
     __syncthreads();
 }
 
-// One CTA of S threads per tile.  MIXED: tile = [S x float4 (offset, m)]
-// [S x float4 (v, 0)]; F64: tile = [S x D4 (x, m)][S x D4 (v, 0)].  Padding
-// sources have zero mass and sit far away, so they contribute exactly 0.
-template <int S, bool MIXED>
+// One CTA of S threads per tile; tile t holds sources [first, first + count)
+// with first = t*S.  MIXED: tile = [S x float4 (offset, m)][S x float4 (v', 0)]
+// (v' = v - cv when VOFF, else v); F64: tile = [S x D4 (x, m)][S x D4 (v, 0)].
+// Padding sources have zero mass and sit far away, so they contribute exactly
+// 0.  `mass` may be NULL (zero masses: the adjoint packs a_bar as "velocity").
+template <int S, bool MIXED, bool VOFF>
 __global__ void __launch_bounds__(S)
 pack_tiles_kernel(int64_t n_src, const double *__restrict__ pos, const double *__restrict__ vel,
                   const double *__restrict__ mass, TileGeom *__restrict__ geo, void *__restrict__ src,
                   int32_t *flags)
 {
-    __shared__ double slo[3], shi[3];
+    __shared__ double slo[3], shi[3], svlo[3], svhi[3];
     const int t = blockIdx.x, j = threadIdx.x;
     const int64_t gj = (int64_t)t * S + j;
     const bool ok = gj < n_src;
@@ -246,6 +261,17 @@ pack_tiles_kernel(int64_t n_src, const double *__restrict__ pos, const double *_
         hi[c] = ok ? x[c] : -inf;
     }
     block_minmax_d<S>(lo, hi, slo, shi);
+    float cvf[3] = {0.0f, 0.0f, 0.0f};
+    if (VOFF) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = ok ? v[c] : inf;
+            hi[c] = ok ? v[c] : -inf;
+        }
+        block_minmax_d<S>(lo, hi, svlo, svhi);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cvf[c] = __double2float_rn(__dmul_rn(0.5, __dadd_rn(svlo[c], svhi[c])));
+    }
     double cc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) cc[c] = __dmul_rn(0.5, __dadd_rn(slo[c], shi[c]));
@@ -256,8 +282,9 @@ pack_tiles_kernel(int64_t n_src, const double *__restrict__ pos, const double *_
             pm = make_float4(__double2float_rn(__dsub_rn(x[0], cc[0])),
                              __double2float_rn(__dsub_rn(x[1], cc[1])),
                              __double2float_rn(__dsub_rn(x[2], cc[2])), __double2float_rn(m));
-            pv = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]),
-                             __double2float_rn(v[2]), 0.0f);
+            pv = make_float4(__double2float_rn(__dsub_rn(v[0], (double)cvf[0])),
+                             __double2float_rn(__dsub_rn(v[1], (double)cvf[1])),
+                             __double2float_rn(__dsub_rn(v[2], (double)cvf[2])), 0.0f);
         } else {
             pm = make_float4(1.0e18f, 0.0f, 0.0f, 0.0f);
             pv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -284,10 +311,9 @@ pack_tiles_kernel(int64_t n_src, const double *__restrict__ pos, const double *_
             g.c[c] = cc[c];
             g.lo[c] = __double2float_rd(slo[c]);
             g.hi[c] = __double2float_ru(shi[c]);
+            g.cv[c] = cvf[c];
         }
-        int64_t cnt = n_src - (int64_t)t * S;
-        g.count = (int32_t)(cnt < S ? cnt : S);
-        g.pad[0] = g.pad[1] = g.pad[2] = 0;
+        g.first = t * S;
         geo[t] = g;
     }
 }
@@ -321,19 +347,20 @@ __device__ __forceinline__ void spline_kernel(T u, T &F, T &Gp, T &P)
 // Pair loops, mixed precision
 // ---------------------------------------------------------------------------
 
+// Sums of one pair (target q): A, J1', J2', Tp (and P).  v' is the source
+// velocity relative to the tile's velocity centre.
 template <int KT, bool POT>
 __device__ __forceinline__ void accumulate_f(float acc[KT][kNCPot], int q, float dx, float dy,
-                                             float dz, float ux, float uy, float uz, float mf,
+                                             float dz, float vx, float vy, float vz, float mf,
                                              float mg, float mp)
 {
     acc[q][A0 + 0] = fmaf(mf, dx, acc[q][A0 + 0]);
     acc[q][A0 + 1] = fmaf(mf, dy, acc[q][A0 + 1]);
     acc[q][A0 + 2] = fmaf(mf, dz, acc[q][A0 + 2]);
-    acc[q][FSUM] += mf;
-    float dv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-    acc[q][J10 + 0] = fmaf(mf, ux, acc[q][J10 + 0]);
-    acc[q][J10 + 1] = fmaf(mf, uy, acc[q][J10 + 1]);
-    acc[q][J10 + 2] = fmaf(mf, uz, acc[q][J10 + 2]);
+    acc[q][J10 + 0] = fmaf(mf, vx, acc[q][J10 + 0]);
+    acc[q][J10 + 1] = fmaf(mf, vy, acc[q][J10 + 1]);
+    acc[q][J10 + 2] = fmaf(mf, vz, acc[q][J10 + 2]);
+    float dv = fmaf(dx, vx, fmaf(dy, vy, dz * vz));
     float gx = mg * dx, gy = mg * dy, gz = mg * dz;
     acc[q][TXX] = fmaf(gx, dx, acc[q][TXX]);
     acc[q][TYY] = fmaf(gy, dy, acc[q][TYY]);
@@ -348,12 +375,12 @@ __device__ __forceinline__ void accumulate_f(float acc[KT][kNCPot], int q, float
 }
 
 // Newtonian loop: every pair is at least h apart and none is a self pair.
-template <int KT, int S, bool POT>
+template <int KT, int S, int U, bool POT>
 __device__ __forceinline__ void far_loop_f(const float4 *__restrict__ sp,
                                            const float4 *__restrict__ sv, const float tx[KT][3],
-                                           const float tv[KT][3], float acc[KT][kNCPot])
+                                           float acc[KT][kNCPot])
 {
-#pragma unroll 8
+#pragma unroll U
     for (int j = 0; j < S; ++j) {
         const float4 p = sp[j];
         const float4 v = sv[j];
@@ -366,19 +393,18 @@ __device__ __forceinline__ void far_loop_f(const float4 *__restrict__ sp,
             float mp = p.w * ri;
             float mf = mp * ri2;
             float mg = mf * ri2;
-            accumulate_f<KT, POT>(acc, q, dx, dy, dz, v.x - tv[q][0], v.y - tv[q][1],
-                                  v.z - tv[q][2], mf, mg, mp);
+            accumulate_f<KT, POT>(acc, q, dx, dy, dz, v.x, v.y, v.z, mf, mg, mp);
         }
     }
 }
 
-// Softened loop: cubic-spline kernel inside h, self pair excluded by index.
+// Softened loop: cubic-spline kernel inside h, self pair excluded by index,
+// E collects m f - m g' r^2 of the softened pairs.
 template <int KT, int S, bool POT>
 __device__ __forceinline__ void near_loop_f(const float4 *__restrict__ sp,
                                             const float4 *__restrict__ sv, const float tx[KT][3],
-                                            const float tv[KT][3], const int64_t ti[KT],
-                                            int64_t jbase, float h2, float hinv,
-                                            float acc[KT][kNCPot])
+                                            const int64_t ti[KT], int64_t jbase, float h2,
+                                            float hinv, float acc[KT][kNCPot])
 {
     const float hinv3 = hinv * hinv * hinv;
     const float hinv5 = hinv3 * hinv * hinv;
@@ -407,9 +433,9 @@ __device__ __forceinline__ void near_loop_f(const float4 *__restrict__ sp,
                     mg = 0.0f;
                     mp = 0.0f;
                 }
+                acc[q][ESUM] += fmaf(-mg, r2, mf);
             }
-            accumulate_f<KT, POT>(acc, q, dx, dy, dz, v.x - tv[q][0], v.y - tv[q][1],
-                                  v.z - tv[q][2], mf, mg, mp);
+            accumulate_f<KT, POT>(acc, q, dx, dy, dz, v.x, v.y, v.z, mf, mg, mp);
         }
     }
 }
@@ -479,6 +505,7 @@ __device__ __forceinline__ void loop_d(const D4 *__restrict__ sp, const D4 *__re
     }
 }
 
+
 // ---------------------------------------------------------------------------
 // Shared pieces of both eval kernels
 // ---------------------------------------------------------------------------
@@ -494,25 +521,38 @@ __device__ __forceinline__ void write_partial(const EvalArgs &a, int sp, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// K5: mixed-precision eval kernel
+// K5: mixed-precision eval kernel.  SACC: compensated accumulators and FP64
+// target positions live in shared memory (fewer registers, more targets per
+// thread); otherwise in registers.
 // ---------------------------------------------------------------------------
 
-template <int NT, int KT, int S, int MINB, bool POT>
+template <int NT, int KT, int S, bool POT, bool SACC>
+struct MixedSmem {
+    static constexpr int BT = NT * KT;
+    static constexpr int NC = POT ? kNCPot : kNC;
+    float4 stage[2][2 * S];
+    float acc[SACC ? NC * 2 * BT : 1];     // [c][hi, lo][BT]
+    double x[SACC ? 3 * BT : 1];           // [c][BT]
+    uint64_t bar[2];
+    float blo[3], bhi[3];
+    int abort_flag;
+};
+
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC>
 __global__ void __launch_bounds__(NT, MINB)
 eval_mixed_kernel(const EvalArgs a)
 {
-    constexpr int BT = NT * KT;
+    using Sm = MixedSmem<NT, KT, S, POT, SACC>;
+    constexpr int BT = Sm::BT;
     constexpr int NSTAGE = 2;
-    constexpr int NC = POT ? kNCPot : kNC;
+    constexpr int NC = Sm::NC;
     constexpr uint32_t kTileBytes = S * 2 * sizeof(float4);
-    __shared__ __align__(128) float4 stage[NSTAGE][2 * S];
-    __shared__ __align__(8) uint64_t bar[NSTAGE];
-    __shared__ float blo[3], bhi[3];
-    __shared__ int abort_flag;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
-        abort_flag = 0;
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&sm.bar[s], 1);
+        sm.abort_flag = 0;
         fence_barrier_init();
     }
     __syncthreads();
@@ -533,8 +573,8 @@ eval_mixed_kernel(const EvalArgs a)
         const int t_end = (int)((int64_t)(sp + 1) * a.n_tiles / split);
 
         // ---- targets of this block (KT per thread, strided by NT) ----
-        double xi[KT][3];
-        float tv[KT][3];
+        double xr[SACC ? 1 : KT][3];
+        float tvf[KT][3];
         int64_t ti[KT];
         float lo[3], hi[3];
 #pragma unroll
@@ -554,52 +594,65 @@ eval_mixed_kernel(const EvalArgs a)
                 }
             }
             ti[q] = i;
-            if (i >= 0) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    xi[q][c] = a.pos[3 * i + c];
-                    tv[q][c] = __double2float_rn(a.vel[3 * i + c]);
-                    lo[c] = fminf(lo[c], __double2float_rd(xi[q][c]));
-                    hi[c] = fmaxf(hi[c], __double2float_ru(xi[q][c]));
+            for (int c = 0; c < 3; ++c) {
+                double x = 0.0;
+                tvf[q][c] = 0.0f;
+                if (i >= 0) {
+                    x = a.pos[3 * i + c];
+                    tvf[q][c] = __double2float_rn(a.vel[3 * i + c]);
+                    lo[c] = fminf(lo[c], __double2float_rd(x));
+                    hi[c] = fmaxf(hi[c], __double2float_ru(x));
                 }
-            } else {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    xi[q][c] = 0.0;
-                    tv[q][c] = 0.0f;
-                }
+                if (SACC)
+                    sm.x[c * BT + q * NT + threadIdx.x] = x;
+                else
+                    xr[SACC ? 0 : q][c] = x;
             }
         }
-        block_bbox<NT>(lo, hi, blo, bhi);
-        const float blo_r[3] = {blo[0], blo[1], blo[2]};
-        const float bhi_r[3] = {bhi[0], bhi[1], bhi[2]};
+        block_bbox<NT>(lo, hi, sm.blo, sm.bhi);     // (its barriers also publish sm.x)
+        const float blo_r[3] = {sm.blo[0], sm.blo[1], sm.blo[2]};
+        const float bhi_r[3] = {sm.bhi[0], sm.bhi[1], sm.bhi[2]};
 
-        float shi[KT][kNCPot], slo[KT][kNCPot];
+        float rhi[SACC ? 1 : KT][SACC ? 1 : kNCPot], rlo[SACC ? 1 : KT][SACC ? 1 : kNCPot];
+        if (SACC) {
 #pragma unroll
-        for (int q = 0; q < KT; ++q)
+            for (int q = 0; q < KT; ++q)
 #pragma unroll
-            for (int c = 0; c < kNCPot; ++c) {
-                shi[q][c] = 0.0f;
-                slo[q][c] = 0.0f;
-            }
+                for (int c = 0; c < 2 * NC; ++c) sm.acc[c * BT + q * NT + threadIdx.x] = 0.0f;
+        } else {
+#pragma unroll
+            for (int q = 0; q < (SACC ? 1 : KT); ++q)
+#pragma unroll
+                for (int c = 0; c < (SACC ? 1 : kNCPot); ++c) {
+                    rhi[q][c] = 0.0f;
+                    rlo[q][c] = 0.0f;
+                }
+        }
 
         if (threadIdx.x == 0) {
             for (int s = 0; s < NSTAGE; ++s) {
                 int t = t_begin + s;
                 if (t < t_end) {
-                    tma_load_1d(stage[s], src + (int64_t)t * 2 * S, kTileBytes, &bar[s]);
+                    tma_load_1d(sm.stage[s], src + (int64_t)t * 2 * S, kTileBytes, &sm.bar[s]);
                     pending |= 1u << s;
                 }
             }
         }
 
-        // offsets of the targets to the first tile's centre (FP64, rounded once)
+        // offsets of the targets to a tile's centre (FP64, rounded once)
+        auto offsets = [&](const TileGeom &g, float out[KT][3]) {
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double x = SACC ? sm.x[c * BT + q * NT + threadIdx.x] : xr[SACC ? 0 : q][c];
+                    out[q][c] = __double2float_rn(__dsub_rn(x, g.c[c]));
+                }
+        };
         float tx[KT][3], tx_next[KT][3];
         TileGeom g = a.geo[t_begin];
-#pragma unroll
-        for (int q = 0; q < KT; ++q)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) tx[q][c] = __double2float_rn(__dsub_rn(xi[q][c], g.c[c]));
+        offsets(g, tx);
 
         for (int t = t_begin; t < t_end; ++t) {
             const int s = (t - t_begin) % NSTAGE;
@@ -608,44 +661,65 @@ eval_mixed_kernel(const EvalArgs a)
             TileGeom gn = g;
             if (t + 1 < t_end) {
                 gn = a.geo[t + 1];
-#pragma unroll
-                for (int q = 0; q < KT; ++q)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        tx_next[q][c] = __double2float_rn(__dsub_rn(xi[q][c], gn.c[c]));
+                offsets(gn, tx_next);
             }
-            const bool got = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, a.flags);
+            const bool got = mbar_wait_bounded(&sm.bar[s], (parity >> s) & 1u, a.flags);
             if (got)
                 parity ^= 1u << s;
             else
-                atomicExch(&abort_flag, 1);
+                atomicExch(&sm.abort_flag, 1);
 
             float acc[KT][kNCPot];
 #pragma unroll
             for (int q = 0; q < KT; ++q)
 #pragma unroll
                 for (int c = 0; c < kNCPot; ++c) acc[q][c] = 0.0f;
-            const float4 *sp_ = stage[s];
-            const float4 *sv_ = stage[s] + S;
+            const float4 *sp_ = sm.stage[s];
+            const float4 *sv_ = sm.stage[s] + S;
             if (!near)
-                far_loop_f<KT, S, POT>(sp_, sv_, tx, tv, acc);
+                far_loop_f<KT, S, U, POT>(sp_, sv_, tx, acc);
             else
-                near_loop_f<KT, S, POT>(sp_, sv_, tx, tv, ti, (int64_t)t * S, a.h2f_up, a.hinvf,
-                                        acc);
+                near_loop_f<KT, S, POT>(sp_, sv_, tx, ti, g.first, a.h2f_up, a.hinvf, acc);
+
+            // per-tile corrections for the target velocity, then the carry
 #pragma unroll
-            for (int q = 0; q < KT; ++q)
+            for (int q = 0; q < KT; ++q) {
+                const float ux = tvf[q][0] - g.cv[0], uy = tvf[q][1] - g.cv[1], uz = tvf[q][2] - g.cv[2];
+                const float Ft = acc[q][ESUM] + (acc[q][TXX] + acc[q][TYY] + acc[q][TZZ]);
+                acc[q][J10 + 0] = fmaf(-ux, Ft, acc[q][J10 + 0]);
+                acc[q][J10 + 1] = fmaf(-uy, Ft, acc[q][J10 + 1]);
+                acc[q][J10 + 2] = fmaf(-uz, Ft, acc[q][J10 + 2]);
+                acc[q][J20 + 0] -= fmaf(acc[q][TXX], ux, fmaf(acc[q][TXY], uy, acc[q][TXZ] * uz));
+                acc[q][J20 + 1] -= fmaf(acc[q][TXY], ux, fmaf(acc[q][TYY], uy, acc[q][TYZ] * uz));
+                acc[q][J20 + 2] -= fmaf(acc[q][TXZ], ux, fmaf(acc[q][TYZ], uy, acc[q][TZZ] * uz));
+                if (SACC) {
 #pragma unroll
-                for (int c = 0; c < NC; ++c) two_sum_acc(shi[q][c], slo[q][c], acc[q][c]);
+                    for (int c = 0; c < NC; ++c) {
+                        float *ph = &sm.acc[(2 * c) * BT + q * NT + threadIdx.x];
+                        float *pl = &sm.acc[(2 * c + 1) * BT + q * NT + threadIdx.x];
+                        float h = *ph, l = *pl;
+                        two_sum_acc(h, l, acc[q][c]);
+                        *ph = h;
+                        *pl = l;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c)
+                        two_sum_acc(rhi[SACC ? 0 : q][SACC ? 0 : c], rlo[SACC ? 0 : q][SACC ? 0 : c],
+                                    acc[q][c]);
+                }
+            }
 
             __syncthreads();                       // all reads of stage s are done
             if (threadIdx.x == 0) {
                 if (got) pending &= ~(1u << s);
-                if (t + NSTAGE < t_end && !abort_flag) {
-                    tma_load_1d(stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes, &bar[s]);
+                if (t + NSTAGE < t_end && !sm.abort_flag) {
+                    tma_load_1d(sm.stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes,
+                                &sm.bar[s]);
                     pending |= 1u << s;
                 }
             }
-            if (abort_flag) break;
+            if (sm.abort_flag) break;
             g = gn;
 #pragma unroll
             for (int q = 0; q < KT; ++q)
@@ -658,21 +732,30 @@ eval_mixed_kernel(const EvalArgs a)
         for (int q = 0; q < KT; ++q) {
             double sum[kNCPot];
 #pragma unroll
-            for (int c = 0; c < kNCPot; ++c) sum[c] = (double)shi[q][c] + (double)slo[q][c];
+            for (int c = 0; c < kNCPot; ++c) {
+                if (c >= NC) {
+                    sum[c] = 0.0;
+                } else if (SACC) {
+                    sum[c] = (double)sm.acc[(2 * c) * BT + q * NT + threadIdx.x] +
+                             (double)sm.acc[(2 * c + 1) * BT + q * NT + threadIdx.x];
+                } else {
+                    sum[c] = (double)rhi[SACC ? 0 : q][SACC ? 0 : c] + (double)rlo[SACC ? 0 : q][SACC ? 0 : c];
+                }
+            }
             const int64_t slot = tb * BT + (int64_t)q * NT + threadIdx.x;
             if (split == 1) {
-                if (ti[q] >= 0) write_target<POT>(a, ti[q], sum);
+                if (ti[q] >= 0) write_target<POT, true>(a, ti[q], sum);
             } else {
                 write_partial<NC>(a, sp, rows, slot, sum);
             }
         }
-        if (abort_flag) break;
+        if (sm.abort_flag) break;
         __syncthreads();
     }
     // Never leave a copy in flight into shared memory (only after a timeout).
     if (threadIdx.x == 0 && pending) {
         for (int s = 0; s < NSTAGE; ++s)
-            if (pending & (1u << s)) mbar_wait_bounded(&bar[s], (parity >> s) & 1u, a.flags);
+            if (pending & (1u << s)) mbar_wait_bounded(&sm.bar[s], (parity >> s) & 1u, a.flags);
     }
 }
 
@@ -770,9 +853,9 @@ eval_f64_kernel(const EvalArgs a)
 #pragma unroll
             for (int c = 0; c < kNCPot; ++c) acc[c] = 0.0;
             if (!near)
-                loop_d<S, POT, false>(stage[s], stage[s] + S, xi, vi, i, (int64_t)t * S, h2, hinv, acc);
+                loop_d<S, POT, false>(stage[s], stage[s] + S, xi, vi, i, g.first, h2, hinv, acc);
             else
-                loop_d<S, POT, true>(stage[s], stage[s] + S, xi, vi, i, (int64_t)t * S, h2, hinv, acc);
+                loop_d<S, POT, true>(stage[s], stage[s] + S, xi, vi, i, g.first, h2, hinv, acc);
 #pragma unroll
             for (int c = 0; c < NC; ++c) two_sum_acc(shi[c], slo[c], acc[c]);
             __syncthreads();
@@ -789,7 +872,7 @@ eval_f64_kernel(const EvalArgs a)
 #pragma unroll
         for (int c = 0; c < kNCPot; ++c) sum[c] = shi[c] + slo[c];
         if (split == 1) {
-            if (i >= 0) write_target<POT>(a, i, sum);
+            if (i >= 0) write_target<POT, false>(a, i, sum);
         } else {
             write_partial<NC>(a, sp, rows, slot, sum);
         }
@@ -806,7 +889,7 @@ eval_f64_kernel(const EvalArgs a)
 // K9: deterministic reduction of the chunk partials (fixed chunk order)
 // ---------------------------------------------------------------------------
 
-template <bool POT>
+template <bool POT, bool ETRACE>
 __global__ void __launch_bounds__(256)
 reduce_partials_kernel(const EvalArgs a, int32_t BT)
 {
@@ -834,7 +917,7 @@ reduce_partials_kernel(const EvalArgs a, int32_t BT)
     double sum[kNCPot];
 #pragma unroll
     for (int c = 0; c < kNCPot; ++c) sum[c] = hi[c] + lo[c];
-    write_target<POT>(a, i, sum);
+    write_target<POT, ETRACE>(a, i, sum);
 }
 
 // ---------------------------------------------------------------------------
@@ -854,17 +937,21 @@ struct EvalConfig {
     pack_launch_fn pack;
 };
 
-template <int NT, int KT, int S, int MINB, bool POT>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC>
 void launch_mixed(const EvalArgs &a, int grid, cudaStream_t st)
 {
-    eval_mixed_kernel<NT, KT, S, MINB, POT><<<grid, NT, 0, st>>>(a);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC>);
+    eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC><<<grid, NT, bytes, st>>>(a);
 }
 
-template <int NT, int KT, int S, int MINB, bool POT>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC>
 int occupancy_mixed(int *b)
 {
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        b, eval_mixed_kernel<NT, KT, S, MINB, POT>, NT, 0);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC>);
+    auto k = eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, k, NT, bytes);
 }
 
 template <int NT, int S, bool POT>
@@ -879,16 +966,16 @@ int occupancy_f64(int *b)
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_kernel<NT, S, POT>, NT, 0);
 }
 
-template <int S, bool MIXED>
+template <int S, bool MIXED, bool VOFF>
 void launch_pack(int64_t n_src, const double *pos, const double *vel, const double *mass,
                  TileGeom *geo, void *src, int32_t *flags, int n_tiles, cudaStream_t st)
 {
-    pack_tiles_kernel<S, MIXED><<<n_tiles, S, 0, st>>>(n_src, pos, vel, mass, geo, src, flags);
+    pack_tiles_kernel<S, MIXED, VOFF><<<n_tiles, S, 0, st>>>(n_src, pos, vel, mass, geo, src, flags);
 }
 
 // Defined in the per-precision translation units.
 const EvalConfig *mixed_configs(int *count);
 const EvalConfig *f64_configs(int *count);
-void launch_reduce(const EvalArgs &a, int32_t BT, bool pot, int blocks, cudaStream_t st);
+void launch_reduce(const EvalArgs &a, int32_t BT, bool pot, bool etrace, int blocks, cudaStream_t st);
 
 }  // namespace grav

@@ -5,7 +5,7 @@ namespace grav {
 
 #define GRAV_F64_CFG(NT, S)                                                                   \
     {GRAV_F64, NT, 1, S, {launch_f64<NT, S, false>, launch_f64<NT, S, true>},                 \
-     {occupancy_f64<NT, S, false>, occupancy_f64<NT, S, true>}, launch_pack<S, false>}
+     {occupancy_f64<NT, S, false>, occupancy_f64<NT, S, true>}, launch_pack<S, false, false>}
 
 static const EvalConfig kF64Configs[] = {
     GRAV_F64_CFG(128, 128),
@@ -19,12 +19,16 @@ const EvalConfig *f64_configs(int *count)
     return kF64Configs;
 }
 
-void launch_reduce(const EvalArgs &a, int32_t BT, bool pot, int blocks, cudaStream_t st)
+void launch_reduce(const EvalArgs &a, int32_t BT, bool pot, bool etrace, int blocks, cudaStream_t st)
 {
-    if (pot)
-        reduce_partials_kernel<true><<<blocks, 256, 0, st>>>(a, BT);
+    if (pot && etrace)
+        reduce_partials_kernel<true, true><<<blocks, 256, 0, st>>>(a, BT);
+    else if (pot)
+        reduce_partials_kernel<true, false><<<blocks, 256, 0, st>>>(a, BT);
+    else if (etrace)
+        reduce_partials_kernel<false, true><<<blocks, 256, 0, st>>>(a, BT);
     else
-        reduce_partials_kernel<false><<<blocks, 256, 0, st>>>(a, BT);
+        reduce_partials_kernel<false, false><<<blocks, 256, 0, st>>>(a, BT);
 }
 
 }  // namespace grav

@@ -10,7 +10,7 @@
 namespace grav {
 namespace {
 
-constexpr int kDefaultMixed = 0;
+constexpr int kDefaultMixed = 2;
 constexpr int kDefaultF64 = 0;
 constexpr int64_t kSplitRowsPerSM = 16;   // partial capacity, in target blocks per SM
 
@@ -226,7 +226,7 @@ extern "C" int grav_eval_active(const grav_params *p, int64_t n_src, const doubl
     }
     if (need_reduce) {
         int blocks = (int)((n_idx_max + 255) / 256);
-        launch_reduce(a, BT, want_pot, blocks, st);
+        launch_reduce(a, BT, want_pot, c->precision == GRAV_MIXED, blocks, st);
         rc = check_launch("grav_eval_active/reduce");
         if (rc) return rc;
     }

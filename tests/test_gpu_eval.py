@@ -43,8 +43,10 @@ def test_mixed_uniform_sphere_4096(sphere4096):
     assert_mixed(e)
 
 
-@pytest.mark.parametrize("cfg", range(5))
+@pytest.mark.parametrize("cfg", range(12))
 def test_mixed_tile_configs(cfg):
+    if cfg >= grav.lib().grav_tile_config_count(grav.MIXED):
+        pytest.skip("no such tile configuration")
     n = 2500
     pos, vel, mass = ics.plummer(n, seed=11)
     idx = ics.active_subset(n, 0.37, 12)
@@ -53,8 +55,10 @@ def test_mixed_tile_configs(cfg):
     assert_mixed(errors(out, ref, idx))
 
 
-@pytest.mark.parametrize("cfg", range(3))
+@pytest.mark.parametrize("cfg", range(6))
 def test_f64_tile_configs(cfg):
+    if cfg >= grav.lib().grav_tile_config_count(grav.F64):
+        pytest.skip("no such tile configuration")
     n = 1777
     pos, vel, mass = ics.uniform_sphere(n, seed=13)
     idx = ics.active_subset(n, 0.6, 14)
@@ -212,3 +216,17 @@ def test_cloud_2e20_f64_sampled(cloud_2e20):
     rows = np.sort(ics.rng(42).choice(idx, size=96, replace=False)).astype(np.int32)
     ref = O.eval_active(pos, vel, mass, rows, h=2e-3)
     assert_f64(errors(out, ref, rows))
+
+
+@pytest.mark.parametrize("cfg", range(12))
+def test_cloud_2e20_every_mixed_config(cloud_2e20, cfg):
+    if cfg >= grav.lib().grav_tile_config_count(grav.MIXED):
+        pytest.skip("no such tile configuration")
+    pos, vel, mass = cloud_2e20
+    n = mass.size
+    idx = ics.active_subset(n, 0.02, 77)
+    out = run_eval(pos, vel, mass, idx, h=2e-3, precision=grav.MIXED, tile_config=cfg,
+                   want_pot=False)
+    rows = np.sort(ics.rng(78).choice(idx, size=64, replace=False)).astype(np.int32)
+    ref = O.eval_active(pos, vel, mass, rows, h=2e-3, want_pot=False)
+    assert_mixed(errors(out, ref, rows))
