@@ -281,7 +281,8 @@ def run_ours(args, rank, local, ws):
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "tile_config": grav.tile_configs(grav.MIXED)[
-                       args.tile_config if args.tile_config >= 0 else 0]},
+                       args.tile_config if args.tile_config >= 0
+                       else grav.default_tile_config(grav.MIXED)]},
         "gpu_launches": path.launches_per_step * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": wall,
@@ -366,6 +367,8 @@ def extras(args, path, dev, sms, peak32, flush):
     tp = statistics.median(ts)
     bytes_pred = n * (1 + 1 + 8 + 24 + 24 + 24)
     out["predict"] = {"bytes_per_element": 82, "GB_per_s": bytes_pred / tp / 1e9, "us": tp * 1e6}
+    out["batched_256_systems"] = batched_extra(dev, flush)
+    out["adaptive_plummer_131072"] = adaptive_extra(dev)
     try:
         f32 = grav.measure_fma_peak(grav.MIXED, 0.5)
         f64 = grav.measure_fma_peak(grav.F64, 0.5)
@@ -373,6 +376,93 @@ def extras(args, path, dev, sms, peak32, flush):
     except grav.GravError as e:
         out["measured_fma_peak_tflops"] = {"error": str(e)}
     return out
+
+
+def batched_extra(dev, flush):
+    """256 independent systems (half Plummer, half uniform; sizes log-uniform
+    in [512, 65536]; 1-50% of each active) in one persistent launch with
+    autotuned tiles, mixed and FP64; and 100 substeps of the batched adaptive
+    loop captured as one CUDA graph."""
+    import torch
+
+    from paper_2010_13792_gb300 import autotune, grav, ics
+    from paper_2010_13792_gb300.adaptive import AdaptiveIntegrator
+    pos, vel, mass, offsets, sizes, act = ics.batched_systems(256, 512, 65536,
+                                                              seed=ics.BASE_SEED + 4)
+    n = mass.size
+    idx_np = np.concatenate([a + o for a, o in zip(act, offsets)]).astype(np.int32)
+    inter = float(sum(a.size * int(s) for a, s in zip(act, sizes)))
+    f64 = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    P, V, M = f64(pos), f64(vel), f64(mass)
+    systems = torch.as_tensor(np.stack([offsets, sizes], 1), dtype=torch.int64, device=dev)
+    idx = torch.as_tensor(idx_np, device=dev)
+    acc = torch.empty(n, 3, dtype=torch.float64, device=dev)
+    jerk, tid = torch.empty_like(acc), torch.empty(n, 6, dtype=torch.float64, device=dev)
+    res = {"n_total": int(n), "n_targets": int(idx_np.size), "interactions": inter}
+    for name, prec in (("mixed", grav.MIXED), ("f64", grav.F64)):
+        p = grav.params(h=1e-3, precision=prec)
+        best, ms = autotune.tune_eval(p, P, V, M, idx, idx_np.size, systems=systems, reps=2,
+                                      use_cache=False)
+        p = grav.params(h=1e-3, precision=prec, tile_config=best)
+        ws = grav.Workspace()
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            grav.eval_batched(p, systems, P, V, M, idx, None, idx_np.size, acc, jerk, tid,
+                              workspace=ws)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) * 1e-3)
+        t = statistics.median(ts)
+        res[name] = {"interactions_per_s": inter / t, "ms": 1e3 * t, "tile_config": best,
+                     "autotune_ms": {str(k): round(v, 3) for k, v in ms.items()}}
+    it = AdaptiveIntegrator(pos, vel, mass, h=1e-3, q_f=0.5, k_max=6, dt_max=2.0**-4,
+                            precision=grav.MIXED, systems=np.stack([offsets, sizes], 1),
+                            tile_config=res["mixed"]["tile_config"])
+    it.start()
+    it.capture(99)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    it.replay(1)
+    b.record()
+    torch.cuda.synchronize()
+    res["graph_100_substeps"] = {"ms": a.elapsed_time(b), "work_ratio": it.work_ratio(),
+                                 "substeps": 100}
+    return res
+
+
+def adaptive_extra(dev):
+    """Plummer N = 2^17, h = 1e-3, k_max = 6: one 64-substep cycle of the
+    adaptive loop (q_f = 1/2, jerk predictor) against update-every-substep
+    (q_f = 0), both captured as CUDA graphs, mixed precision."""
+    import torch
+
+    from paper_2010_13792_gb300 import grav, ics
+    from paper_2010_13792_gb300.adaptive import AdaptiveIntegrator
+    pos, vel, mass = ics.plummer(1 << 17, seed=ics.BASE_SEED + 1)
+    res = {}
+    runs = {}
+    for name, q_f in (("standard_qf0", 0.0), ("adaptive_qf0.5", 0.5)):
+        it = AdaptiveIntegrator(pos, vel, mass, h=1e-3, q_f=q_f, k_max=6, dt_max=2.0**-4,
+                                precision=grav.MIXED)
+        e0 = sum(it.energy())
+        it.start()
+        it.capture_cycle()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        it.replay(1)
+        b.record()
+        torch.cuda.synchronize()
+        e1 = sum(it.energy())
+        runs[name] = it
+        res[name] = {"ms_per_64_substeps": a.elapsed_time(b), "work_ratio": it.work_ratio(),
+                     "rel_energy_change": abs(e1 - e0) / abs(e0)}
+    s, ad = runs["standard_qf0"], runs["adaptive_qf0.5"]
+    res["speedup"] = res["standard_qf0"]["ms_per_64_substeps"] / res["adaptive_qf0.5"]["ms_per_64_substeps"]
+    res["median_position_difference"] = float((ad.pos - s.pos).norm(dim=1).median().item())
+    return res
 
 
 def e2e(args, path, dev, flush):

@@ -81,7 +81,17 @@ typedef struct grav_tile_info {
     int32_t targets_per_thread;
     int32_t sources_per_tile; /* S: sources staged per shared-memory tile */
     int32_t targets_per_block;/* threads * targets_per_thread */
+    int32_t unroll;           /* unroll depth of the Newtonian pair loop (mixed), 0 if fixed */
+    int32_t shared_accumulators; /* 1: compensated sums kept in shared memory */
 } grav_tile_info;
+
+/* One independent system of a batched launch: elements [offset, offset + n)
+ * of the packed arrays.  Systems are given in ascending, non-overlapping
+ * order. */
+typedef struct grav_system {
+    int64_t offset;
+    int64_t n;
+} grav_system;
 
 GRAV_API const char *grav_last_error_string(void);
 GRAV_API const char *grav_version(void);
@@ -225,17 +235,51 @@ GRAV_API int grav_eval_backward(const grav_params *p, int64_t n, const double *p
                        const double *pot, double *pos_bar, double *mass_bar, int32_t *flags_dev,
                        void *workspace, int64_t workspace_bytes, void *stream);
 
+/*
+ * grav_eval_batched -- grav_eval_active over many independent systems in one
+ * persistent launch (pattern (2) of the batched workloads; the paper's method
+ * per system is unchanged).  systems [n_sys] is a DEVICE array of
+ * {offset, n} describing systems packed back to back in pos/vel/mass
+ * (ascending, non-overlapping, inside [0, n_total)); the sources of a target
+ * are the elements of its own system only.  idx[0..c) are GLOBAL target
+ * indices in ascending order (for example grav_compact_active over the
+ * packed due flags), c = *n_idx_dev or n_idx_max; each system's targets are
+ * found on the device by binary search, so counts never visit the host and
+ * the call can be captured in a CUDA graph.  Outputs are scattered to the
+ * targets' rows as in grav_eval_active.
+ * Work is split into (system, target block) items, ordered by decreasing
+ * per-item cost (system size) and taken by a fixed grid of CTAs through an
+ * atomic ticket; each target's sum is formed by one CTA over its system's
+ * tiles in a fixed order, so results do not depend on scheduling and equal
+ * grav_eval_active on that system alone with max_split = 1.
+ * A system that is out of range or overlaps its predecessor is skipped and
+ * sets GRAV_FLAG_BADINDEX; targets that belong to no system are not
+ * evaluated.
+ * n_sys <= GRAV_BATCH_MAX_SYSTEMS.
+ * workspace: >= grav_batched_workspace_bytes(p, n_sys, n_total) bytes.
+ */
+#define GRAV_BATCH_MAX_SYSTEMS 16384
+GRAV_API int64_t grav_batched_workspace_bytes(const grav_params *p, int32_t n_sys, int64_t n_total);
+GRAV_API int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav_system *systems,
+                               int64_t n_total, const double *pos, const double *vel,
+                               const double *mass, const int32_t *idx, const int32_t *n_idx_dev,
+                               int64_t n_idx_max, double *acc, double *jerk, double *tidal,
+                               double *pot, double *dt_grav, int32_t *flags_dev, void *workspace,
+                               int64_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Measurement helper (not part of the method).                               */
 /* ------------------------------------------------------------------------ */
 
 /*
  * grav_measure_fma_peak -- times a register-resident FMA throughput kernel
- * (FP32 when precision == GRAV_MIXED, FP64 when GRAV_F64) on the current
+ * (FP32 when precision == GRAV_MIXED, FP64 when GRAV_F64, packed FP32x2
+ * when GRAV_PEAK_F32X2) on the current
  * device with CUDA events and returns the achieved FLOP/s (FMA = 2 flops).
  * Synchronises the stream.  Used to state the CUDA-core peak that the force
  * kernels are measured against.
  */
+#define GRAV_PEAK_F32X2 2
 GRAV_API int grav_measure_fma_peak(int32_t precision, double seconds_target, double *flops_per_s,
                           void *stream);
 

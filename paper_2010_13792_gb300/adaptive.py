@@ -27,7 +27,9 @@ class AdaptiveIntegrator:
     def __init__(self, pos, vel, mass, *, h: float, q_f: float, k_max: int = 6,
                  dt_max: float = 2.0**-4, eta: float = 0.01, G: float = 1.0,
                  precision: int = grav.MIXED, dt_hydro=None, predictor: bool = True,
-                 device=None):
+                 systems=None, tile_config: int = -1, device=None):
+        """systems: optional [n_sys, 2] (offset, n) of independent systems packed
+        back to back; their forces come from one batched launch per tick."""
         device = device or torch.device("cuda", torch.cuda.current_device())
         f64 = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()
         self.dev = device
@@ -36,7 +38,9 @@ class AdaptiveIntegrator:
         self.h, self.q_f, self.k_max, self.dt_max, self.G = h, q_f, k_max, dt_max, G
         self.dt_min = dt_max * 2.0**-k_max
         self.predictor = predictor
-        self.params = grav.params(G=G, h=h, eta=eta, precision=precision)
+        self.params = grav.params(G=G, h=h, eta=eta, precision=precision, tile_config=tile_config)
+        self.systems = None if systems is None else \
+            torch.as_tensor(systems, dtype=torch.int64, device=device).contiguous()
         self.acc = torch.zeros(n, 3, dtype=torch.float64, device=device)
         self.jerk = torch.zeros_like(self.acc)
         self.tidal = torch.zeros(n, 6, dtype=torch.float64, device=device)
@@ -57,7 +61,11 @@ class AdaptiveIntegrator:
         self.ws_compact = grav.Workspace()
         self.ws_eval = grav.Workspace()
         self.ws_compact.get(grav.compact_workspace_bytes(n), device)
-        self.ws_eval.get(grav.eval_workspace_bytes(self.params, n, n), device)
+        if self.systems is None:
+            self.ws_eval.get(grav.eval_workspace_bytes(self.params, n, n), device)
+        else:
+            self.ws_eval.get(grav.batched_workspace_bytes(self.params, self.systems.shape[0], n),
+                             device)
         self.tick = 0
         self.graph = None
         self.graph_ticks = 0
@@ -71,8 +79,13 @@ class AdaptiveIntegrator:
         g.select_due(tick, self.k_max, self.bins, self.tf, self.dt_grav, self.q_f, self.dt_min,
                      self.active, self.due)
         g.compact_active(self.due, self.idx, self.count, workspace=self.ws_compact)
-        g.eval_active(self.params, self.pos, self.vel, self.mass, self.idx, self.count, self.n,
-                      self.acc, self.jerk, self.tidal, None, self.dt_grav, workspace=self.ws_eval)
+        if self.systems is None:
+            g.eval_active(self.params, self.pos, self.vel, self.mass, self.idx, self.count, self.n,
+                          self.acc, self.jerk, self.tidal, None, self.dt_grav, workspace=self.ws_eval)
+        else:
+            g.eval_batched(self.params, self.systems, self.pos, self.vel, self.mass, self.idx,
+                           self.count, self.n, self.acc, self.jerk, self.tidal, None, self.dt_grav,
+                           workspace=self.ws_eval)
         g.predict(self.active, self.due, self.acc, self.jerk if self.predictor else self.zero_j,
                   self.tf, self.dt_min, self.a_kick)
         self.n_due_total += self.count.to(torch.int64)
@@ -125,16 +138,36 @@ class AdaptiveIntegrator:
         self.graph_ticks = period
         return g
 
+    def capture(self, n_ticks: int):
+        """Capture the next n_ticks ticks as one CUDA graph (after start()).  It
+        may be replayed repeatedly only when n_ticks is a multiple of 2^k_max."""
+        if self.tick == 0:
+            self.start()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        base = self.tick
+        with torch.cuda.graph(g):
+            for r in range(n_ticks):
+                self.substep(base + r)
+        self.graph = g
+        self.graph_ticks = n_ticks
+        return g
+
     def replay(self, cycles: int = 1):
         if self.graph is None:
             raise RuntimeError("capture_cycle() first")
+        period = 1 << self.k_max
+        if cycles > 1 and self.graph_ticks % period:
+            raise RuntimeError("a graph of a partial cycle can be replayed once only")
         for _ in range(cycles):
             self.graph.replay()
             self.tick += self.graph_ticks
 
     # -- diagnostics ----------------------------------------------------------
     def energy(self):
-        """Kinetic + potential energy from a fresh all-element evaluation."""
+        """Kinetic + potential energy from a fresh all-element evaluation (one
+        system; for packed systems the sum over systems is not a physical
+        energy)."""
         n = self.n
         p = grav.params(G=self.G, h=self.h, precision=grav.F64, want_pot=True)
         acc = torch.empty(n, 3, dtype=torch.float64, device=self.dev)

@@ -124,26 +124,31 @@ __device__ __forceinline__ int64_t active_count(const EvalArgs &a)
 
 // Final FP64 outputs of one target from its accumulated sums.  ETRACE: slot 9
 // holds E and F = E + trace(Tp) (mixed path); otherwise slot 9 holds F.
+// Every operation is an explicit correctly rounded intrinsic, so all kernels
+// that end in this epilogue (single-system, batched, reduction) turn the same
+// sums into bit-identical outputs whatever the compiler fuses elsewhere.
 template <bool POT, bool ETRACE>
 __device__ __forceinline__ void write_target(const EvalArgs &a, int64_t i, const double s[kNCPot])
 {
     const double G = a.G;
-    const double F = ETRACE ? s[ESUM] + (s[TXX] + s[TYY] + s[TZZ]) : s[FSUM];
+    const double F = ETRACE ? __dadd_rn(s[ESUM], __dadd_rn(__dadd_rn(s[TXX], s[TYY]), s[TZZ]))
+                            : s[FSUM];
+    const double G3 = __dmul_rn(3.0, G);
     double t6[6];
-    t6[0] = -G * (F - 3.0 * s[TXX]);
-    t6[1] = -G * (F - 3.0 * s[TYY]);
-    t6[2] = -G * (F - 3.0 * s[TZZ]);
-    t6[3] = 3.0 * G * s[TXY];
-    t6[4] = 3.0 * G * s[TXZ];
-    t6[5] = 3.0 * G * s[TYZ];
+    t6[0] = __dmul_rn(-G, __dsub_rn(F, __dmul_rn(3.0, s[TXX])));
+    t6[1] = __dmul_rn(-G, __dsub_rn(F, __dmul_rn(3.0, s[TYY])));
+    t6[2] = __dmul_rn(-G, __dsub_rn(F, __dmul_rn(3.0, s[TZZ])));
+    t6[3] = __dmul_rn(G3, s[TXY]);
+    t6[4] = __dmul_rn(G3, s[TXZ]);
+    t6[5] = __dmul_rn(G3, s[TYZ]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        a.acc[3 * i + c] = G * s[A0 + c];
-        a.jerk[3 * i + c] = G * (s[J10 + c] - 3.0 * s[J20 + c]);
+        a.acc[3 * i + c] = __dmul_rn(G, s[A0 + c]);
+        a.jerk[3 * i + c] = __dmul_rn(G, __dsub_rn(s[J10 + c], __dmul_rn(3.0, s[J20 + c])));
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) a.tidal[6 * i + c] = t6[c];
-    if (POT) a.pot[i] = -G * s[PSUM];
+    if (POT) a.pot[i] = __dmul_rn(-G, s[PSUM]);
     if (a.dt_grav) a.dt_grav[i] = tidal_dt(t6, a.sqrt_eta);
 }
 
@@ -227,21 +232,23 @@ __device__ __forceinline__ void block_minmax_d(double lo[3], double hi[3], doubl
     __syncthreads();
 }
 
-// One CTA of S threads per tile; tile t holds sources [first, first + count)
-// with first = t*S.  MIXED: tile = [S x float4 (offset, m)][S x float4 (v', 0)]
-// (v' = v - cv when VOFF, else v); F64: tile = [S x D4 (x, m)][S x D4 (v, 0)].
-// Padding sources have zero mass and sit far away, so they contribute exactly
-// 0.  `mass` may be NULL (zero masses: the adjoint packs a_bar as "velocity").
-template <int S, bool MIXED, bool VOFF>
-__global__ void __launch_bounds__(S)
-pack_tiles_kernel(int64_t n_src, const double *__restrict__ pos, const double *__restrict__ vel,
-                  const double *__restrict__ mass, TileGeom *__restrict__ geo, void *__restrict__ src,
-                  int32_t *flags)
+// One CTA of S threads packs one tile holding the sources [first, end).
+// MIXED: tile = [S x float4 (offset, m)][S x float4 (v', 0)] (v' = v - cv
+// when VOFF, else v); F64: tile = [S x D4 (x, m)][S x D4 (v, 0)].  Padding
+// sources have zero mass and sit far away, so they contribute exactly 0.
+// `mass` may be NULL (zero masses: the adjoint packs a_bar as "velocity").
+template <int S, bool MIXED, bool VOFF, bool PAIR = false>
+__device__ __forceinline__ void pack_tile(int t, int64_t first, int64_t end,
+                                          const double *__restrict__ pos,
+                                          const double *__restrict__ vel,
+                                          const double *__restrict__ mass,
+                                          TileGeom *__restrict__ geo, void *__restrict__ src,
+                                          int32_t *flags)
 {
     __shared__ double slo[3], shi[3], svlo[3], svhi[3];
-    const int t = blockIdx.x, j = threadIdx.x;
-    const int64_t gj = (int64_t)t * S + j;
-    const bool ok = gj < n_src;
+    const int j = threadIdx.x;
+    const int64_t gj = first + j;
+    const bool ok = gj < end;
     double x[3] = {0, 0, 0}, v[3] = {0, 0, 0}, m = 0.0;
     if (ok) {
 #pragma unroll
@@ -275,7 +282,32 @@ pack_tiles_kernel(int64_t n_src, const double *__restrict__ pos, const double *_
     double cc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) cc[c] = __dmul_rn(0.5, __dadd_rn(slo[c], shi[c]));
-    if (MIXED) {
+    if (MIXED && PAIR) {
+        // paired layout: for source j = 2k + h, floats
+        //   [4k + h] x, [4k + 2 + h] y          (S/2 float4: x0 x1 y0 y1)
+        //   [2S + 4k + h] z, [2S + 4k + 2 + h] m (S/2 float4: z0 z1 m0 m1)
+        //   [4S + 4k + h] vx, [4S + 4k + 2 + h] vy
+        //   [6S + 2k + h] vz                     (S/2 float2)
+        float *tile = static_cast<float *>(src) + (int64_t)t * 8 * S;
+        const int k = j >> 1, h = j & 1;
+        float px = 1.0e18f, py = 0.0f, pz = 0.0f, pmv = 0.0f, qx = 0.0f, qy = 0.0f, qz = 0.0f;
+        if (ok) {
+            px = __double2float_rn(__dsub_rn(x[0], cc[0]));
+            py = __double2float_rn(__dsub_rn(x[1], cc[1]));
+            pz = __double2float_rn(__dsub_rn(x[2], cc[2]));
+            pmv = __double2float_rn(m);
+            qx = __double2float_rn(__dsub_rn(v[0], (double)cvf[0]));
+            qy = __double2float_rn(__dsub_rn(v[1], (double)cvf[1]));
+            qz = __double2float_rn(__dsub_rn(v[2], (double)cvf[2]));
+        }
+        tile[4 * k + h] = px;
+        tile[4 * k + 2 + h] = py;
+        tile[2 * S + 4 * k + h] = pz;
+        tile[2 * S + 4 * k + 2 + h] = pmv;
+        tile[4 * S + 4 * k + h] = qx;
+        tile[4 * S + 4 * k + 2 + h] = qy;
+        tile[6 * S + 2 * k + h] = qz;
+    } else if (MIXED) {
         float4 *tile = static_cast<float4 *>(src) + (int64_t)t * 2 * S;
         float4 pm, pv;
         if (ok) {
@@ -313,9 +345,21 @@ pack_tiles_kernel(int64_t n_src, const double *__restrict__ pos, const double *_
             g.hi[c] = __double2float_ru(shi[c]);
             g.cv[c] = cvf[c];
         }
-        g.first = t * S;
+        g.first = (int32_t)first;
         geo[t] = g;
     }
+}
+
+// Single system: tile t holds sources [t*S, min((t+1)*S, n_src)).
+template <int S, bool MIXED, bool VOFF, bool PAIR = false>
+__global__ void __launch_bounds__(S)
+pack_tiles_kernel(int64_t n_src, const double *__restrict__ pos, const double *__restrict__ vel,
+                  const double *__restrict__ mass, TileGeom *__restrict__ geo, void *__restrict__ src,
+                  int32_t *flags)
+{
+    const int64_t first = (int64_t)blockIdx.x * S;
+    const int64_t end = first + S < n_src ? first + S : n_src;
+    pack_tile<S, MIXED, VOFF, PAIR>(blockIdx.x, first, end, pos, vel, mass, geo, src, flags);
 }
 
 // ---------------------------------------------------------------------------
@@ -440,6 +484,96 @@ __device__ __forceinline__ void near_loop_f(const float4 *__restrict__ sp,
     }
 }
 
+// Paired layout, Newtonian loop: two sources per packed FP32x2 instruction
+// (fma/add/mul .f32x2), so one issue slot does the work of two pairs; the
+// SFU rsqrt runs per source.  Lane 0 sums the even sources, lane 1 the odd.
+template <int S, int U, bool POT>
+__device__ __forceinline__ void far_loop_pair(const float *__restrict__ tile, float tx, float ty,
+                                              float tz, float2 acc[kNCPot])
+{
+    const float4 *P0 = reinterpret_cast<const float4 *>(tile);
+    const float4 *P1 = P0 + S / 2;
+    const float4 *V0 = P1 + S / 2;
+    const float2 *V1 = reinterpret_cast<const float2 *>(V0 + S / 2);
+    const float2 ntx = make_float2(-tx, -tx), nty = make_float2(-ty, -ty), ntz = make_float2(-tz, -tz);
+#pragma unroll U
+    for (int k = 0; k < S / 2; ++k) {
+        const float4 p0 = P0[k], p1 = P1[k], v0 = V0[k];
+        const float2 vz = V1[k];
+        const float2 dx = __fadd2_rn(make_float2(p0.x, p0.y), ntx);
+        const float2 dy = __fadd2_rn(make_float2(p0.z, p0.w), nty);
+        const float2 dz = __fadd2_rn(make_float2(p1.x, p1.y), ntz);
+        float2 r2 = __fmul2_rn(dz, dz);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dx, dx, r2);
+        const float2 ri = make_float2(rsqrt_sfu(r2.x), rsqrt_sfu(r2.y));
+        const float2 ri2 = __fmul2_rn(ri, ri);
+        const float2 mp = __fmul2_rn(make_float2(p1.z, p1.w), ri);
+        const float2 mf = __fmul2_rn(mp, ri2);
+        const float2 mg = __fmul2_rn(mf, ri2);
+        const float2 vx = make_float2(v0.x, v0.y), vy = make_float2(v0.z, v0.w);
+        acc[A0 + 0] = __ffma2_rn(mf, dx, acc[A0 + 0]);
+        acc[A0 + 1] = __ffma2_rn(mf, dy, acc[A0 + 1]);
+        acc[A0 + 2] = __ffma2_rn(mf, dz, acc[A0 + 2]);
+        acc[J10 + 0] = __ffma2_rn(mf, vx, acc[J10 + 0]);
+        acc[J10 + 1] = __ffma2_rn(mf, vy, acc[J10 + 1]);
+        acc[J10 + 2] = __ffma2_rn(mf, vz, acc[J10 + 2]);
+        float2 dv = __fmul2_rn(dz, vz);
+        dv = __ffma2_rn(dy, vy, dv);
+        dv = __ffma2_rn(dx, vx, dv);
+        const float2 gx = __fmul2_rn(mg, dx), gy = __fmul2_rn(mg, dy), gz = __fmul2_rn(mg, dz);
+        acc[TXX] = __ffma2_rn(gx, dx, acc[TXX]);
+        acc[TYY] = __ffma2_rn(gy, dy, acc[TYY]);
+        acc[TZZ] = __ffma2_rn(gz, dz, acc[TZZ]);
+        acc[TXY] = __ffma2_rn(gx, dy, acc[TXY]);
+        acc[TXZ] = __ffma2_rn(gx, dz, acc[TXZ]);
+        acc[TYZ] = __ffma2_rn(gy, dz, acc[TYZ]);
+        acc[J20 + 0] = __ffma2_rn(gx, dv, acc[J20 + 0]);
+        acc[J20 + 1] = __ffma2_rn(gy, dv, acc[J20 + 1]);
+        acc[J20 + 2] = __ffma2_rn(gz, dv, acc[J20 + 2]);
+        if (POT) acc[PSUM] = __fadd2_rn(acc[PSUM], mp);
+    }
+}
+
+// Paired layout, softened loop: one source at a time (scalar).
+template <int S, bool POT>
+__device__ __forceinline__ void near_loop_pair(const float *__restrict__ tile, const float tx[1][3],
+                                               const int64_t ti[1], int64_t jbase, float h2,
+                                               float hinv, float acc[1][kNCPot])
+{
+    const float hinv3 = hinv * hinv * hinv;
+    const float hinv5 = hinv3 * hinv * hinv;
+#pragma unroll 2
+    for (int j = 0; j < S; ++j) {
+        const int k = j >> 1, h = j & 1;
+        const float x = tile[4 * k + h], y = tile[4 * k + 2 + h];
+        const float z = tile[2 * S + 4 * k + h], m = tile[2 * S + 4 * k + 2 + h];
+        const float vx = tile[4 * S + 4 * k + h], vy = tile[4 * S + 4 * k + 2 + h];
+        const float vz = tile[6 * S + 2 * k + h];
+        float dx = x - tx[0][0], dy = y - tx[0][1], dz = z - tx[0][2];
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float ri = rsqrt_sfu(r2);
+        float ri2 = ri * ri;
+        float mp = m * ri;
+        float mf = mp * ri2;
+        float mg = mf * ri2;
+        if (r2 < h2) {
+            float F, Gp, P;
+            spline_kernel<float>(sqrtf(r2) * hinv, F, Gp, P);
+            mf = m * F * hinv3;
+            mg = m * Gp * hinv5;
+            mp = m * P * hinv;
+            if (jbase + j == ti[0]) {
+                mf = 0.0f;
+                mg = 0.0f;
+                mp = 0.0f;
+            }
+            acc[0][ESUM] += fmaf(-mg, r2, mf);
+        }
+        accumulate_f<1, POT>(acc, 0, dx, dy, dz, vx, vy, vz, mf, mg, mp);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Pair loops, FP64
 // ---------------------------------------------------------------------------
@@ -521,7 +655,110 @@ __device__ __forceinline__ void write_partial(const EvalArgs &a, int sp, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// K5: mixed-precision eval kernel.  SACC: compensated accumulators and FP64
+// Work items.  One item is the targets idx[slot], slot in
+// [slot0, min(slot0 + BT, slot_end)) (slot itself when idx is NULL), against
+// the source tiles [t_begin, t_end).  Its sums go to the outputs when
+// split == 1, else to column `slot` of chunk `sp`'s partial block.  Targets
+// outside [elem_lo, elem_hi) are flagged and skipped.
+// ---------------------------------------------------------------------------
+
+struct ItemSpec {
+    const int32_t *idx;
+    int64_t slot0, slot_end;
+    int64_t elem_lo, elem_hi;
+    int32_t t_begin, t_end;
+    int32_t sp, split;
+    int64_t rows;
+};
+
+// TMA ring state of a CTA, carried from item to item.
+struct Ring {
+    uint32_t parity;   // bit s: parity of stage s's next completion
+    uint32_t pending;  // thread 0 only: bit s while a copy is in flight into stage s
+};
+
+__device__ __forceinline__ int64_t item_target(const ItemSpec &it, int64_t slot, int32_t *flags)
+{
+    if (slot >= it.slot_end) return -1;
+    int64_t i = it.idx ? (int64_t)it.idx[slot] : slot;
+    if (i < it.elem_lo || i >= it.elem_hi) {
+        flag_or(flags, GRAV_FLAG_BADINDEX);
+        return -1;
+    }
+    return i;
+}
+
+// Never leave a copy in flight into shared memory (only after a timeout).
+template <int NSTAGE>
+__device__ __forceinline__ void drain_ring(uint64_t *bar, const Ring &ring, int32_t *flags)
+{
+    if (threadIdx.x == 0 && ring.pending) {
+        for (int s = 0; s < NSTAGE; ++s)
+            if (ring.pending & (1u << s)) mbar_wait_bounded(&bar[s], (ring.parity >> s) & 1u, flags);
+    }
+}
+
+// Batched launches: the device-side plan (see grav_eval_batched).
+struct BatchHeader {
+    int64_t total_items;
+    int32_t total_tiles;
+    int32_t pad;
+    unsigned long long ticket;   // next work item (atomic counter, reset by the plan kernel)
+    int64_t pad2;
+};
+
+struct BatchView {
+    BatchHeader *hdr;
+    const grav_system *sys;    // [n_sys] (device)
+    int32_t *tile_off;         // [n_sys + 1]
+    int32_t *idx_lo, *idx_hi;  // [n_sys]: each system's range of the target list
+    int32_t *ntb;              // [n_sys]: target blocks
+    int32_t *order;            // [n_sys]: systems, longest work item first
+    int64_t *item_off;         // [n_sys + 1]: first work item of each rank
+    int32_t n_sys;
+    int32_t pad;
+};
+
+// Rank r such that item_off[r] <= ticket < item_off[r + 1].
+__device__ __forceinline__ int item_rank(const BatchView &b, int64_t ticket)
+{
+    int lo = 0, hi = b.n_sys;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (b.item_off[mid] <= ticket)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Batched packing: tile t belongs to the system s with
+// tile_off[s] <= t < tile_off[s + 1]; tiles never straddle two systems.
+template <int S, bool MIXED, bool VOFF, bool PAIR>
+__global__ void __launch_bounds__(S)
+pack_tiles_batched_kernel(const BatchView b, const double *__restrict__ pos,
+                          const double *__restrict__ vel, const double *__restrict__ mass,
+                          TileGeom *__restrict__ geo, void *__restrict__ src, int32_t *flags)
+{
+    const int t = blockIdx.x;
+    if (t >= b.hdr->total_tiles) return;
+    int lo = 0, hi = b.n_sys;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (b.tile_off[mid] <= t)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const int64_t first = b.sys[lo].offset + (int64_t)(t - b.tile_off[lo]) * S;
+    const int64_t sys_end = b.sys[lo].offset + b.sys[lo].n;
+    const int64_t end = first + S < sys_end ? first + S : sys_end;
+    pack_tile<S, MIXED, VOFF, PAIR>(t, first, end, pos, vel, mass, geo, src, flags);
+}
+
+// ---------------------------------------------------------------------------
+// K5: mixed-precision force kernel.  SACC: compensated accumulators and FP64
 // target positions live in shared memory (fewer registers, more targets per
 // thread); otherwise in registers.
 // ---------------------------------------------------------------------------
@@ -536,353 +773,454 @@ struct MixedSmem {
     uint64_t bar[2];
     float blo[3], bhi[3];
     int abort_flag;
+    long long ticket;
 };
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC>
-__global__ void __launch_bounds__(NT, MINB)
-eval_mixed_kernel(const EvalArgs a)
+template <typename Sm>
+__device__ __forceinline__ void init_ring(Sm &sm)
+{
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) mbar_init(&sm.bar[s], 1);
+        sm.abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+}
+
+// One work item of the mixed kernel; false if a bounded wait gave up.
+template <int NT, int KT, int S, int U, bool POT, bool SACC, bool PAIR>
+__device__ __forceinline__ bool mixed_item(const EvalArgs &a, MixedSmem<NT, KT, S, POT, SACC> &sm,
+                                           Ring &ring, const ItemSpec &it)
 {
     using Sm = MixedSmem<NT, KT, S, POT, SACC>;
     constexpr int BT = Sm::BT;
     constexpr int NSTAGE = 2;
     constexpr int NC = Sm::NC;
-    constexpr uint32_t kTileBytes = S * 2 * sizeof(float4);
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; ++s) mbar_init(&sm.bar[s], 1);
-        sm.abort_flag = 0;
-        fence_barrier_init();
-    }
-    __syncthreads();
-    uint32_t parity = 0;             // bit s: parity of stage s's next completion
-    uint32_t pending = 0;            // thread 0 only: bit s set while a copy is in flight
-
-    const int64_t n_act = active_count(a);
-    const int64_t n_tb = (n_act + BT - 1) / BT;
-    const int split = choose_split(n_tb, a.n_tiles, a.grid, a.max_split, a.part_cap_rows, BT);
-    const int64_t items = n_tb * split;
-    const int64_t rows = n_tb * BT;
+    static_assert(!PAIR || KT == 1, "the paired layout serves one target per thread");
+    constexpr uint32_t kTileBytes = PAIR ? S * 28 : S * 2 * sizeof(float4);
     const float4 *src = static_cast<const float4 *>(a.src);
+    const int t_begin = it.t_begin, t_end = it.t_end;
 
-    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const int64_t tb = item / split;
-        const int sp = (int)(item - tb * split);
-        const int t_begin = (int)((int64_t)sp * a.n_tiles / split);
-        const int t_end = (int)((int64_t)(sp + 1) * a.n_tiles / split);
-
-        // ---- targets of this block (KT per thread, strided by NT) ----
-        double xr[SACC ? 1 : KT][3];
-        float tvf[KT][3];
-        int64_t ti[KT];
-        float lo[3], hi[3];
+    // ---- targets of this item (KT per thread, strided by NT) ----
+    double xr[SACC ? 1 : KT][3];
+    float tvf[KT][3];
+    int64_t ti[KT];
+    float lo[3], hi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = __int_as_float(0x7f800000);
+        hi[c] = -__int_as_float(0x7f800000);
+    }
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        const int64_t i = item_target(it, it.slot0 + (int64_t)q * NT + threadIdx.x, a.flags);
+        ti[q] = i;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            lo[c] = __int_as_float(0x7f800000);
-            hi[c] = -__int_as_float(0x7f800000);
-        }
-#pragma unroll
-        for (int q = 0; q < KT; ++q) {
-            const int64_t slot = tb * BT + (int64_t)q * NT + threadIdx.x;
-            int64_t i = -1;
-            if (slot < n_act) {
-                i = a.idx ? (int64_t)a.idx[slot] : slot;
-                if (i < 0 || i >= a.n_src) {
-                    flag_or(a.flags, GRAV_FLAG_BADINDEX);
-                    i = -1;
-                }
+            double x = 0.0;
+            tvf[q][c] = 0.0f;
+            if (i >= 0) {
+                x = a.pos[3 * i + c];
+                tvf[q][c] = __double2float_rn(a.vel[3 * i + c]);
+                lo[c] = fminf(lo[c], __double2float_rd(x));
+                hi[c] = fmaxf(hi[c], __double2float_ru(x));
             }
-            ti[q] = i;
+            if (SACC)
+                sm.x[c * BT + q * NT + threadIdx.x] = x;
+            else
+                xr[SACC ? 0 : q][c] = x;
+        }
+    }
+    block_bbox<NT>(lo, hi, sm.blo, sm.bhi);     // (its barriers also publish sm.x)
+    const float blo_r[3] = {sm.blo[0], sm.blo[1], sm.blo[2]};
+    const float bhi_r[3] = {sm.bhi[0], sm.bhi[1], sm.bhi[2]};
+
+    float rhi[SACC ? 1 : KT][SACC ? 1 : kNCPot], rlo[SACC ? 1 : KT][SACC ? 1 : kNCPot];
+    if (SACC) {
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+#pragma unroll
+            for (int c = 0; c < 2 * NC; ++c) sm.acc[c * BT + q * NT + threadIdx.x] = 0.0f;
+    } else {
+#pragma unroll
+        for (int q = 0; q < (SACC ? 1 : KT); ++q)
+#pragma unroll
+            for (int c = 0; c < (SACC ? 1 : kNCPot); ++c) {
+                rhi[q][c] = 0.0f;
+                rlo[q][c] = 0.0f;
+            }
+    }
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            int t = t_begin + s;
+            if (t < t_end) {
+                tma_load_1d(sm.stage[s], src + (int64_t)t * 2 * S, kTileBytes, &sm.bar[s]);
+                ring.pending |= 1u << s;
+            }
+        }
+    }
+
+    // offsets of the targets to a tile's centre (FP64, rounded once)
+    auto offsets = [&](const TileGeom &g, float out[KT][3]) {
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                double x = 0.0;
-                tvf[q][c] = 0.0f;
-                if (i >= 0) {
-                    x = a.pos[3 * i + c];
-                    tvf[q][c] = __double2float_rn(a.vel[3 * i + c]);
-                    lo[c] = fminf(lo[c], __double2float_rd(x));
-                    hi[c] = fmaxf(hi[c], __double2float_ru(x));
-                }
-                if (SACC)
-                    sm.x[c * BT + q * NT + threadIdx.x] = x;
-                else
-                    xr[SACC ? 0 : q][c] = x;
+                const double x = SACC ? sm.x[c * BT + q * NT + threadIdx.x] : xr[SACC ? 0 : q][c];
+                out[q][c] = __double2float_rn(__dsub_rn(x, g.c[c]));
             }
-        }
-        block_bbox<NT>(lo, hi, sm.blo, sm.bhi);     // (its barriers also publish sm.x)
-        const float blo_r[3] = {sm.blo[0], sm.blo[1], sm.blo[2]};
-        const float bhi_r[3] = {sm.bhi[0], sm.bhi[1], sm.bhi[2]};
+    };
+    float tx[KT][3], tx_next[KT][3];
+    TileGeom g = a.geo[t_begin];
+    offsets(g, tx);
 
-        float rhi[SACC ? 1 : KT][SACC ? 1 : kNCPot], rlo[SACC ? 1 : KT][SACC ? 1 : kNCPot];
-        if (SACC) {
+    for (int t = t_begin; t < t_end; ++t) {
+        const int s = (t - t_begin) % NSTAGE;
+        const bool near = tile_is_near(blo_r, bhi_r, g, a.h2f_up);
+        // next tile's geometry and offsets, computed ahead (FP64 latency)
+        TileGeom gn = g;
+        if (t + 1 < t_end) {
+            gn = a.geo[t + 1];
+            offsets(gn, tx_next);
+        }
+        const bool got = mbar_wait_bounded(&sm.bar[s], (ring.parity >> s) & 1u, a.flags);
+        if (got)
+            ring.parity ^= 1u << s;
+        else
+            atomicExch(&sm.abort_flag, 1);
+
+        float acc[KT][kNCPot];
 #pragma unroll
-            for (int q = 0; q < KT; ++q)
+        for (int q = 0; q < KT; ++q)
 #pragma unroll
-                for (int c = 0; c < 2 * NC; ++c) sm.acc[c * BT + q * NT + threadIdx.x] = 0.0f;
+            for (int c = 0; c < kNCPot; ++c) acc[q][c] = 0.0f;
+        if (PAIR) {
+            const float *tf = reinterpret_cast<const float *>(sm.stage[s]);
+            if (!near) {
+                float2 acc2[kNCPot];
+#pragma unroll
+                for (int c = 0; c < kNCPot; ++c) acc2[c] = make_float2(0.0f, 0.0f);
+                far_loop_pair<S, U, POT>(tf, tx[0][0], tx[0][1], tx[0][2], acc2);
+#pragma unroll
+                for (int c = 0; c < kNCPot; ++c) acc[0][c] = acc2[c].x + acc2[c].y;
+            } else {
+                near_loop_pair<S, POT>(tf, reinterpret_cast<const float(*)[3]>(tx),
+                                       ti, g.first, a.h2f_up, a.hinvf,
+                                       reinterpret_cast<float(*)[kNCPot]>(acc));
+            }
         } else {
-#pragma unroll
-            for (int q = 0; q < (SACC ? 1 : KT); ++q)
-#pragma unroll
-                for (int c = 0; c < (SACC ? 1 : kNCPot); ++c) {
-                    rhi[q][c] = 0.0f;
-                    rlo[q][c] = 0.0f;
-                }
-        }
-
-        if (threadIdx.x == 0) {
-            for (int s = 0; s < NSTAGE; ++s) {
-                int t = t_begin + s;
-                if (t < t_end) {
-                    tma_load_1d(sm.stage[s], src + (int64_t)t * 2 * S, kTileBytes, &sm.bar[s]);
-                    pending |= 1u << s;
-                }
-            }
-        }
-
-        // offsets of the targets to a tile's centre (FP64, rounded once)
-        auto offsets = [&](const TileGeom &g, float out[KT][3]) {
-#pragma unroll
-            for (int q = 0; q < KT; ++q)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double x = SACC ? sm.x[c * BT + q * NT + threadIdx.x] : xr[SACC ? 0 : q][c];
-                    out[q][c] = __double2float_rn(__dsub_rn(x, g.c[c]));
-                }
-        };
-        float tx[KT][3], tx_next[KT][3];
-        TileGeom g = a.geo[t_begin];
-        offsets(g, tx);
-
-        for (int t = t_begin; t < t_end; ++t) {
-            const int s = (t - t_begin) % NSTAGE;
-            const bool near = tile_is_near(blo_r, bhi_r, g, a.h2f_up);
-            // next tile's geometry and offsets, computed ahead (FP64 latency)
-            TileGeom gn = g;
-            if (t + 1 < t_end) {
-                gn = a.geo[t + 1];
-                offsets(gn, tx_next);
-            }
-            const bool got = mbar_wait_bounded(&sm.bar[s], (parity >> s) & 1u, a.flags);
-            if (got)
-                parity ^= 1u << s;
-            else
-                atomicExch(&sm.abort_flag, 1);
-
-            float acc[KT][kNCPot];
-#pragma unroll
-            for (int q = 0; q < KT; ++q)
-#pragma unroll
-                for (int c = 0; c < kNCPot; ++c) acc[q][c] = 0.0f;
             const float4 *sp_ = sm.stage[s];
             const float4 *sv_ = sm.stage[s] + S;
             if (!near)
                 far_loop_f<KT, S, U, POT>(sp_, sv_, tx, acc);
             else
                 near_loop_f<KT, S, POT>(sp_, sv_, tx, ti, g.first, a.h2f_up, a.hinvf, acc);
-
-            // per-tile corrections for the target velocity, then the carry
-#pragma unroll
-            for (int q = 0; q < KT; ++q) {
-                const float ux = tvf[q][0] - g.cv[0], uy = tvf[q][1] - g.cv[1], uz = tvf[q][2] - g.cv[2];
-                const float Ft = acc[q][ESUM] + (acc[q][TXX] + acc[q][TYY] + acc[q][TZZ]);
-                acc[q][J10 + 0] = fmaf(-ux, Ft, acc[q][J10 + 0]);
-                acc[q][J10 + 1] = fmaf(-uy, Ft, acc[q][J10 + 1]);
-                acc[q][J10 + 2] = fmaf(-uz, Ft, acc[q][J10 + 2]);
-                acc[q][J20 + 0] -= fmaf(acc[q][TXX], ux, fmaf(acc[q][TXY], uy, acc[q][TXZ] * uz));
-                acc[q][J20 + 1] -= fmaf(acc[q][TXY], ux, fmaf(acc[q][TYY], uy, acc[q][TYZ] * uz));
-                acc[q][J20 + 2] -= fmaf(acc[q][TXZ], ux, fmaf(acc[q][TYZ], uy, acc[q][TZZ] * uz));
-                if (SACC) {
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        float *ph = &sm.acc[(2 * c) * BT + q * NT + threadIdx.x];
-                        float *pl = &sm.acc[(2 * c + 1) * BT + q * NT + threadIdx.x];
-                        float h = *ph, l = *pl;
-                        two_sum_acc(h, l, acc[q][c]);
-                        *ph = h;
-                        *pl = l;
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < NC; ++c)
-                        two_sum_acc(rhi[SACC ? 0 : q][SACC ? 0 : c], rlo[SACC ? 0 : q][SACC ? 0 : c],
-                                    acc[q][c]);
-                }
-            }
-
-            __syncthreads();                       // all reads of stage s are done
-            if (threadIdx.x == 0) {
-                if (got) pending &= ~(1u << s);
-                if (t + NSTAGE < t_end && !sm.abort_flag) {
-                    tma_load_1d(sm.stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes,
-                                &sm.bar[s]);
-                    pending |= 1u << s;
-                }
-            }
-            if (sm.abort_flag) break;
-            g = gn;
-#pragma unroll
-            for (int q = 0; q < KT; ++q)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) tx[q][c] = tx_next[q][c];
         }
 
-        // ---- results ----
+        // per-tile corrections for the target velocity, then the carry
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
-            double sum[kNCPot];
+            const float ux = tvf[q][0] - g.cv[0], uy = tvf[q][1] - g.cv[1], uz = tvf[q][2] - g.cv[2];
+            const float Ft = acc[q][ESUM] + (acc[q][TXX] + acc[q][TYY] + acc[q][TZZ]);
+            acc[q][J10 + 0] = fmaf(-ux, Ft, acc[q][J10 + 0]);
+            acc[q][J10 + 1] = fmaf(-uy, Ft, acc[q][J10 + 1]);
+            acc[q][J10 + 2] = fmaf(-uz, Ft, acc[q][J10 + 2]);
+            acc[q][J20 + 0] -= fmaf(acc[q][TXX], ux, fmaf(acc[q][TXY], uy, acc[q][TXZ] * uz));
+            acc[q][J20 + 1] -= fmaf(acc[q][TXY], ux, fmaf(acc[q][TYY], uy, acc[q][TYZ] * uz));
+            acc[q][J20 + 2] -= fmaf(acc[q][TXZ], ux, fmaf(acc[q][TYZ], uy, acc[q][TZZ] * uz));
+            if (SACC) {
 #pragma unroll
-            for (int c = 0; c < kNCPot; ++c) {
-                if (c >= NC) {
-                    sum[c] = 0.0;
-                } else if (SACC) {
-                    sum[c] = (double)sm.acc[(2 * c) * BT + q * NT + threadIdx.x] +
-                             (double)sm.acc[(2 * c + 1) * BT + q * NT + threadIdx.x];
-                } else {
-                    sum[c] = (double)rhi[SACC ? 0 : q][SACC ? 0 : c] + (double)rlo[SACC ? 0 : q][SACC ? 0 : c];
+                for (int c = 0; c < NC; ++c) {
+                    float *ph = &sm.acc[(2 * c) * BT + q * NT + threadIdx.x];
+                    float *pl = &sm.acc[(2 * c + 1) * BT + q * NT + threadIdx.x];
+                    float h = *ph, l = *pl;
+                    two_sum_acc(h, l, acc[q][c]);
+                    *ph = h;
+                    *pl = l;
                 }
-            }
-            const int64_t slot = tb * BT + (int64_t)q * NT + threadIdx.x;
-            if (split == 1) {
-                if (ti[q] >= 0) write_target<POT, true>(a, ti[q], sum);
             } else {
-                write_partial<NC>(a, sp, rows, slot, sum);
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    two_sum_acc(rhi[SACC ? 0 : q][SACC ? 0 : c], rlo[SACC ? 0 : q][SACC ? 0 : c],
+                                acc[q][c]);
+            }
+        }
+
+        __syncthreads();                       // all reads of stage s are done
+        if (threadIdx.x == 0) {
+            if (got) ring.pending &= ~(1u << s);
+            if (t + NSTAGE < t_end && !sm.abort_flag) {
+                tma_load_1d(sm.stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes, &sm.bar[s]);
+                ring.pending |= 1u << s;
             }
         }
         if (sm.abort_flag) break;
+        g = gn;
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tx[q][c] = tx_next[q][c];
+    }
+
+    // ---- results ----
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        double sum[kNCPot];
+#pragma unroll
+        for (int c = 0; c < kNCPot; ++c) {
+            if (c >= NC) {
+                sum[c] = 0.0;
+            } else if (SACC) {
+                sum[c] = __dadd_rn((double)sm.acc[(2 * c) * BT + q * NT + threadIdx.x],
+                                   (double)sm.acc[(2 * c + 1) * BT + q * NT + threadIdx.x]);
+            } else {
+                sum[c] = __dadd_rn((double)rhi[SACC ? 0 : q][SACC ? 0 : c],
+                                   (double)rlo[SACC ? 0 : q][SACC ? 0 : c]);
+            }
+        }
+        if (it.split == 1) {
+            if (ti[q] >= 0) write_target<POT, true>(a, ti[q], sum);
+        } else {
+            write_partial<NC>(a, it.sp, it.rows, it.slot0 + (int64_t)q * NT + threadIdx.x, sum);
+        }
+    }
+    return !sm.abort_flag;
+}
+
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
+__global__ void __launch_bounds__(NT, MINB)
+eval_mixed_kernel(const EvalArgs a)
+{
+    using Sm = MixedSmem<NT, KT, S, POT, SACC>;
+    constexpr int BT = Sm::BT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
+    init_ring(sm);
+    Ring ring{0u, 0u};
+    const int64_t n_act = active_count(a);
+    const int64_t n_tb = (n_act + BT - 1) / BT;
+    const int split = choose_split(n_tb, a.n_tiles, a.grid, a.max_split, a.part_cap_rows, BT);
+    const int64_t items = n_tb * split;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t tb = item / split;
+        const int sp = (int)(item - tb * split);
+        ItemSpec it;
+        it.idx = a.idx;
+        it.slot0 = tb * BT;
+        it.slot_end = n_act;
+        it.elem_lo = 0;
+        it.elem_hi = a.n_src;
+        it.t_begin = (int)((int64_t)sp * a.n_tiles / split);
+        it.t_end = (int)((int64_t)(sp + 1) * a.n_tiles / split);
+        it.sp = sp;
+        it.split = split;
+        it.rows = n_tb * BT;
+        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR>(a, sm, ring, it)) break;
         __syncthreads();
     }
-    // Never leave a copy in flight into shared memory (only after a timeout).
-    if (threadIdx.x == 0 && pending) {
-        for (int s = 0; s < NSTAGE; ++s)
-            if (pending & (1u << s)) mbar_wait_bounded(&sm.bar[s], (parity >> s) & 1u, a.flags);
+    drain_ring<2>(sm.bar, ring, a.flags);
+}
+
+// Batched: items of all systems from the plan, taken through an atomic
+// ticket (no waiting on other CTAs).  Each target is summed by one CTA over
+// its system's tiles in a fixed order, so results do not depend on which CTA
+// takes which item.
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
+__global__ void __launch_bounds__(NT, MINB)
+eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
+{
+    using Sm = MixedSmem<NT, KT, S, POT, SACC>;
+    constexpr int BT = Sm::BT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
+    init_ring(sm);
+    Ring ring{0u, 0u};
+    const int64_t total = b.hdr->total_items;
+    for (;;) {
+        if (threadIdx.x == 0) sm.ticket = (long long)atomicAdd(&b.hdr->ticket, 1ULL);
+        __syncthreads();
+        const int64_t ticket = sm.ticket;
+        __syncthreads();
+        if (ticket >= total) break;
+        const int r = item_rank(b, ticket);
+        const int s = b.order[r];
+        ItemSpec it;
+        it.idx = a.idx;
+        it.slot0 = (int64_t)b.idx_lo[s] + (ticket - b.item_off[r]) * BT;
+        it.slot_end = b.idx_hi[s];
+        it.elem_lo = b.sys[s].offset;
+        it.elem_hi = b.sys[s].offset + b.sys[s].n;
+        it.t_begin = b.tile_off[s];
+        it.t_end = b.tile_off[s + 1];
+        it.sp = 0;
+        it.split = 1;
+        it.rows = 0;
+        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR>(a, sm, ring, it)) break;
+        __syncthreads();
     }
+    drain_ring<2>(sm.bar, ring, a.flags);
 }
 
 // ---------------------------------------------------------------------------
-// K4: FP64 eval kernel (one target per thread)
+// K4: FP64 force kernel (one target per thread)
 // ---------------------------------------------------------------------------
+
+template <int S>
+struct F64Smem {
+    D4 stage[2][2 * S];
+    uint64_t bar[2];
+    float blo[3], bhi[3];
+    int abort_flag;
+    long long ticket;
+};
+
+template <int NT, int S, bool POT>
+__device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring &ring,
+                                         const ItemSpec &it)
+{
+    constexpr int NSTAGE = 2;
+    constexpr int NC = POT ? kNCPot : kNC;
+    constexpr uint32_t kTileBytes = S * 2 * sizeof(D4);
+    const D4 *src = static_cast<const D4 *>(a.src);
+    const double h2 = a.h * a.h;
+    const double hinv = 1.0 / a.h;
+    const int t_begin = it.t_begin, t_end = it.t_end;
+
+    const int64_t i = item_target(it, it.slot0 + threadIdx.x, a.flags);
+    double xi[3] = {0, 0, 0}, vi[3] = {0, 0, 0};
+    float lo[3], hi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = __int_as_float(0x7f800000);
+        hi[c] = -__int_as_float(0x7f800000);
+        if (i >= 0) {
+            xi[c] = a.pos[3 * i + c];
+            vi[c] = a.vel[3 * i + c];
+            lo[c] = __double2float_rd(xi[c]);
+            hi[c] = __double2float_ru(xi[c]);
+        }
+    }
+    block_bbox<NT>(lo, hi, sm.blo, sm.bhi);
+    const float blo_r[3] = {sm.blo[0], sm.blo[1], sm.blo[2]};
+    const float bhi_r[3] = {sm.bhi[0], sm.bhi[1], sm.bhi[2]};
+
+    double shi[kNCPot], slo[kNCPot];
+#pragma unroll
+    for (int c = 0; c < kNCPot; ++c) {
+        shi[c] = 0.0;
+        slo[c] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            int t = t_begin + s;
+            if (t < t_end) {
+                tma_load_1d(sm.stage[s], src + (int64_t)t * 2 * S, kTileBytes, &sm.bar[s]);
+                ring.pending |= 1u << s;
+            }
+        }
+    }
+    for (int t = t_begin; t < t_end; ++t) {
+        const int s = (t - t_begin) % NSTAGE;
+        const TileGeom g = a.geo[t];
+        const bool near = tile_is_near(blo_r, bhi_r, g, a.h2f_up);
+        const bool got = mbar_wait_bounded(&sm.bar[s], (ring.parity >> s) & 1u, a.flags);
+        if (got)
+            ring.parity ^= 1u << s;
+        else
+            atomicExch(&sm.abort_flag, 1);
+        double acc[kNCPot];
+#pragma unroll
+        for (int c = 0; c < kNCPot; ++c) acc[c] = 0.0;
+        if (!near)
+            loop_d<S, POT, false>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, h2, hinv, acc);
+        else
+            loop_d<S, POT, true>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, h2, hinv, acc);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) two_sum_acc(shi[c], slo[c], acc[c]);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (got) ring.pending &= ~(1u << s);
+            if (t + NSTAGE < t_end && !sm.abort_flag) {
+                tma_load_1d(sm.stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes, &sm.bar[s]);
+                ring.pending |= 1u << s;
+            }
+        }
+        if (sm.abort_flag) break;
+    }
+    double sum[kNCPot];
+#pragma unroll
+    for (int c = 0; c < kNCPot; ++c) sum[c] = __dadd_rn(shi[c], slo[c]);
+    if (it.split == 1) {
+        if (i >= 0) write_target<POT, false>(a, i, sum);
+    } else {
+        write_partial<NC>(a, it.sp, it.rows, it.slot0 + threadIdx.x, sum);
+    }
+    return !sm.abort_flag;
+}
 
 template <int NT, int S, bool POT>
 __global__ void __launch_bounds__(NT, 2)
 eval_f64_kernel(const EvalArgs a)
 {
-    constexpr int BT = NT;
-    constexpr int NSTAGE = 2;
-    constexpr int NC = POT ? kNCPot : kNC;
-    constexpr uint32_t kTileBytes = S * 2 * sizeof(D4);
-    __shared__ __align__(128) D4 stage[NSTAGE][2 * S];
-    __shared__ __align__(8) uint64_t bar[NSTAGE];
-    __shared__ float blo[3], bhi[3];
-    __shared__ int abort_flag;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
-        abort_flag = 0;
-        fence_barrier_init();
-    }
-    __syncthreads();
-    uint32_t parity = 0, pending = 0;
-
+    __shared__ __align__(128) F64Smem<S> sm;
+    init_ring(sm);
+    Ring ring{0u, 0u};
     const int64_t n_act = active_count(a);
-    const int64_t n_tb = (n_act + BT - 1) / BT;
-    const int split = choose_split(n_tb, a.n_tiles, a.grid, a.max_split, a.part_cap_rows, BT);
+    const int64_t n_tb = (n_act + NT - 1) / NT;
+    const int split = choose_split(n_tb, a.n_tiles, a.grid, a.max_split, a.part_cap_rows, NT);
     const int64_t items = n_tb * split;
-    const int64_t rows = n_tb * BT;
-    const D4 *src = static_cast<const D4 *>(a.src);
-    const double h2 = a.h * a.h;
-    const double hinv = 1.0 / a.h;
-
     for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const int64_t tb = item / split;
         const int sp = (int)(item - tb * split);
-        const int t_begin = (int)((int64_t)sp * a.n_tiles / split);
-        const int t_end = (int)((int64_t)(sp + 1) * a.n_tiles / split);
-
-        const int64_t slot = tb * BT + threadIdx.x;
-        int64_t i = -1;
-        if (slot < n_act) {
-            i = a.idx ? (int64_t)a.idx[slot] : slot;
-            if (i < 0 || i >= a.n_src) {
-                flag_or(a.flags, GRAV_FLAG_BADINDEX);
-                i = -1;
-            }
-        }
-        double xi[3] = {0, 0, 0}, vi[3] = {0, 0, 0};
-        float lo[3], hi[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            lo[c] = __int_as_float(0x7f800000);
-            hi[c] = -__int_as_float(0x7f800000);
-            if (i >= 0) {
-                xi[c] = a.pos[3 * i + c];
-                vi[c] = a.vel[3 * i + c];
-                lo[c] = __double2float_rd(xi[c]);
-                hi[c] = __double2float_ru(xi[c]);
-            }
-        }
-        block_bbox<NT>(lo, hi, blo, bhi);
-        const float blo_r[3] = {blo[0], blo[1], blo[2]};
-        const float bhi_r[3] = {bhi[0], bhi[1], bhi[2]};
-
-        double shi[kNCPot], slo[kNCPot];
-#pragma unroll
-        for (int c = 0; c < kNCPot; ++c) {
-            shi[c] = 0.0;
-            slo[c] = 0.0;
-        }
-        if (threadIdx.x == 0) {
-            for (int s = 0; s < NSTAGE; ++s) {
-                int t = t_begin + s;
-                if (t < t_end) {
-                    tma_load_1d(stage[s], src + (int64_t)t * 2 * S, kTileBytes, &bar[s]);
-                    pending |= 1u << s;
-                }
-            }
-        }
-        for (int t = t_begin; t < t_end; ++t) {
-            const int s = (t - t_begin) % NSTAGE;
-            const TileGeom g = a.geo[t];
-            const bool near = tile_is_near(blo_r, bhi_r, g, a.h2f_up);
-            const bool got = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, a.flags);
-            if (got)
-                parity ^= 1u << s;
-            else
-                atomicExch(&abort_flag, 1);
-            double acc[kNCPot];
-#pragma unroll
-            for (int c = 0; c < kNCPot; ++c) acc[c] = 0.0;
-            if (!near)
-                loop_d<S, POT, false>(stage[s], stage[s] + S, xi, vi, i, g.first, h2, hinv, acc);
-            else
-                loop_d<S, POT, true>(stage[s], stage[s] + S, xi, vi, i, g.first, h2, hinv, acc);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) two_sum_acc(shi[c], slo[c], acc[c]);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                if (got) pending &= ~(1u << s);
-                if (t + NSTAGE < t_end && !abort_flag) {
-                    tma_load_1d(stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes, &bar[s]);
-                    pending |= 1u << s;
-                }
-            }
-            if (abort_flag) break;
-        }
-        double sum[kNCPot];
-#pragma unroll
-        for (int c = 0; c < kNCPot; ++c) sum[c] = shi[c] + slo[c];
-        if (split == 1) {
-            if (i >= 0) write_target<POT, false>(a, i, sum);
-        } else {
-            write_partial<NC>(a, sp, rows, slot, sum);
-        }
-        if (abort_flag) break;
+        ItemSpec it;
+        it.idx = a.idx;
+        it.slot0 = tb * NT;
+        it.slot_end = n_act;
+        it.elem_lo = 0;
+        it.elem_hi = a.n_src;
+        it.t_begin = (int)((int64_t)sp * a.n_tiles / split);
+        it.t_end = (int)((int64_t)(sp + 1) * a.n_tiles / split);
+        it.sp = sp;
+        it.split = split;
+        it.rows = n_tb * NT;
+        if (!f64_item<NT, S, POT>(a, sm, ring, it)) break;
         __syncthreads();
     }
-    if (threadIdx.x == 0 && pending) {
-        for (int s = 0; s < NSTAGE; ++s)
-            if (pending & (1u << s)) mbar_wait_bounded(&bar[s], (parity >> s) & 1u, a.flags);
+    drain_ring<2>(sm.bar, ring, a.flags);
+}
+
+template <int NT, int S, bool POT>
+__global__ void __launch_bounds__(NT, 2)
+eval_f64_batched_kernel(const EvalArgs a, const BatchView b)
+{
+    __shared__ __align__(128) F64Smem<S> sm;
+    init_ring(sm);
+    Ring ring{0u, 0u};
+    const int64_t total = b.hdr->total_items;
+    for (;;) {
+        if (threadIdx.x == 0) sm.ticket = (long long)atomicAdd(&b.hdr->ticket, 1ULL);
+        __syncthreads();
+        const int64_t ticket = sm.ticket;
+        __syncthreads();
+        if (ticket >= total) break;
+        const int r = item_rank(b, ticket);
+        const int s = b.order[r];
+        ItemSpec it;
+        it.idx = a.idx;
+        it.slot0 = (int64_t)b.idx_lo[s] + (ticket - b.item_off[r]) * NT;
+        it.slot_end = b.idx_hi[s];
+        it.elem_lo = b.sys[s].offset;
+        it.elem_hi = b.sys[s].offset + b.sys[s].n;
+        it.t_begin = b.tile_off[s];
+        it.t_end = b.tile_off[s + 1];
+        it.sp = 0;
+        it.split = 1;
+        it.rows = 0;
+        if (!f64_item<NT, S, POT>(a, sm, ring, it)) break;
+        __syncthreads();
     }
+    drain_ring<2>(sm.bar, ring, a.flags);
 }
 
 // ---------------------------------------------------------------------------
@@ -916,7 +1254,7 @@ reduce_partials_kernel(const EvalArgs a, int32_t BT)
     }
     double sum[kNCPot];
 #pragma unroll
-    for (int c = 0; c < kNCPot; ++c) sum[c] = hi[c] + lo[c];
+    for (int c = 0; c < kNCPot; ++c) sum[c] = __dadd_rn(hi[c], lo[c]);
     write_target<POT, ETRACE>(a, i, sum);
 }
 
@@ -929,29 +1267,73 @@ typedef int (*occupancy_fn)(int *blocks_per_sm);
 typedef void (*pack_launch_fn)(int64_t n_src, const double *, const double *, const double *,
                                TileGeom *, void *, int32_t *, int n_tiles, cudaStream_t);
 
+typedef void (*batched_launch_fn)(const EvalArgs &, const BatchView &, int grid, cudaStream_t);
+typedef void (*batched_pack_fn)(const BatchView &, const double *, const double *, const double *,
+                                TileGeom *, void *, int32_t *, int max_tiles, cudaStream_t);
+
 struct EvalConfig {
     int32_t precision;
-    int32_t threads, kt, s;
+    int32_t threads, kt, s, unroll, sacc;
     eval_launch_fn launch[2];      // [want_pot]
     occupancy_fn occupancy[2];
     pack_launch_fn pack;
+    batched_launch_fn launch_batched[2];
+    occupancy_fn occupancy_batched[2];
+    batched_pack_fn pack_batched;
+    bool paired;                   // mixed source tiles in the paired (FP32x2) layout
 };
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
 void launch_mixed(const EvalArgs &a, int grid, cudaStream_t st)
 {
     constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC>);
-    eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC><<<grid, NT, bytes, st>>>(a);
+    eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR><<<grid, NT, bytes, st>>>(a);
 }
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
 int occupancy_mixed(int *b)
 {
     constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC>);
-    auto k = eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC>;
+    auto k = eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, k, NT, bytes);
+}
+
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
+void launch_mixed_batched(const EvalArgs &a, const BatchView &b, int grid, cudaStream_t st)
+{
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC>);
+    eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR><<<grid, NT, bytes, st>>>(a, b);
+}
+
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
+int occupancy_mixed_batched(int *b)
+{
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC>);
+    auto k = eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, k, NT, bytes);
+}
+
+template <int NT, int S, bool POT>
+void launch_f64_batched(const EvalArgs &a, const BatchView &b, int grid, cudaStream_t st)
+{
+    eval_f64_batched_kernel<NT, S, POT><<<grid, NT, 0, st>>>(a, b);
+}
+
+template <int NT, int S, bool POT>
+int occupancy_f64_batched(int *b)
+{
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_batched_kernel<NT, S, POT>, NT, 0);
+}
+
+template <int S, bool MIXED, bool VOFF, bool PAIR>
+void launch_pack_batched(const BatchView &b, const double *pos, const double *vel, const double *mass,
+                         TileGeom *geo, void *src, int32_t *flags, int max_tiles, cudaStream_t st)
+{
+    pack_tiles_batched_kernel<S, MIXED, VOFF, PAIR><<<max_tiles, S, 0, st>>>(b, pos, vel, mass, geo, src, flags);
 }
 
 template <int NT, int S, bool POT>
@@ -966,11 +1348,11 @@ int occupancy_f64(int *b)
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_kernel<NT, S, POT>, NT, 0);
 }
 
-template <int S, bool MIXED, bool VOFF>
+template <int S, bool MIXED, bool VOFF, bool PAIR>
 void launch_pack(int64_t n_src, const double *pos, const double *vel, const double *mass,
                  TileGeom *geo, void *src, int32_t *flags, int n_tiles, cudaStream_t st)
 {
-    pack_tiles_kernel<S, MIXED, VOFF><<<n_tiles, S, 0, st>>>(n_src, pos, vel, mass, geo, src, flags);
+    pack_tiles_kernel<S, MIXED, VOFF, PAIR><<<n_tiles, S, 0, st>>>(n_src, pos, vel, mass, geo, src, flags);
 }
 
 // Defined in the per-precision translation units.

@@ -4,8 +4,11 @@
 namespace grav {
 
 #define GRAV_F64_CFG(NT, S)                                                                   \
-    {GRAV_F64, NT, 1, S, {launch_f64<NT, S, false>, launch_f64<NT, S, true>},                 \
-     {occupancy_f64<NT, S, false>, occupancy_f64<NT, S, true>}, launch_pack<S, false, false>}
+    {GRAV_F64, NT, 1, S, 4, 0, {launch_f64<NT, S, false>, launch_f64<NT, S, true>},          \
+     {occupancy_f64<NT, S, false>, occupancy_f64<NT, S, true>}, launch_pack<S, false, false, false>, \
+     {launch_f64_batched<NT, S, false>, launch_f64_batched<NT, S, true>},                     \
+     {occupancy_f64_batched<NT, S, false>, occupancy_f64_batched<NT, S, true>},               \
+     launch_pack_batched<S, false, false, false>, false}
 
 static const EvalConfig kF64Configs[] = {
     GRAV_F64_CFG(128, 128),

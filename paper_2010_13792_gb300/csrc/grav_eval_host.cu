@@ -10,7 +10,7 @@
 namespace grav {
 namespace {
 
-constexpr int kDefaultMixed = 2;
+constexpr int kDefaultMixed = 8;
 constexpr int kDefaultF64 = 0;
 constexpr int64_t kSplitRowsPerSM = 16;   // partial capacity, in target blocks per SM
 
@@ -127,6 +127,8 @@ extern "C" int grav_tile_config(int32_t precision, int32_t index, grav_tile_info
     out->targets_per_thread = t[index].kt;
     out->sources_per_tile = t[index].s;
     out->targets_per_block = t[index].threads * t[index].kt;
+    out->unroll = t[index].unroll;
+    out->shared_accumulators = t[index].sacc;
     return GRAV_OK;
 }
 
@@ -231,4 +233,278 @@ extern "C" int grav_eval_active(const grav_params *p, int64_t n_src, const doubl
         if (rc) return rc;
     }
     return GRAV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches
+// ---------------------------------------------------------------------------
+
+namespace grav {
+namespace {
+
+constexpr int kPlanThreads = 1024;
+
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, int64_t key)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)a[mid] < key)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Exclusive scan of vals[0..n) by one CTA; out[0..n] receives the prefix
+// sums and the total.  vals and out may alias.
+template <typename TIn, typename TOut>
+__device__ void cta_exclusive_scan(const TIn *vals, TOut *out, int n)
+{
+    __shared__ long long warp_tot[kPlanThreads / 32];
+    __shared__ long long carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < n; b0 += kPlanThreads) {
+        const int b = b0 + threadIdx.x;
+        const long long v = (b < n) ? (long long)vals[b] : 0;
+        long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            long long t = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                long long y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        const long long excl = carry + (wid ? warp_tot[wid - 1] : 0) + x - v;
+        __syncthreads();
+        if (b < n) out[b] = (TOut)excl;
+        if (threadIdx.x == 0) carry += warp_tot[kPlanThreads / 32 - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = (TOut)carry;
+    __syncthreads();
+}
+
+// The plan of a batched launch (one CTA): per-system tiles and target
+// ranges, the longest-first order of the systems and the work-item offsets;
+// resets the ticket counter.
+__global__ void __launch_bounds__(kPlanThreads)
+batch_plan_kernel(BatchView b, const int32_t *__restrict__ idx, const int32_t *n_idx_dev,
+                  int64_t n_idx_max, int64_t n_total, int32_t S, int32_t BT, int32_t *flags)
+{
+    const int n = b.n_sys;
+    int64_t count = n_idx_max;
+    if (n_idx_dev) {
+        int64_t c = *n_idx_dev;
+        count = c < 0 ? 0 : (c < n_idx_max ? c : n_idx_max);
+    }
+    for (int s = threadIdx.x; s < n; s += kPlanThreads) {
+        const int64_t off = b.sys[s].offset, len = b.sys[s].n;
+        bool ok = off >= 0 && len >= 0 && off + len <= n_total;
+        if (ok && s > 0) ok = off >= b.sys[s - 1].offset + b.sys[s - 1].n;
+        if (!ok) flag_or(flags, GRAV_FLAG_BADINDEX);
+        const int64_t lo = ok ? lower_bound_i32(idx, count, off) : 0;
+        const int64_t hi = ok ? lower_bound_i32(idx, count, off + len) : 0;
+        b.idx_lo[s] = (int32_t)lo;
+        b.idx_hi[s] = (int32_t)hi;
+        b.ntb[s] = ok ? (int32_t)((hi - lo + BT - 1) / BT) : 0;
+        b.tile_off[s] = ok ? (int32_t)((len + S - 1) / S) : 0;     // tile counts, scanned below
+    }
+    __syncthreads();
+    cta_exclusive_scan<int32_t, int32_t>(b.tile_off, b.tile_off, n);
+    // longest work item first: rank by system size, ties by index
+    for (int s = threadIdx.x; s < n; s += kPlanThreads) {
+        const int64_t key = b.sys[s].n;
+        int rank = 0;
+        for (int q = 0; q < n; ++q) {
+            const int64_t kq = b.sys[q].n;
+            rank += (kq > key) || (kq == key && q < s);
+        }
+        b.order[rank] = s;
+    }
+    __syncthreads();
+    // items per rank, then their offsets (item_off doubles as the buffer)
+    for (int r = threadIdx.x; r < n; r += kPlanThreads) b.item_off[r] = b.ntb[b.order[r]];
+    __syncthreads();
+    cta_exclusive_scan<int64_t, int64_t>(b.item_off, b.item_off, n);
+    if (threadIdx.x == 0) {
+        b.hdr->total_items = b.item_off[n];
+        b.hdr->total_tiles = b.tile_off[n];
+        b.hdr->ticket = 0ULL;
+    }
+}
+
+struct BatchLayout {
+    int64_t hdr, tile_off, idx_lo, idx_hi, ntb, order, item_off, geo, src, total;
+    int64_t max_tiles;
+};
+
+BatchLayout batch_layout(const EvalConfig *c, int32_t n_sys, int64_t n_total)
+{
+    BatchLayout L;
+    const int64_t S = c->s;
+    const int64_t elem = (c->precision == GRAV_MIXED) ? 16 : 32;
+    L.max_tiles = (n_total + S - 1) / S + n_sys;
+    int64_t o = 0;
+    L.hdr = o;
+    o += 256;
+    L.tile_off = o;
+    o += round_up(4 * ((int64_t)n_sys + 1), 256);
+    L.idx_lo = o;
+    o += round_up(4 * (int64_t)n_sys, 256);
+    L.idx_hi = o;
+    o += round_up(4 * (int64_t)n_sys, 256);
+    L.ntb = o;
+    o += round_up(4 * (int64_t)n_sys, 256);
+    L.order = o;
+    o += round_up(4 * (int64_t)n_sys, 256);
+    L.item_off = o;
+    o += round_up(8 * ((int64_t)n_sys + 1), 256);
+    L.geo = o;
+    o += round_up(L.max_tiles * (int64_t)sizeof(TileGeom), 256);
+    L.src = o;
+    o += round_up(L.max_tiles * 2 * S * elem, 256);
+    L.total = o;
+    return L;
+}
+
+int batch_grid_for(const EvalConfig *c, int index, bool pot, int *grid)
+{
+    static std::mutex mu;
+    static int cache[64][2][16][2];
+    int dev = 0, sms = 0;
+    int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    rc = device_sm_count(&sms);
+    if (rc) return rc;
+    if (dev >= 64 || index >= 16) return fail(GRAV_ECUDA, "device or config index out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    int &slot = cache[dev][c->precision][index][pot ? 1 : 0];
+    if (slot == 0) {
+        int b = 0;
+        rc = check_cuda((cudaError_t)c->occupancy_batched[pot ? 1 : 0](&b),
+                        "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        if (rc) return rc;
+        if (b < 1) return fail(GRAV_ECUDA, "batched force kernel cannot be resident on an SM");
+        slot = b * sms;
+    }
+    *grid = slot;
+    return GRAV_OK;
+}
+
+}  // namespace
+}  // namespace grav
+
+extern "C" int64_t grav_batched_workspace_bytes(const grav_params *p, int32_t n_sys, int64_t n_total)
+{
+    int rc = check_params(p, "grav_batched_workspace_bytes");
+    if (rc) return rc;
+    if (n_sys < 0 || n_sys > GRAV_BATCH_MAX_SYSTEMS || n_total < 0 || n_total > INT32_MAX)
+        return fail(GRAV_EINVAL, "grav_batched_workspace_bytes: n_sys or n_total out of range");
+    int index = 0;
+    const EvalConfig *c = resolve(p, &index);
+    return batch_layout(c, n_sys, n_total).total;
+}
+
+extern "C" int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav_system *systems,
+                                 int64_t n_total, const double *pos, const double *vel,
+                                 const double *mass, const int32_t *idx, const int32_t *n_idx_dev,
+                                 int64_t n_idx_max, double *acc, double *jerk, double *tidal,
+                                 double *pot, double *dt_grav, int32_t *flags_dev, void *workspace,
+                                 int64_t workspace_bytes, void *stream)
+{
+    static const char *who = "grav_eval_batched";
+    int rc = check_params(p, who);
+    if (rc) return rc;
+    if (n_sys < 0 || n_sys > GRAV_BATCH_MAX_SYSTEMS)
+        return fail(GRAV_EINVAL, "%s: n_sys outside [0, %d]", who, GRAV_BATCH_MAX_SYSTEMS);
+    if (n_total < 0 || n_total > INT32_MAX || n_idx_max < 0 || n_idx_max > n_total)
+        return fail(GRAV_EINVAL, "%s: need 0 <= n_idx_max <= n_total < 2^31", who);
+    if (n_sys == 0 || n_total == 0 || n_idx_max == 0) return GRAV_OK;
+    if (!systems || !pos || !vel || !mass || !idx || !acc || !jerk || !tidal)
+        return fail(GRAV_EINVAL, "%s: null array", who);
+    if (p->want_pot && !pot) return fail(GRAV_EINVAL, "%s: want_pot set but pot is NULL", who);
+    if (!workspace || !aligned(workspace, 256))
+        return fail(GRAV_EINVAL, "%s: workspace missing or not 256-byte aligned", who);
+    int index = 0;
+    const EvalConfig *c = resolve(p, &index);
+    const BatchLayout L = batch_layout(c, n_sys, n_total);
+    if (workspace_bytes < L.total)
+        return fail(GRAV_ENOMEM, "%s: workspace of %lld bytes < %lld", who, (long long)workspace_bytes,
+                    (long long)L.total);
+    const bool want_pot = p->want_pot != 0;
+    int grid = 0;
+    rc = batch_grid_for(c, index, want_pot, &grid);
+    if (rc) return rc;
+
+    char *ws = static_cast<char *>(workspace);
+    BatchView b;
+    b.hdr = reinterpret_cast<BatchHeader *>(ws + L.hdr);
+    b.sys = systems;
+    b.tile_off = reinterpret_cast<int32_t *>(ws + L.tile_off);
+    b.idx_lo = reinterpret_cast<int32_t *>(ws + L.idx_lo);
+    b.idx_hi = reinterpret_cast<int32_t *>(ws + L.idx_hi);
+    b.ntb = reinterpret_cast<int32_t *>(ws + L.ntb);
+    b.order = reinterpret_cast<int32_t *>(ws + L.order);
+    b.item_off = reinterpret_cast<int64_t *>(ws + L.item_off);
+    b.n_sys = n_sys;
+    b.pad = 0;
+
+    EvalArgs a;
+    a.n_src = n_total;
+    a.idx = idx;
+    a.n_idx_dev = n_idx_dev;
+    a.n_idx_max = n_idx_max;
+    a.geo = reinterpret_cast<const TileGeom *>(ws + L.geo);
+    a.src = ws + L.src;
+    a.n_tiles = 0;
+    a.max_split = 1;
+    a.grid = grid;
+    a.pad0 = 0;
+    a.part = nullptr;
+    a.part_cap_rows = 0;
+    a.pos = pos;
+    a.vel = vel;
+    a.G = p->G;
+    a.h = p->h;
+    a.sqrt_eta = std::sqrt(p->eta);
+    a.hf = (float)p->h;
+    double h2 = p->h * p->h;
+    float h2f = (float)h2;
+    if ((double)h2f < h2) h2f = std::nextafter(h2f, INFINITY);
+    a.h2f_up = h2f;
+    a.hinvf = (float)(1.0 / p->h);
+    a.pad1 = 0.0f;
+    a.acc = acc;
+    a.jerk = jerk;
+    a.tidal = tidal;
+    a.pot = want_pot ? pot : nullptr;
+    a.dt_grav = dt_grav;
+    a.flags = flags_dev;
+
+    cudaStream_t st = as_stream(stream);
+    const int32_t BT = c->threads * c->kt;
+    batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(b, idx, n_idx_dev, n_idx_max, n_total, c->s, BT,
+                                                   flags_dev);
+    rc = check_launch("grav_eval_batched/plan");
+    if (rc) return rc;
+    c->pack_batched(b, pos, vel, mass, const_cast<TileGeom *>(a.geo), const_cast<void *>(a.src),
+                    flags_dev, (int)L.max_tiles, st);
+    rc = check_launch("grav_eval_batched/pack");
+    if (rc) return rc;
+    c->launch_batched[want_pot ? 1 : 0](a, b, grid, st);
+    return check_launch("grav_eval_batched/eval");
 }

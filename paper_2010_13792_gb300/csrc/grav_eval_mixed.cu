@@ -4,24 +4,34 @@
 
 namespace grav {
 
-#define GRAV_MIXED_CFG(NT, KT, S, MINB, U, SACC)                                              \
-    {GRAV_MIXED, NT, KT, S,                                                                       \
-     {launch_mixed<NT, KT, S, MINB, U, false, SACC>, launch_mixed<NT, KT, S, MINB, U, true, SACC>}, \
-     {occupancy_mixed<NT, KT, S, MINB, U, false, SACC>,                                           \
-      occupancy_mixed<NT, KT, S, MINB, U, true, SACC>},                                           \
-     launch_pack<S, true, true>}
+#define GRAV_MIXED_CFG(NT, KT, S, MINB, U, SACC, PAIR)                                        \
+    {GRAV_MIXED, NT, KT, S, U, SACC,                                                              \
+     {launch_mixed<NT, KT, S, MINB, U, false, SACC, PAIR>,                                        \
+      launch_mixed<NT, KT, S, MINB, U, true, SACC, PAIR>},                                        \
+     {occupancy_mixed<NT, KT, S, MINB, U, false, SACC, PAIR>,                                     \
+      occupancy_mixed<NT, KT, S, MINB, U, true, SACC, PAIR>},                                     \
+     launch_pack<S, true, true, PAIR>,                                                            \
+     {launch_mixed_batched<NT, KT, S, MINB, U, false, SACC, PAIR>,                                \
+      launch_mixed_batched<NT, KT, S, MINB, U, true, SACC, PAIR>},                                \
+     {occupancy_mixed_batched<NT, KT, S, MINB, U, false, SACC, PAIR>,                             \
+      occupancy_mixed_batched<NT, KT, S, MINB, U, true, SACC, PAIR>},                             \
+     launch_pack_batched<S, true, true, PAIR>, PAIR}
 
 // threads, targets per thread, sources per tile, min CTAs per SM (register
-// budget), unroll depth of the Newtonian loop, accumulators in shared memory
+// budget), unroll depth of the Newtonian loop, accumulators in shared memory,
+// paired source layout (two sources per packed FP32x2 instruction)
 static const EvalConfig kMixedConfigs[] = {
-    GRAV_MIXED_CFG(128, 1, 256, 4, 8, false),
-    GRAV_MIXED_CFG(128, 1, 256, 6, 4, true),
-    GRAV_MIXED_CFG(128, 2, 256, 4, 4, true),
-    GRAV_MIXED_CFG(128, 2, 256, 4, 2, true),
-    GRAV_MIXED_CFG(256, 1, 256, 3, 4, true),
-    GRAV_MIXED_CFG(64, 2, 256, 8, 2, true),
-    GRAV_MIXED_CFG(128, 1, 256, 5, 8, true),
-    GRAV_MIXED_CFG(256, 1, 256, 2, 4, false),
+    GRAV_MIXED_CFG(128, 1, 256, 4, 8, false, false),
+    GRAV_MIXED_CFG(128, 1, 256, 6, 4, true, false),
+    GRAV_MIXED_CFG(128, 2, 256, 4, 4, true, false),
+    GRAV_MIXED_CFG(128, 2, 256, 4, 2, true, false),
+    GRAV_MIXED_CFG(256, 1, 256, 3, 4, true, false),
+    GRAV_MIXED_CFG(64, 2, 256, 8, 2, true, false),
+    GRAV_MIXED_CFG(128, 1, 256, 4, 2, false, true),
+    GRAV_MIXED_CFG(128, 1, 256, 4, 4, false, true),
+    GRAV_MIXED_CFG(128, 1, 256, 6, 2, true, true),
+    GRAV_MIXED_CFG(256, 1, 256, 2, 2, false, true),
+    GRAV_MIXED_CFG(128, 1, 256, 5, 4, true, true),
 };
 
 const EvalConfig *mixed_configs(int *count)

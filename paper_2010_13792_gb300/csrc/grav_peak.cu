@@ -34,6 +34,46 @@ fma_peak_kernel(int iters, T a, T b)
     if (s == (T)-1.2345) g_peak_sink = (double)s;
 }
 
+// Packed FP32x2 variant: each __ffma2_rn is two FMAs (four flops).
+__global__ void __launch_bounds__(kPeakThreads)
+fma2_peak_kernel(int iters, float2 a, float2 b)
+{
+    float2 x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = make_float2((threadIdx.x + c) * 1e-3f, (threadIdx.x - c) * 1e-3f);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = __ffma2_rn(x[c], a, b);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c].x + x[c].y;
+    if (s == -1.2345f) g_peak_sink = (double)s;
+}
+
+template <typename T>
+struct PeakKernel {
+    static void launch(int blocks, int iters, cudaStream_t st)
+    {
+        fma_peak_kernel<T><<<blocks, kPeakThreads, 0, st>>>(iters, (T)0.999999, (T)1e-7);
+    }
+    static const void *fn() { return (const void *)fma_peak_kernel<T>; }
+    static constexpr double flops_per_op = 2.0;
+};
+
+template <>
+struct PeakKernel<float2> {
+    static void launch(int blocks, int iters, cudaStream_t st)
+    {
+        fma2_peak_kernel<<<blocks, kPeakThreads, 0, st>>>(iters, make_float2(0.999999f, 0.999998f),
+                                                          make_float2(1e-7f, 2e-7f));
+    }
+    static const void *fn() { return (const void *)fma2_peak_kernel; }
+    static constexpr double flops_per_op = 4.0;
+};
+
 template <typename T>
 int run(double seconds, double *flops, cudaStream_t st)
 {
@@ -41,7 +81,7 @@ int run(double seconds, double *flops, cudaStream_t st)
     int rc = device_sm_count(&sms);
     if (rc) return rc;
     int per_sm = 0;
-    rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_peak_kernel<T>,
+    rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, PeakKernel<T>::fn(),
                                                                    kPeakThreads, 0),
                     "occupancy");
     if (rc) return rc;
@@ -54,18 +94,18 @@ int run(double seconds, double *flops, cudaStream_t st)
         cudaEventDestroy(e0);
         return rc;
     }
-    const T a = (T)0.999999, b = (T)1e-7;
     int iters = 256;
     double best = 0.0, last = 0.0;
     for (int round = 0; round < 8 && rc == GRAV_OK; ++round) {
         cudaEventRecord(e0, st);
-        fma_peak_kernel<T><<<blocks, kPeakThreads, 0, st>>>(iters, a, b);
+        PeakKernel<T>::launch(blocks, iters, st);
         cudaEventRecord(e1, st);
         rc = check_cuda(cudaEventSynchronize(e1), "fma peak kernel");
         if (rc) break;
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
-        const double fl = 2.0 * kChains * kUnroll * (double)iters * blocks * kPeakThreads;
+        const double fl = PeakKernel<T>::flops_per_op * kChains * kUnroll * (double)iters * blocks *
+                          kPeakThreads;
         const double rate = fl / (ms * 1e-3);
         last = rate;
         if (ms > 0.25 * seconds * 1e3) best = std::max(best, rate);
@@ -93,5 +133,6 @@ extern "C" int grav_measure_fma_peak(int32_t precision, double seconds_target, d
         return fail(GRAV_EINVAL, "grav_measure_fma_peak: seconds_target outside (0, 30]");
     if (precision == GRAV_MIXED) return run<float>(seconds_target, flops_per_s, as_stream(stream));
     if (precision == GRAV_F64) return run<double>(seconds_target, flops_per_s, as_stream(stream));
+    if (precision == GRAV_PEAK_F32X2) return run<float2>(seconds_target, flops_per_s, as_stream(stream));
     return fail(GRAV_EINVAL, "grav_measure_fma_peak: bad precision");
 }

@@ -55,7 +55,7 @@ class Params(ctypes.Structure):
 
 class TileInfo(ctypes.Structure):
     _fields_ = [("threads", _c_i32), ("targets_per_thread", _c_i32), ("sources_per_tile", _c_i32),
-                ("targets_per_block", _c_i32)]
+                ("targets_per_block", _c_i32), ("unroll", _c_i32), ("shared_accumulators", _c_i32)]
 
 
 def params(*, G: float = 1.0, h: float, eta: float = 0.01, precision: int = MIXED,
@@ -85,6 +85,10 @@ _SIGS = {
     "grav_eval_active": (ctypes.c_int, [ctypes.POINTER(Params), _c_i64, _c_ptr, _c_ptr, _c_ptr,
                                         _c_ptr, _c_ptr, _c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                         _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr]),
+    "grav_batched_workspace_bytes": (_c_i64, [ctypes.POINTER(Params), _c_i32, _c_i64]),
+    "grav_eval_batched": (ctypes.c_int, [ctypes.POINTER(Params), _c_i32, _c_ptr, _c_i64, _c_ptr,
+                                         _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr, _c_ptr,
+                                         _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr]),
     "grav_backward_workspace_bytes": (_c_i64, [ctypes.POINTER(Params), _c_i64]),
     "grav_eval_backward": (ctypes.c_int, [ctypes.POINTER(Params), _c_i64, _c_ptr, _c_ptr, _c_ptr,
                                           _c_dbl, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
@@ -153,13 +157,27 @@ def version() -> str:
     return lib().grav_version().decode()
 
 
+def default_tile_config(precision: int) -> int:
+    """Index of the library's default tile configuration for a precision."""
+    ti = TileInfo()
+    _err("grav_tile_config", lib().grav_tile_config(precision, -1, ctypes.byref(ti)))
+    key = (ti.threads, ti.targets_per_thread, ti.sources_per_tile, ti.unroll,
+           ti.shared_accumulators)
+    for c in tile_configs(precision):
+        if (c["threads"], c["targets_per_thread"], c["sources_per_tile"], c["unroll"],
+                c["shared_accumulators"]) == key:
+            return c["index"]
+    return -1
+
+
 def tile_configs(precision: int):
     out = []
     for i in range(lib().grav_tile_config_count(precision)):
         ti = TileInfo()
         _err("grav_tile_config", lib().grav_tile_config(precision, i, ctypes.byref(ti)))
         out.append({"index": i, "threads": ti.threads, "targets_per_thread": ti.targets_per_thread,
-                    "sources_per_tile": ti.sources_per_tile, "targets_per_block": ti.targets_per_block})
+                    "sources_per_tile": ti.sources_per_tile, "targets_per_block": ti.targets_per_block,
+                    "unroll": ti.unroll, "shared_accumulators": ti.shared_accumulators})
     return out
 
 
@@ -293,6 +311,42 @@ def eval_active(p: Params, pos, vel, mass, idx, n_idx_dev, n_idx_max: int, acc, 
         _ptr(flags, torch.int32, "flags", (1,), allow_none=True),
         ctypes.c_void_p(buf.data_ptr()), nb, _stream(stream))
     _err("grav_eval_active", rc)
+
+
+BATCH_MAX_SYSTEMS = 16384
+
+
+def batched_workspace_bytes(p: Params, n_sys: int, n_total: int) -> int:
+    r = lib().grav_batched_workspace_bytes(ctypes.byref(p), int(n_sys), int(n_total))
+    if r < 0:
+        _err("grav_batched_workspace_bytes", r)
+    return r
+
+
+def eval_batched(p: Params, systems, pos, vel, mass, idx, n_idx_dev, n_idx_max: int, acc, jerk,
+                 tidal, pot=None, dt_grav=None, flags=None, workspace: Workspace | None = None,
+                 stream=None):
+    """Force evaluation over independent systems in one launch.
+
+    systems: int64 CUDA tensor [n_sys, 2] of (offset, n); idx: ascending
+    global target indices (int32), count *n_idx_dev or n_idx_max."""
+    n = mass.numel()
+    n_sys = systems.shape[0] if systems.dim() == 2 else 0
+    dev = mass.device
+    nb = batched_workspace_bytes(p, n_sys, n)
+    buf = _ws(workspace, "batched", dev).get(nb, dev)
+    rc = lib().grav_eval_batched(
+        ctypes.byref(p), n_sys, _ptr(systems, torch.int64, "systems", (n_sys, 2)), n,
+        _ptr(pos, torch.float64, "pos", (n, 3)), _ptr(vel, torch.float64, "vel", (n, 3)),
+        _ptr(mass, torch.float64, "mass", (n,)), _ptr(idx, torch.int32, "idx"),
+        _ptr(n_idx_dev, torch.int32, "n_idx_dev", (1,), allow_none=True), int(n_idx_max),
+        _ptr(acc, torch.float64, "acc", (n, 3)), _ptr(jerk, torch.float64, "jerk", (n, 3)),
+        _ptr(tidal, torch.float64, "tidal", (n, 6)),
+        _ptr(pot, torch.float64, "pot", (n,), allow_none=True),
+        _ptr(dt_grav, torch.float64, "dt_grav", (n,), allow_none=True),
+        _ptr(flags, torch.int32, "flags", (1,), allow_none=True),
+        ctypes.c_void_p(buf.data_ptr()), nb, _stream(stream))
+    _err("grav_eval_batched", rc)
 
 
 def backward_workspace_bytes(p: Params, n: int) -> int:
