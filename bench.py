@@ -41,6 +41,11 @@ FLOPS_PER_INTERACTION = 56      # FP32 flops of the Newtonian pair body (FFMA = 
 WORKLOAD = "turbulent_cloud_N1048576_h2e-3"
 METRIC = "acc+jerk+tidal interactions/s at N=2^20 (mixed precision)"
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one force-kernel launch from an ncu capture of
+# the default tile configuration on the turbulent cloud with N = 2^18, all
+# active (profiles/eval_mixed_kernel_default_turbulent_cloud_N262144.md).  The
+# traffic is the sources and targets streamed once, so it scales with N.
+TRAFFIC_CAPTURE = {"tile_config": 11, "n": 262144, "bytes": 21950976 + 15993600}
 
 
 def parse():
@@ -288,6 +293,10 @@ def run_ours(args, rank, local, ws):
         "wall_s_timed_region": wall,
     }
 
+    used_cfg = args.tile_config if args.tile_config >= 0 else grav.default_tile_config(grav.MIXED)
+    traffic = None
+    if used_cfg == TRAFFIC_CAPTURE["tile_config"] and args.fraction == 1.0:
+        traffic = TRAFFIC_CAPTURE["bytes"] * args.n / TRAFFIC_CAPTURE["n"]
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peak32 = sms * 128 * 2 * 2070e6 / 1e12       # FP32 lanes x FMA x max SM clock
@@ -297,12 +306,15 @@ def run_ours(args, rank, local, ws):
         "bound": "alu", "kernel": "eval_mixed_kernel (grav_eval_active: pack + direct sum)",
         "achieved": achieved, "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32,
         "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
-        "flops_per_interaction": FLOPS_PER_INTERACTION, "traffic": None,
+        "flops_per_interaction": FLOPS_PER_INTERACTION, "traffic": traffic,
+        "traffic_basis": "ncu dram bytes of the same kernel at N=2^18, scaled by N (see profiles/)",
         "eval_ms_mean": 1e3 * eval_s,
     }
 
     if rank == 0 and not args.no_extras:
         result["extras"] = extras(args, path, dev, sms, peak32, flush)
+        result["extras"]["fp64_path"]["mixed_over_fp64"] = \
+            value / result["extras"]["fp64_path"]["interactions_per_s"]
         result["e2e"] = e2e(args, path, dev, flush)
         result["cpu_baseline"] = cpu_baseline(path, args.cpu_seconds)
     return result
@@ -351,7 +363,8 @@ def extras(args, path, dev, sms, peak32, flush):
     p64 = grav.params(h=H, precision=grav.F64)
     t64 = _time_eval(path, p64, idx, cnt, idx_np.size, 2, flush)
     ips64 = idx_np.size * n / t64
-    out["fp64_path"] = {"interactions_per_s": ips64, "active_fraction": 0.01, "eval_ms": 1e3 * t64}
+    out["fp64_path"] = {"interactions_per_s": ips64, "active_fraction": 0.01, "eval_ms": 1e3 * t64,
+                        "mixed_over_fp64": None}
     # predictor (HBM-bound): all elements active, none due
     ones = torch.ones(n, dtype=torch.uint8, device=dev)
     zeros = torch.zeros(n, dtype=torch.uint8, device=dev)
@@ -367,15 +380,47 @@ def extras(args, path, dev, sms, peak32, flush):
     tp = statistics.median(ts)
     bytes_pred = n * (1 + 1 + 8 + 24 + 24 + 24)
     out["predict"] = {"bytes_per_element": 82, "GB_per_s": bytes_pred / tp / 1e9, "us": tp * 1e6}
+    out["predict_N16777216"] = predict_bandwidth(dev, 1 << 24)
     out["batched_256_systems"] = batched_extra(dev, flush)
     out["adaptive_plummer_131072"] = adaptive_extra(dev)
     try:
         f32 = grav.measure_fma_peak(grav.MIXED, 0.5)
         f64 = grav.measure_fma_peak(grav.F64, 0.5)
-        out["measured_fma_peak_tflops"] = {"fp32": f32 / 1e12, "fp64": f64 / 1e12}
+        f32x2 = grav.measure_fma_peak(grav.PEAK_F32X2, 0.5)
+        out["measured_fma_peak_tflops"] = {"fp32": f32 / 1e12, "fp32x2": f32x2 / 1e12,
+                                           "fp64": f64 / 1e12}
+        # the FP64 path against the measured FP64 FMA peak, same 56-flop tally
+        out["fp64_path"]["frac_of_measured_fp64_peak"] = FLOPS_PER_INTERACTION * ips64 / f64
     except grav.GravError as e:
         out["measured_fma_peak_tflops"] = {"error": str(e)}
     return out
+
+
+def predict_bandwidth(dev, n):
+    """The predictor (HBM-bound) on n elements, all active, none due:
+    82 B per element (flags 2, T_f 8, a_last 24, j_last 24 read; a_out 24
+    written); inputs larger than L2, median of 5 event-timed launches."""
+    import torch
+
+    from paper_2010_13792_gb300 import grav
+    g = torch.Generator(device=dev).manual_seed(5)
+    ones = torch.ones(n, dtype=torch.uint8, device=dev)
+    zeros = torch.zeros(n, dtype=torch.uint8, device=dev)
+    a_last = torch.randn(n, 3, dtype=torch.float64, device=dev, generator=g)
+    j_last = torch.randn(n, 3, dtype=torch.float64, device=dev, generator=g)
+    tf = torch.randint(0, 64, (n,), dtype=torch.int64, device=dev, generator=g)
+    a_out = torch.empty_like(a_last)
+    grav.predict(ones, zeros, a_last, j_last, tf, 2.0**-10, a_out)
+    ts = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        grav.predict(ones, zeros, a_last, j_last, tf, 2.0**-10, a_out)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    t = statistics.median(ts)
+    return {"n": n, "bytes": 82 * n, "us": 1e6 * t, "GB_per_s": 82 * n / t / 1e9}
 
 
 def batched_extra(dev, flush):

@@ -763,11 +763,11 @@ pack_tiles_batched_kernel(const BatchView b, const double *__restrict__ pos,
 // thread); otherwise in registers.
 // ---------------------------------------------------------------------------
 
-template <int NT, int KT, int S, bool POT, bool SACC>
+template <int NT, int KT, int S, bool POT, bool SACC, bool PAIR = false>
 struct MixedSmem {
     static constexpr int BT = NT * KT;
     static constexpr int NC = POT ? kNCPot : kNC;
-    float4 stage[2][2 * S];
+    float4 stage[2][PAIR ? 7 * S / 4 : 2 * S];   // 28 or 32 bytes per source
     float acc[SACC ? NC * 2 * BT : 1];     // [c][hi, lo][BT]
     double x[SACC ? 3 * BT : 1];           // [c][BT]
     uint64_t bar[2];
@@ -789,10 +789,11 @@ __device__ __forceinline__ void init_ring(Sm &sm)
 
 // One work item of the mixed kernel; false if a bounded wait gave up.
 template <int NT, int KT, int S, int U, bool POT, bool SACC, bool PAIR>
-__device__ __forceinline__ bool mixed_item(const EvalArgs &a, MixedSmem<NT, KT, S, POT, SACC> &sm,
-                                           Ring &ring, const ItemSpec &it)
+__device__ __forceinline__ bool mixed_item(const EvalArgs &a,
+                                           MixedSmem<NT, KT, S, POT, SACC, PAIR> &sm, Ring &ring,
+                                           const ItemSpec &it)
 {
-    using Sm = MixedSmem<NT, KT, S, POT, SACC>;
+    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR>;
     constexpr int BT = Sm::BT;
     constexpr int NSTAGE = 2;
     constexpr int NC = Sm::NC;
@@ -992,7 +993,7 @@ template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR
 __global__ void __launch_bounds__(NT, MINB)
 eval_mixed_kernel(const EvalArgs a)
 {
-    using Sm = MixedSmem<NT, KT, S, POT, SACC>;
+    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR>;
     constexpr int BT = Sm::BT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
@@ -1030,7 +1031,7 @@ template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR
 __global__ void __launch_bounds__(NT, MINB)
 eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
 {
-    using Sm = MixedSmem<NT, KT, S, POT, SACC>;
+    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR>;
     constexpr int BT = Sm::BT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
@@ -1286,14 +1287,14 @@ struct EvalConfig {
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
 void launch_mixed(const EvalArgs &a, int grid, cudaStream_t st)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
     eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR><<<grid, NT, bytes, st>>>(a);
 }
 
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
 int occupancy_mixed(int *b)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
     auto k = eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
@@ -1303,14 +1304,14 @@ int occupancy_mixed(int *b)
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
 void launch_mixed_batched(const EvalArgs &a, const BatchView &b, int grid, cudaStream_t st)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
     eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR><<<grid, NT, bytes, st>>>(a, b);
 }
 
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
 int occupancy_mixed_batched(int *b)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
     auto k = eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;

@@ -10,7 +10,7 @@
 namespace grav {
 namespace {
 
-constexpr int kDefaultMixed = 8;
+constexpr int kDefaultMixed = 11;
 constexpr int kDefaultF64 = 0;
 constexpr int64_t kSplitRowsPerSM = 16;   // partial capacity, in target blocks per SM
 

@@ -33,6 +33,7 @@ FLAG_BADINDEX = 4
 
 F64 = 0
 MIXED = 1
+PEAK_F32X2 = 2      # grav_measure_fma_peak only: packed FP32x2 FMA
 
 _c_i64 = ctypes.c_int64
 _c_i32 = ctypes.c_int32
