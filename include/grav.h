@@ -267,6 +267,17 @@ GRAV_API int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav_s
                                double *pot, double *dt_grav, int32_t *flags_dev, void *workspace,
                                int64_t workspace_bytes, void *stream);
 
+/*
+ * grav_selftest_wait_timeout -- failure-detection self-test (not part of the
+ * method).  Launches one CTA whose shared-memory barrier waits for a transfer
+ * that is never issued; the wait gives up after `limit` polls (1..2^20), sets
+ * GRAV_FLAG_TIMEOUT in *flags_dev and the kernel returns.  This call then
+ * synchronises `stream`, reads the flag word and returns GRAV_ETIMEOUT when
+ * the bit is set (the expected outcome) or GRAV_OK.  Nothing faults, traps or
+ * hangs, and the CUDA context remains usable.
+ */
+GRAV_API int grav_selftest_wait_timeout(uint32_t limit, int32_t *flags_dev, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Measurement helper (not part of the method).                               */
 /* ------------------------------------------------------------------------ */

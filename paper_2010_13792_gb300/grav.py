@@ -95,6 +95,7 @@ _SIGS = {
                                           _c_dbl, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                           _c_ptr, _c_i64, _c_ptr]),
     "grav_measure_fma_peak": (ctypes.c_int, [_c_i32, _c_dbl, ctypes.POINTER(_c_dbl), _c_ptr]),
+    "grav_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_uint32, _c_ptr, _c_ptr]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -383,3 +384,9 @@ def measure_fma_peak(precision: int, seconds: float = 0.5, stream=None) -> float
                                      _stream(stream))
     _err("grav_measure_fma_peak", rc)
     return out.value
+
+
+def selftest_wait_timeout(limit: int, flags, stream=None) -> int:
+    """Failure-detection self-test; returns the status (GRAV_ETIMEOUT expected)."""
+    return int(lib().grav_selftest_wait_timeout(int(limit), _ptr(flags, torch.int32, "flags", (1,)),
+                                                _stream(stream)))
