@@ -16,7 +16,9 @@
  *   - the force-update counter (Eq. 3) and update condition
  *     (Eq. updatecondition) on power-of-two time bins (Section 3);
  *   - compaction of the due set in ascending index order;
- *   - the first-order jerk predictor (Eq. jerkupdate) in closed form;
+ *   - the first-order jerk predictor (Eq. jerkupdate) in closed form, and
+ *     the first-order polynomial predictor from logged accelerations
+ *     (Section 2.2);
  *   - the adjoint (reverse-mode) sums for a loss on a and on the potential
  *     energy (not in the paper; derived from Eq. 4 and the tidal tensor).
  *
@@ -272,6 +274,57 @@ int oracle_predict(int64_t n, const uint8_t *active, const uint8_t *due, const d
         double tau = (double)tf_ticks[i] * dt_min;
         for (int c = 0; c < 3; ++c) {
             double inc = j_last[3 * i + c] * tau;
+            a_out[3 * i + c] = a_last[3 * i + c] + inc;
+        }
+    }
+    return 0;
+}
+
+/*
+ * History for the polynomial predictor (Section 2.2: log past g_i values and
+ * extrapolate).  For every element due at `tick`, before its new evaluation
+ * overwrites a_last: dt_prev = (tick - t_last) * dt_min, the gap between its
+ * last two evaluations; t_last = tick; a_prev = a_last, the acceleration of
+ * the evaluation before the new one.  t_last starts at 0 (the evaluation at
+ * tick 0 leaves dt_prev = 0: no history yet).
+ */
+int oracle_push_history(int64_t n, int64_t tick, const uint8_t *due, const double *a_last,
+                        int64_t *t_last, double *a_prev, double *dt_prev, double dt_min)
+{
+    if (n < 0 || tick < 0) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!due[i]) continue;
+        dt_prev[i] = (double)(tick - t_last[i]) * dt_min;
+        t_last[i] = tick;
+        for (int c = 0; c < 3; ++c) a_prev[3 * i + c] = a_last[3 * i + c];
+    }
+    return 0;
+}
+
+/*
+ * First-order polynomial predictor through the last two evaluations
+ * (Section 2.2): for active, not-due elements with dt_prev > 0
+ *     a_out = a_last + (a_last - a_prev) * (tau / dt_prev),  tau = T_f * dt_min,
+ * evaluated as tau, the ratio, the difference, the product and the sum, each
+ * correctly rounded; with dt_prev = 0 (one evaluation so far) a_out = a_last.
+ * Active due elements get a_last; inactive ones are untouched.
+ */
+int oracle_predict_poly(int64_t n, const uint8_t *active, const uint8_t *due, const double *a_last,
+                        const double *a_prev, const double *dt_prev, const int64_t *tf_ticks,
+                        double dt_min, double *a_out)
+{
+    if (n < 0) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!active[i]) continue;
+        if (due[i] || !(dt_prev[i] > 0.0)) {
+            for (int c = 0; c < 3; ++c) a_out[3 * i + c] = a_last[3 * i + c];
+            continue;
+        }
+        double tau = (double)tf_ticks[i] * dt_min;
+        double frac = tau / dt_prev[i];
+        for (int c = 0; c < 3; ++c) {
+            double diff = a_last[3 * i + c] - a_prev[3 * i + c];
+            double inc = diff * frac;
             a_out[3 * i + c] = a_last[3 * i + c] + inc;
         }
     }

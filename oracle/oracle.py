@@ -72,6 +72,12 @@ def load(path: str | None = None):
         lib.oracle_predict.argtypes = [ctypes.c_int64, _u8p, _u8p, _dp, _dp, _i64p,
                                        ctypes.c_double, _dp]
         lib.oracle_predict.restype = ctypes.c_int
+        lib.oracle_push_history.argtypes = [ctypes.c_int64, ctypes.c_int64, _u8p, _dp, _i64p, _dp,
+                                            _dp, ctypes.c_double]
+        lib.oracle_push_history.restype = ctypes.c_int
+        lib.oracle_predict_poly.argtypes = [ctypes.c_int64, _u8p, _u8p, _dp, _dp, _dp, _i64p,
+                                            ctypes.c_double, _dp]
+        lib.oracle_predict_poly.restype = ctypes.c_int
         lib.oracle_assign_bins.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                            ctypes.c_double, _u8p, _dp, _dp, _i8p]
         lib.oracle_assign_bins.restype = ctypes.c_int
@@ -181,6 +187,36 @@ def predict(active, due, a_last, j_last, tf_ticks, dt_min, a_out, lib=None):
                                float(dt_min), _p(out, _dp))
     if rc != 0:
         raise ValueError("oracle_predict: bad arguments")
+    return out
+
+
+def push_history(tick, due, a_last, t_last, a_prev, dt_prev, dt_min, lib=None):
+    """Log the previous evaluation of due elements; returns (t_last, a_prev, dt_prev)."""
+    due = _c(due, np.uint8)
+    a_last = _c(a_last, np.float64)
+    tl = np.array(t_last, dtype=np.int64, copy=True)
+    ap = np.array(a_prev, dtype=np.float64, copy=True)
+    dp = np.array(dt_prev, dtype=np.float64, copy=True)
+    rc = (lib or load()).oracle_push_history(due.shape[0], int(tick), _p(due, _u8p), _p(a_last, _dp),
+                                             _p(tl, _i64p), _p(ap, _dp), _p(dp, _dp), float(dt_min))
+    if rc != 0:
+        raise ValueError("oracle_push_history: bad arguments")
+    return tl, ap, dp
+
+
+def predict_poly(active, due, a_last, a_prev, dt_prev, tf_ticks, dt_min, a_out, lib=None):
+    active = _c(active, np.uint8)
+    due = _c(due, np.uint8)
+    a_last = _c(a_last, np.float64)
+    a_prev = _c(a_prev, np.float64)
+    dt_prev = _c(dt_prev, np.float64)
+    tf = _c(tf_ticks, np.int64)
+    out = np.array(a_out, dtype=np.float64, copy=True)
+    rc = (lib or load()).oracle_predict_poly(active.shape[0], _p(active, _u8p), _p(due, _u8p),
+                                             _p(a_last, _dp), _p(a_prev, _dp), _p(dt_prev, _dp),
+                                             _p(tf, _i64p), float(dt_min), _p(out, _dp))
+    if rc != 0:
+        raise ValueError("oracle_predict_poly: bad arguments")
     return out
 
 

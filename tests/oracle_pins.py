@@ -516,6 +516,68 @@ def pin_predictor(lib):
     assert np.array_equal(out2, keep)
 
 
+def pin_poly_history(lib):
+    """The logged history equals a brute-force record of evaluation ticks."""
+    g = ics.rng(46)
+    n, dt_min = 40, 2.0**-10
+    t_last = np.zeros(n, np.int64)
+    a_prev = np.zeros((n, 3))
+    dt_prev = np.zeros(n)
+    evals = [[] for _ in range(n)]                 # (tick, acceleration) per element
+    a_last = g.normal(size=(n, 3))
+    for tick in range(0, 60):
+        due = (g.uniform(size=n) < 0.3).astype(np.uint8) if tick else np.ones(n, np.uint8)
+        t_last, a_prev, dt_prev = O.push_history(tick, due, a_last, t_last, a_prev, dt_prev, dt_min,
+                                                  lib=lib)
+        new = g.normal(size=(n, 3))
+        a_last = np.where(due[:, None] == 1, new, a_last)
+        for i in np.flatnonzero(due):
+            evals[i].append((tick, new[i].copy()))
+        for i in range(n):
+            if len(evals[i]) >= 2:
+                (t0, a0), (t1, _) = evals[i][-2], evals[i][-1]
+                assert t_last[i] == t1 and dt_prev[i] == (t1 - t0) * dt_min
+                assert np.array_equal(a_prev[i], a0)
+            else:
+                assert dt_prev[i] == 0.0
+
+
+def pin_poly_predictor(lib):
+    """Linear extrapolation through the last two evaluations: exact on a
+    field linear in time; error c tau (tau + Delta) on a(t) = c t^2; the
+    constant a_last with no history; due elements get a_last."""
+    g = ics.rng(47)
+    n, dt_min = 64, 2.0**-10
+    gap = g.integers(1, 40, n)                         # Delta in ticks
+    t1 = g.integers(40, 200, n)
+    t0 = t1 - gap
+    tau = g.integers(0, 50, n).astype(np.int64)        # T_f
+    a0, j = g.normal(size=(n, 3)), g.normal(size=(n, 3))
+    lin = lambda t: a0 + j * (t * dt_min)[:, None]
+    active = np.ones(n, np.uint8)
+    due = np.zeros(n, np.uint8)
+    out = O.predict_poly(active, due, lin(t1), lin(t0), gap * dt_min, tau, dt_min,
+                         np.zeros((n, 3)), lib=lib)
+    assert np.allclose(out, lin(t1 + tau), rtol=1e-12, atol=1e-12)
+    c = g.normal(size=(n, 3))
+    quad = lambda t: c * ((t * dt_min) ** 2)[:, None]
+    out = O.predict_poly(active, due, quad(t1), quad(t0), gap * dt_min, tau, dt_min,
+                         np.zeros((n, 3)), lib=lib)
+    want_err = c * ((tau * dt_min) * ((tau + gap) * dt_min))[:, None]
+    assert np.allclose(quad(t1 + tau) - out, want_err, rtol=1e-9, atol=1e-15)
+    out = O.predict_poly(active, due, lin(t1), lin(t0), np.zeros(n), tau, dt_min,
+                         np.zeros((n, 3)), lib=lib)
+    assert np.array_equal(out, lin(t1))
+    due[::3] = 1
+    out = O.predict_poly(active, due, lin(t1), lin(t0), gap * dt_min, tau, dt_min,
+                         np.zeros((n, 3)), lib=lib)
+    assert np.array_equal(out[::3], lin(t1)[::3])
+    keep = np.full((n, 3), 5.0)
+    out = O.predict_poly(np.zeros(n, np.uint8), due, lin(t1), lin(t0), gap * dt_min, tau, dt_min,
+                         keep, lib=lib)
+    assert np.array_equal(out, keep)
+
+
 # ---------------------------------------------------------------------------
 # Adjoint
 # ---------------------------------------------------------------------------
@@ -557,5 +619,5 @@ ALL_PINS = [
     pin_kernel_vs_cas, pin_kernel_limits, pin_kernel_identity_g, pin_brute_force, pin_two_body,
     pin_momentum_balance, pin_trace_density, pin_cube_symmetry, pin_scaling, pin_jerk_fd,
     pin_tidal_fd, pin_tidal_dt, pin_update_counts, pin_reverts_exactly, pin_bins, pin_compact,
-    pin_predictor, pin_adjoint_fd,
+    pin_predictor, pin_poly_history, pin_poly_predictor, pin_adjoint_fd,
 ]

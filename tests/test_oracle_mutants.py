@@ -44,6 +44,11 @@ MUTANTS = {
     "bin_round_up": ("if (mm > mi) k += 1;", "if (mm >= mi) k += 1;"),
     "bin_no_align": ("if (k < k_align) k = k_align;", ";"),
     "bin_hydro_ignored": ("if (dt_hydro && dt_hydro[i] < dt) dt = dt_hydro[i];", ";"),
+    "poly_slope_sign": ("double diff = a_last[3 * i + c] - a_prev[3 * i + c];",
+                        "double diff = a_prev[3 * i + c] - a_last[3 * i + c];"),
+    "poly_gap_wrong": ("dt_prev[i] = (double)(tick - t_last[i]) * dt_min;",
+                       "dt_prev[i] = (double)(tick - t_last[i] + 1) * dt_min;"),
+    "poly_no_log": ("for (int c = 0; c < 3; ++c) a_prev[3 * i + c] = a_last[3 * i + c];", ";"),
     "adj_mass_sign": ("nadd(&mb, -f * da);", "nadd(&mb, f * da);"),
     "adj_g_term": ("nadd(&xb[c], f * ab[c] + g * d[c] * da);", "nadd(&xb[c], f * ab[c]);"),
     "adj_tidal_transposed": ("ta[0] = t6[0] * ak[0] + t6[3] * ak[1] + t6[4] * ak[2];",
