@@ -507,6 +507,18 @@ def adaptive_extra(dev):
     s, ad = runs["standard_qf0"], runs["adaptive_qf0.5"]
     res["speedup"] = res["standard_qf0"]["ms_per_64_substeps"] / res["adaptive_qf0.5"]["ms_per_64_substeps"]
     res["median_position_difference"] = float((ad.pos - s.pos).norm(dim=1).median().item())
+    # the paper's predictor ablation (q_f = 1/2): none, linear polynomial, jerk
+    abl = {}
+    for mode in ("none", "poly", "jerk"):
+        it = AdaptiveIntegrator(pos, vel, mass, h=1e-3, q_f=0.5, k_max=6, dt_max=2.0**-4,
+                                precision=grav.MIXED, predictor=mode)
+        e0 = sum(it.energy())
+        it.run(64)
+        err = it.predictor_error()
+        abl[mode] = {"predicted_a_rel_error": err[mode],
+                     "rel_energy_change": abs(sum(it.energy()) - e0) / abs(e0),
+                     "work_ratio": it.work_ratio()}
+    res["predictor_ablation"] = abl
     return res
 
 

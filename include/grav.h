@@ -178,6 +178,36 @@ GRAV_API int grav_predict(int64_t n, const uint8_t *active, const uint8_t *due, 
                  void *stream);
 
 /*
+ * grav_push_history -- log past accelerations for the polynomial predictor
+ * (Section 2.2: "logging some number of past g_i values").  For every
+ * element with due[i] != 0, called after grav_select_due and BEFORE the new
+ * evaluation overwrites a_last:
+ *     dt_prev[i] = (tick - t_last[i]) * dt_min   (gap between its last two
+ *                                                 evaluations; one rounding)
+ *     t_last[i]  = tick
+ *     a_prev[i]  = a_last[i]                      ([n][3])
+ * t_last int64[n] (in/out) starts at 0; dt_prev f64[n] and a_prev (out) are
+ * only written for due elements.  a_prev may not alias a_last.
+ */
+GRAV_API int grav_push_history(int64_t n, int64_t tick, const uint8_t *due, const double *a_last,
+                               int64_t *t_last, double *a_prev, double *dt_prev, double dt_min,
+                               void *stream);
+
+/*
+ * grav_predict_poly -- the first-order polynomial predictor of Section 2.2,
+ * the paper's alternative to the jerk: for active, not-due elements with
+ * dt_prev > 0,
+ *     a_out = a_last + (a_last - a_prev) * (tau / dt_prev),  tau = T_f dt_min
+ * (tau, the ratio, the difference, the product and the sum each correctly
+ * rounded, no fused multiply-add); with dt_prev = 0 (a single evaluation so
+ * far) and for active due elements a_out = a_last; inactive elements are not
+ * written.  a_out may alias neither a_last nor a_prev.
+ */
+GRAV_API int grav_predict_poly(int64_t n, const uint8_t *active, const uint8_t *due,
+                               const double *a_last, const double *a_prev, const double *dt_prev,
+                               const int64_t *tf_ticks, double dt_min, double *a_out, void *stream);
+
+/*
  * grav_assign_bins -- Section 2's dt_i = min(dt_grav_i, dt_hydro_i) placed on
  * Section 3's power-of-two bins, for elements active at `tick`.
  * The target bin is the smallest k in [0, k_max] with dt_max * 2^-k <= dt_i

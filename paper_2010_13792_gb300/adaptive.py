@@ -26,10 +26,13 @@ from . import grav
 class AdaptiveIntegrator:
     def __init__(self, pos, vel, mass, *, h: float, q_f: float, k_max: int = 6,
                  dt_max: float = 2.0**-4, eta: float = 0.01, G: float = 1.0,
-                 precision: int = grav.MIXED, dt_hydro=None, predictor: bool = True,
+                 precision: int = grav.MIXED, dt_hydro=None, predictor="jerk",
                  systems=None, tile_config: int = -1, device=None):
-        """systems: optional [n_sys, 2] (offset, n) of independent systems packed
-        back to back; their forces come from one batched launch per tick."""
+        """predictor: "jerk" (Eq. jerkupdate), "poly" (first-order polynomial
+        through the last two logged evaluations, Section 2.2) or "none" (keep the
+        last evaluated acceleration).  systems: optional [n_sys, 2] (offset, n)
+        of independent systems packed back to back; their forces come from one
+        batched launch per tick."""
         device = device or torch.device("cuda", torch.cuda.current_device())
         f64 = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()
         self.dev = device
@@ -37,6 +40,12 @@ class AdaptiveIntegrator:
         n = self.n = self.mass.numel()
         self.h, self.q_f, self.k_max, self.dt_max, self.G = h, q_f, k_max, dt_max, G
         self.dt_min = dt_max * 2.0**-k_max
+        if predictor is True:
+            predictor = "jerk"
+        elif predictor is False or predictor is None:
+            predictor = "none"
+        if predictor not in ("jerk", "poly", "none"):
+            raise ValueError(f"unknown predictor {predictor!r}")
         self.predictor = predictor
         self.params = grav.params(G=G, h=h, eta=eta, precision=precision, tile_config=tile_config)
         self.systems = None if systems is None else \
@@ -55,6 +64,10 @@ class AdaptiveIntegrator:
         self.count = torch.zeros(1, dtype=torch.int32, device=device)
         self.a_kick = torch.zeros(n, 3, dtype=torch.float64, device=device)
         self.zero_j = torch.zeros_like(self.acc)
+        # history of the polynomial predictor
+        self.t_last = torch.zeros(n, dtype=torch.int64, device=device)
+        self.a_prev = torch.zeros(n, 3, dtype=torch.float64, device=device)
+        self.dt_prev = torch.zeros(n, dtype=torch.float64, device=device)
         # device-side work counters: sum of n_due and of n_active over ticks
         self.n_due_total = torch.zeros(1, dtype=torch.int64, device=device)
         self.n_active_total = torch.zeros(1, dtype=torch.int64, device=device)
@@ -78,6 +91,9 @@ class AdaptiveIntegrator:
         g = grav
         g.select_due(tick, self.k_max, self.bins, self.tf, self.dt_grav, self.q_f, self.dt_min,
                      self.active, self.due)
+        if self.predictor == "poly":
+            g.push_history(tick, self.due, self.acc, self.t_last, self.a_prev, self.dt_prev,
+                           self.dt_min)
         g.compact_active(self.due, self.idx, self.count, workspace=self.ws_compact)
         if self.systems is None:
             g.eval_active(self.params, self.pos, self.vel, self.mass, self.idx, self.count, self.n,
@@ -86,8 +102,13 @@ class AdaptiveIntegrator:
             g.eval_batched(self.params, self.systems, self.pos, self.vel, self.mass, self.idx,
                            self.count, self.n, self.acc, self.jerk, self.tidal, None, self.dt_grav,
                            workspace=self.ws_eval)
-        g.predict(self.active, self.due, self.acc, self.jerk if self.predictor else self.zero_j,
-                  self.tf, self.dt_min, self.a_kick)
+        if self.predictor == "poly":
+            g.predict_poly(self.active, self.due, self.acc, self.a_prev, self.dt_prev, self.tf,
+                           self.dt_min, self.a_kick)
+        else:
+            g.predict(self.active, self.due, self.acc,
+                      self.jerk if self.predictor == "jerk" else self.zero_j, self.tf, self.dt_min,
+                      self.a_kick)
         self.n_due_total += self.count.to(torch.int64)
         self.n_active_total += self.active.sum(dtype=torch.int64)
 
@@ -178,6 +199,52 @@ class AdaptiveIntegrator:
         kin = 0.5 * (self.mass * (self.vel * self.vel).sum(1)).sum()
         w = 0.5 * (self.mass * pot).sum()
         return float(kin.item()), float(w.item())
+
+    def predictor_error(self):
+        """Relative error |a_pred - a|/|a| of the predicted acceleration of every
+        element not re-evaluated at the current tick, against a fresh FP64
+        evaluation at the current positions; call it right after a tick that
+        is a multiple of 2^k_max has run (every element is then at a step
+        boundary, so T_f is its exact time since the last evaluation).  Returns quantiles for
+        this integrator's predictor and, on the same state, for the other
+        predictors whose inputs it keeps."""
+        if self.tick == 0 or (self.tick - 1) % (1 << self.k_max) != 0:
+            raise RuntimeError("call right after a tick that is a multiple of 2^k_max")
+        n = self.n
+        p = grav.params(G=self.G, h=self.h, precision=grav.F64)
+        acc = torch.empty(n, 3, dtype=torch.float64, device=self.dev)
+        jerk = torch.empty_like(acc)
+        tid = torch.empty(n, 6, dtype=torch.float64, device=self.dev)
+        if self.systems is None:
+            grav.eval_active(p, self.pos, self.vel, self.mass, None, None, n, acc, jerk, tid)
+        else:
+            idx = torch.arange(n, dtype=torch.int32, device=self.dev)
+            grav.eval_batched(p, self.systems, self.pos, self.vel, self.mass, idx, None, n, acc,
+                              jerk, tid)
+        ones = torch.ones(n, dtype=torch.uint8, device=self.dev)
+        zeros = torch.zeros(n, dtype=torch.uint8, device=self.dev)
+        stale = self.due == 0
+        preds = {"none": self.acc.clone()}
+        out = torch.empty_like(acc)
+        grav.predict(ones, zeros, self.acc, self.jerk, self.tf, self.dt_min, out)
+        preds["jerk"] = out.clone()
+        if self.predictor == "poly":
+            grav.predict_poly(ones, zeros, self.acc, self.a_prev, self.dt_prev, self.tf, self.dt_min,
+                              out)
+            preds["poly"] = out.clone()
+        res = {}
+        ref = acc[stale]
+        nrm = ref.norm(dim=1)
+        for k, a in preds.items():
+            e = ((a[stale] - ref).norm(dim=1) / nrm).cpu()
+            if e.numel() == 0:
+                res[k] = None
+                continue
+            q = torch.quantile(e, torch.tensor([0.5, 0.9, 0.99], dtype=e.dtype))
+            res[k] = {"median": float(q[0]), "p90": float(q[1]), "p99": float(q[2]),
+                      "max": float(e.max()), "elements": int(e.numel())}
+        res["mode"] = self.predictor
+        return res
 
     def work_ratio(self) -> float:
         """sum(n_due) / sum(n_active): fraction of the standard scheme's force work."""

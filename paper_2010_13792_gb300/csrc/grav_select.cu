@@ -255,6 +255,45 @@ predict_pair_kernel(int64_t n, const uint8_t *__restrict__ active, const uint8_t
     }
 }
 
+// ---- polynomial predictor (Section 2.2) -----------------------------------
+
+// Log the evaluation before the new one for every due element: the gap
+// between its last two evaluations, its tick and its acceleration.
+__global__ void __launch_bounds__(kElemThreads)
+push_history_kernel(int64_t n, int64_t tick, const uint8_t *__restrict__ due,
+                    const double *__restrict__ a_last, int64_t *__restrict__ t_last,
+                    double *__restrict__ a_prev, double *__restrict__ dt_prev, double dt_min)
+{
+    const int64_t i = (int64_t)blockIdx.x * kElemThreads + threadIdx.x;
+    if (i >= n || !due[i]) return;
+    dt_prev[i] = __dmul_rn(__ll2double_rn(tick - t_last[i]), dt_min);
+    t_last[i] = tick;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a_prev[3 * i + c] = a_last[3 * i + c];
+}
+
+// Linear extrapolation through the last two evaluations, flattened over the
+// 3n components (every operation correctly rounded, no fusion).
+__global__ void __launch_bounds__(kElemThreads)
+predict_poly_kernel(int64_t n3, const uint8_t *__restrict__ active, const uint8_t *__restrict__ due,
+                    const double *__restrict__ a_last, const double *__restrict__ a_prev,
+                    const double *__restrict__ dt_prev, const int64_t *__restrict__ tf_ticks,
+                    double dt_min, double *__restrict__ a_out)
+{
+    const int64_t q = (int64_t)blockIdx.x * kElemThreads + threadIdx.x;
+    if (q >= n3) return;
+    const int64_t i = q / 3;
+    if (!active[i]) return;
+    double a = a_last[q];
+    const double gap = dt_prev[i];
+    if (!due[i] && gap > 0.0) {
+        const double tau = __dmul_rn(__ll2double_rn(tf_ticks[i]), dt_min);
+        const double frac = __ddiv_rn(tau, gap);
+        a = __dadd_rn(a, __dmul_rn(__dsub_rn(a, a_prev[q]), frac));
+    }
+    a_out[q] = a;
+}
+
 // ---- bins -----------------------------------------------------------------
 
 __device__ __forceinline__ int32_t target_bin(double dt, double dt_max, int32_t k_max)
@@ -468,4 +507,35 @@ extern "C" int grav_compact_active_noalloc(int64_t n, const uint8_t *flags, int3
     if (rc) return rc;
     compact_scatter_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(n, flags, vec_ok, counts, idx_out);
     return check_launch("grav_compact_active_noalloc/scatter");
+}
+
+extern "C" int grav_push_history(int64_t n, int64_t tick, const uint8_t *due, const double *a_last,
+                                 int64_t *t_last, double *a_prev, double *dt_prev, double dt_min,
+                                 void *stream)
+{
+    if (n < 0 || tick < 0) return fail(GRAV_EINVAL, "grav_push_history: n or tick < 0");
+    if (!(dt_min > 0.0) || isinf(dt_min)) return fail(GRAV_EINVAL, "grav_push_history: dt_min must be finite and > 0");
+    if (n == 0) return GRAV_OK;
+    if (!due || !a_last || !t_last || !a_prev || !dt_prev)
+        return fail(GRAV_EINVAL, "grav_push_history: null array");
+    if (a_prev == a_last) return fail(GRAV_EINVAL, "grav_push_history: a_prev aliases a_last");
+    push_history_kernel<<<elem_blocks(n), kElemThreads, 0, as_stream(stream)>>>(
+        n, tick, due, a_last, t_last, a_prev, dt_prev, dt_min);
+    return check_launch("grav_push_history");
+}
+
+extern "C" int grav_predict_poly(int64_t n, const uint8_t *active, const uint8_t *due,
+                                 const double *a_last, const double *a_prev, const double *dt_prev,
+                                 const int64_t *tf_ticks, double dt_min, double *a_out, void *stream)
+{
+    if (n < 0) return fail(GRAV_EINVAL, "grav_predict_poly: n < 0");
+    if (!(dt_min > 0.0) || isinf(dt_min)) return fail(GRAV_EINVAL, "grav_predict_poly: dt_min must be finite and > 0");
+    if (n == 0) return GRAV_OK;
+    if (!active || !due || !a_last || !a_prev || !dt_prev || !tf_ticks || !a_out)
+        return fail(GRAV_EINVAL, "grav_predict_poly: null array");
+    if (a_out == a_last || a_out == a_prev) return fail(GRAV_EINVAL, "grav_predict_poly: a_out aliases an input");
+    const int64_t n3 = 3 * n;
+    predict_poly_kernel<<<elem_blocks(n3), kElemThreads, 0, as_stream(stream)>>>(
+        n3, active, due, a_last, a_prev, dt_prev, tf_ticks, dt_min, a_out);
+    return check_launch("grav_predict_poly");
 }

@@ -80,6 +80,10 @@ _SIGS = {
     "grav_compact_active_noalloc": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr]),
     "grav_predict": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_dbl, _c_ptr,
                                     _c_ptr]),
+    "grav_push_history": (ctypes.c_int, [_c_i64, _c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+                                         _c_dbl, _c_ptr]),
+    "grav_predict_poly": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+                                         _c_dbl, _c_ptr, _c_ptr]),
     "grav_assign_bins": (ctypes.c_int, [_c_i64, _c_i64, _c_i32, _c_dbl, _c_ptr, _c_ptr, _c_ptr,
                                         _c_ptr, _c_ptr]),
     "grav_eval_workspace_bytes": (_c_i64, [ctypes.POINTER(Params), _c_i64, _c_i64]),
@@ -269,6 +273,25 @@ def predict(active, due, a_last, j_last, tf_ticks, dt_min: float, a_out, stream=
         _ptr(tf_ticks, torch.int64, "tf_ticks", (n,)), float(dt_min),
         _ptr(a_out, torch.float64, "a_out", (n, 3)), _stream(stream))
     _err("grav_predict", rc)
+
+
+def push_history(tick: int, due, a_last, t_last, a_prev, dt_prev, dt_min: float, stream=None):
+    n = due.numel()
+    rc = lib().grav_push_history(
+        n, int(tick), _ptr(due, torch.uint8, "due", (n,)), _ptr(a_last, torch.float64, "a_last", (n, 3)),
+        _ptr(t_last, torch.int64, "t_last", (n,)), _ptr(a_prev, torch.float64, "a_prev", (n, 3)),
+        _ptr(dt_prev, torch.float64, "dt_prev", (n,)), float(dt_min), _stream(stream))
+    _err("grav_push_history", rc)
+
+
+def predict_poly(active, due, a_last, a_prev, dt_prev, tf_ticks, dt_min: float, a_out, stream=None):
+    n = active.numel()
+    rc = lib().grav_predict_poly(
+        n, _ptr(active, torch.uint8, "active", (n,)), _ptr(due, torch.uint8, "due", (n,)),
+        _ptr(a_last, torch.float64, "a_last", (n, 3)), _ptr(a_prev, torch.float64, "a_prev", (n, 3)),
+        _ptr(dt_prev, torch.float64, "dt_prev", (n,)), _ptr(tf_ticks, torch.int64, "tf_ticks", (n,)),
+        float(dt_min), _ptr(a_out, torch.float64, "a_out", (n, 3)), _stream(stream))
+    _err("grav_predict_poly", rc)
 
 
 def assign_bins(tick: int, k_max: int, dt_max: float, active, dt_grav, dt_hydro, bin_, stream=None):

@@ -93,3 +93,27 @@ def test_batched_loop_graph_of_100_substeps(precision):
     c.params.max_split = 1
     c.run(99)
     assert torch.equal(c.pos, a.pos[sl]) and torch.equal(c.vel, a.vel[sl])
+
+
+def test_predictor_variants_ablation():
+    """The paper's ablation on a Plummer sphere: no predictor, the linear
+    polynomial from logged evaluations and the jerk.  Both predictors beat
+    keeping the last evaluation; the graph replays the poly loop exactly."""
+    n = 1 << 13
+    pos, vel, mass = ics.plummer(n, seed=ics.BASE_SEED + 1)
+    kw = dict(h=1e-3, q_f=1.0, k_max=5, dt_max=2.0**-4, precision=grav.F64)
+    err = {}
+    for mode in ("none", "poly", "jerk"):
+        it = AdaptiveIntegrator(pos, vel, mass, predictor=mode, **kw)
+        it.run(3 * 32)                           # last tick run: 96, a cycle boundary
+        r = it.predictor_error()
+        err[mode] = r[mode]["median"]
+    assert err["jerk"] < 0.5 * err["none"] and err["poly"] < err["none"], err
+    a = AdaptiveIntegrator(pos, vel, mass, predictor="poly", **kw)
+    a.run(2 * 32)
+    b = AdaptiveIntegrator(pos, vel, mass, predictor="poly", **kw)
+    b.start()
+    b.capture_cycle()
+    b.replay(2)
+    torch.cuda.synchronize()
+    assert torch.equal(a.vel, b.vel) and torch.equal(a.a_prev, b.a_prev)

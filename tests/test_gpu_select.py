@@ -144,3 +144,35 @@ def test_assign_bins_bitexact(n):
                              None if hyd is None else T(hyd), bt)
             torch.cuda.synchronize()
             assert np.array_equal(bt.cpu().numpy(), want), tick
+
+
+@pytest.mark.parametrize("n", [1, 999, (1 << 20) + 3])
+def test_polynomial_predictor_bitexact(n):
+    """Logged history and the first-order polynomial predictor against the
+    oracle over a sequence of ticks with random due sets (byte for byte)."""
+    g = ics.rng(600 + n)
+    dt_min = 2.0**-11
+    t_last = np.zeros(n, np.int64)
+    a_prev = np.zeros((n, 3))
+    dt_prev = np.zeros(n)
+    a_last = g.normal(size=(n, 3))
+    tl_t, ap_t, dp_t = T(t_last, torch.int64), T(a_prev), T(dt_prev)
+    for tick in (0, 3, 7, 8, 20, 33):
+        due = (g.uniform(size=n) < 0.4).astype(np.uint8) if tick else np.ones(n, np.uint8)
+        t_last, a_prev, dt_prev = O.push_history(tick, due, a_last, t_last, a_prev, dt_prev, dt_min)
+        grav.push_history(tick, T(due, torch.uint8), T(a_last), tl_t, ap_t, dp_t, dt_min)
+        torch.cuda.synchronize()
+        assert np.array_equal(tl_t.cpu().numpy(), t_last)
+        assert np.array_equal(ap_t.cpu().numpy(), a_prev)
+        assert np.array_equal(dp_t.cpu().numpy().view(np.uint64), dt_prev.view(np.uint64))
+        a_last = np.where(due[:, None] == 1, g.normal(size=(n, 3)), a_last)
+        active = (g.uniform(size=n) < 0.8).astype(np.uint8)
+        due2 = ((g.uniform(size=n) < 0.2) & (active == 1)).astype(np.uint8)
+        tf = g.integers(0, 30, n).astype(np.int64)
+        init = g.normal(size=(n, 3))
+        want = O.predict_poly(active, due2, a_last, a_prev, dt_prev, tf, dt_min, init)
+        out = T(init)
+        grav.predict_poly(T(active, torch.uint8), T(due2, torch.uint8), T(a_last), ap_t, dp_t,
+                          T(tf, torch.int64), dt_min, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint64), want.view(np.uint64))
