@@ -219,8 +219,10 @@ static int is_active(int64_t tick, int32_t k_max, int32_t k)
  */
 int oracle_select_due(int64_t n, int64_t tick, int32_t k_max, const int8_t *bin,
                       int64_t *tf_ticks, const double *dt_grav, double q_f, double dt_min,
-                      uint8_t *active, uint8_t *due)
+                      uint8_t *active, uint8_t *due, int64_t *elapsed_ticks)
 {
+    /* elapsed_ticks (nullable): for due elements, T_f before the reset, i.e. the
+     * time since the previous evaluation in ticks; untouched otherwise. */
     if (n < 0 || k_max < 0 || k_max > 62 || tick < 0) return -1;
     for (int64_t i = 0; i < n; ++i) {
         int32_t k = bin[i];
@@ -236,6 +238,7 @@ int oracle_select_due(int64_t n, int64_t tick, int32_t k_max, const int8_t *bin,
         double need = q_f * dt_grav[i];
         if (elapsed >= need) {
             due[i] = 1;
+            if (elapsed_ticks) elapsed_ticks[i] = tf_ticks[i];
             tf_ticks[i] = 0;
         } else {
             due[i] = 0;
@@ -282,20 +285,20 @@ int oracle_predict(int64_t n, const uint8_t *active, const uint8_t *due, const d
 
 /*
  * History for the polynomial predictor (Section 2.2: log past g_i values and
- * extrapolate).  For every element due at `tick`, before its new evaluation
- * overwrites a_last: dt_prev = (tick - t_last) * dt_min, the gap between its
- * last two evaluations; t_last = tick; a_prev = a_last, the acceleration of
- * the evaluation before the new one.  t_last starts at 0 (the evaluation at
- * tick 0 leaves dt_prev = 0: no history yet).
+ * extrapolate).  For every element due now, before its new evaluation
+ * overwrites a_last: a_prev = a_last (the acceleration of the evaluation
+ * before the new one) and dt_prev = elapsed * dt_min, the gap between the two,
+ * where elapsed is T_f at the moment it became due (from the selection).  An
+ * element never evaluated before (dt_grav == 0) gets dt_prev = 0: no history.
  */
-int oracle_push_history(int64_t n, int64_t tick, const uint8_t *due, const double *a_last,
-                        int64_t *t_last, double *a_prev, double *dt_prev, double dt_min)
+int oracle_push_history(int64_t n, const uint8_t *due, const int64_t *elapsed_ticks,
+                        const double *dt_grav, const double *a_last, double *a_prev,
+                        double *dt_prev, double dt_min)
 {
-    if (n < 0 || tick < 0) return -1;
+    if (n < 0) return -1;
     for (int64_t i = 0; i < n; ++i) {
         if (!due[i]) continue;
-        dt_prev[i] = (double)(tick - t_last[i]) * dt_min;
-        t_last[i] = tick;
+        dt_prev[i] = (dt_grav[i] == 0.0) ? 0.0 : (double)elapsed_ticks[i] * dt_min;
         for (int c = 0; c < 3; ++c) a_prev[3 * i + c] = a_last[3 * i + c];
     }
     return 0;

@@ -65,15 +65,16 @@ def load(path: str | None = None):
                                     _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
         lib.oracle_eval.restype = ctypes.c_int
         lib.oracle_select_due.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _i8p,
-                                          _i64p, _dp, ctypes.c_double, ctypes.c_double, _u8p, _u8p]
+                                          _i64p, _dp, ctypes.c_double, ctypes.c_double, _u8p, _u8p,
+                                          _i64p]
         lib.oracle_select_due.restype = ctypes.c_int
         lib.oracle_compact.argtypes = [ctypes.c_int64, _u8p, _i32p, _i32p]
         lib.oracle_compact.restype = ctypes.c_int
         lib.oracle_predict.argtypes = [ctypes.c_int64, _u8p, _u8p, _dp, _dp, _i64p,
                                        ctypes.c_double, _dp]
         lib.oracle_predict.restype = ctypes.c_int
-        lib.oracle_push_history.argtypes = [ctypes.c_int64, ctypes.c_int64, _u8p, _dp, _i64p, _dp,
-                                            _dp, ctypes.c_double]
+        lib.oracle_push_history.argtypes = [ctypes.c_int64, _u8p, _i64p, _dp, _dp, _dp, _dp,
+                                            ctypes.c_double]
         lib.oracle_push_history.restype = ctypes.c_int
         lib.oracle_predict_poly.argtypes = [ctypes.c_int64, _u8p, _u8p, _dp, _dp, _dp, _i64p,
                                             ctypes.c_double, _dp]
@@ -148,19 +149,24 @@ def eval_active(pos, vel, mass, idx=None, *, G=1.0, h, eta=0.01, want_pot=True,
     return out
 
 
-def select_due(tick, k_max, bin_, tf_ticks, dt_grav, q_f, dt_min, lib=None):
-    """Counter update and due test; returns (active, due, tf_ticks_new)."""
+def select_due(tick, k_max, bin_, tf_ticks, dt_grav, q_f, dt_min, lib=None, elapsed=None):
+    """Counter update and due test; returns (active, due, tf_ticks_new), plus
+    the elapsed ticks of due elements (a copy of `elapsed`, updated) when
+    `elapsed` is given."""
     bin_ = _c(bin_, np.int8)
     tf = np.array(tf_ticks, dtype=np.int64, copy=True)
     dt_grav = _c(dt_grav, np.float64)
     n = bin_.shape[0]
     active = np.zeros(n, np.uint8)
     due = np.zeros(n, np.uint8)
+    el = None if elapsed is None else np.array(elapsed, dtype=np.int64, copy=True)
     rc = (lib or load()).oracle_select_due(n, int(tick), int(k_max), _p(bin_, _i8p), _p(tf, _i64p),
                                   _p(dt_grav, _dp), float(q_f), float(dt_min),
-                                  _p(active, _u8p), _p(due, _u8p))
+                                  _p(active, _u8p), _p(due, _u8p), _p(el, _i64p))
     if rc != 0:
         raise ValueError("oracle_select_due: bad arguments")
+    if el is not None:
+        return active, due, tf, el
     return active, due, tf
 
 
@@ -190,18 +196,19 @@ def predict(active, due, a_last, j_last, tf_ticks, dt_min, a_out, lib=None):
     return out
 
 
-def push_history(tick, due, a_last, t_last, a_prev, dt_prev, dt_min, lib=None):
-    """Log the previous evaluation of due elements; returns (t_last, a_prev, dt_prev)."""
+def push_history(due, elapsed, dt_grav, a_last, a_prev, dt_prev, dt_min, lib=None):
+    """Log the previous evaluation of due elements; returns (a_prev, dt_prev)."""
     due = _c(due, np.uint8)
+    el = _c(elapsed, np.int64)
+    dtg = _c(dt_grav, np.float64)
     a_last = _c(a_last, np.float64)
-    tl = np.array(t_last, dtype=np.int64, copy=True)
     ap = np.array(a_prev, dtype=np.float64, copy=True)
     dp = np.array(dt_prev, dtype=np.float64, copy=True)
-    rc = (lib or load()).oracle_push_history(due.shape[0], int(tick), _p(due, _u8p), _p(a_last, _dp),
-                                             _p(tl, _i64p), _p(ap, _dp), _p(dp, _dp), float(dt_min))
+    rc = (lib or load()).oracle_push_history(due.shape[0], _p(due, _u8p), _p(el, _i64p), _p(dtg, _dp),
+                                             _p(a_last, _dp), _p(ap, _dp), _p(dp, _dp), float(dt_min))
     if rc != 0:
         raise ValueError("oracle_push_history: bad arguments")
-    return tl, ap, dp
+    return ap, dp
 
 
 def predict_poly(active, due, a_last, a_prev, dt_prev, tf_ticks, dt_min, a_out, lib=None):

@@ -517,26 +517,33 @@ def pin_predictor(lib):
 
 
 def pin_poly_history(lib):
-    """The logged history equals a brute-force record of evaluation ticks."""
+    """The logged history equals a brute-force record of evaluation ticks:
+    with the selection's elapsed ticks, dt_prev is the gap between each
+    element's last two evaluations and a_prev the earlier of them."""
     g = ics.rng(46)
-    n, dt_min = 40, 2.0**-10
-    t_last = np.zeros(n, np.int64)
+    n, dt_min, k_max = 40, 2.0**-10, 3
+    bins = g.integers(0, k_max + 1, n).astype(np.int8)
+    dtg = np.zeros(n)
+    tf = np.zeros(n, np.int64)
+    elapsed = np.zeros(n, np.int64)
     a_prev = np.zeros((n, 3))
     dt_prev = np.zeros(n)
     evals = [[] for _ in range(n)]                 # (tick, acceleration) per element
-    a_last = g.normal(size=(n, 3))
-    for tick in range(0, 60):
-        due = (g.uniform(size=n) < 0.3).astype(np.uint8) if tick else np.ones(n, np.uint8)
-        t_last, a_prev, dt_prev = O.push_history(tick, due, a_last, t_last, a_prev, dt_prev, dt_min,
-                                                  lib=lib)
+    a_last = np.zeros((n, 3))
+    for tick in range(0, 80):
+        q_f = 0.0 if tick == 0 else 1.0
+        active, due, tf, elapsed = O.select_due(tick, k_max, bins, tf, dtg, q_f, dt_min, lib=lib,
+                                                elapsed=elapsed)
+        a_prev, dt_prev = O.push_history(due, elapsed, dtg, a_last, a_prev, dt_prev, dt_min, lib=lib)
         new = g.normal(size=(n, 3))
         a_last = np.where(due[:, None] == 1, new, a_last)
+        dtg = np.where(due == 1, g.uniform(0.5, 12.0, n) * dt_min, dtg)   # "evaluated"
         for i in np.flatnonzero(due):
             evals[i].append((tick, new[i].copy()))
-        for i in range(n):
+        for i in np.flatnonzero(due):
             if len(evals[i]) >= 2:
                 (t0, a0), (t1, _) = evals[i][-2], evals[i][-1]
-                assert t_last[i] == t1 and dt_prev[i] == (t1 - t0) * dt_min
+                assert t1 == tick and dt_prev[i] == (t1 - t0) * dt_min, (i, tick)
                 assert np.array_equal(a_prev[i], a0)
             else:
                 assert dt_prev[i] == 0.0

@@ -35,7 +35,7 @@ MUTANTS = {
     "dt_offdiag_once": ("s = s + 2.0 * (t6[3] * t6[3]);", "s = s + (t6[3] * t6[3]);"),
     "dt_norm_6": ("return sqrt(eta) / sqrt(sqrt(s / 6.0));", "return sqrt(eta) / sqrt(sqrt(s / 3.0));"),
     "due_strict": ("if (elapsed >= need) {", "if (elapsed > need) {"),
-    "no_reset": ("            tf_ticks[i] = 0;\n", "\n"),
+    "no_reset": ("            tf_ticks[i] = 0;\n        } else {", "        } else {"),
     "counter_one_tick": ("tf_ticks[i] += (int64_t)1 << (k_max - k);", "tf_ticks[i] += 1;"),
     "active_wrong_step": ("int64_t step = (int64_t)1 << (k_max - k);", "int64_t step = (int64_t)1 << k;"),
     "compact_off_by_one": ("if (flags[i]) idx[c++] = (int32_t)i;", "if (flags[i]) idx[c++] = (int32_t)i + 1;"),
@@ -46,8 +46,10 @@ MUTANTS = {
     "bin_hydro_ignored": ("if (dt_hydro && dt_hydro[i] < dt) dt = dt_hydro[i];", ";"),
     "poly_slope_sign": ("double diff = a_last[3 * i + c] - a_prev[3 * i + c];",
                         "double diff = a_prev[3 * i + c] - a_last[3 * i + c];"),
-    "poly_gap_wrong": ("dt_prev[i] = (double)(tick - t_last[i]) * dt_min;",
-                       "dt_prev[i] = (double)(tick - t_last[i] + 1) * dt_min;"),
+    "poly_gap_wrong": ("dt_prev[i] = (dt_grav[i] == 0.0) ? 0.0 : (double)elapsed_ticks[i] * dt_min;",
+                       "dt_prev[i] = (dt_grav[i] == 0.0) ? 0.0 : (double)(elapsed_ticks[i] + 1) * dt_min;"),
+    "elapsed_after_reset": ("            if (elapsed_ticks) elapsed_ticks[i] = tf_ticks[i];\n            tf_ticks[i] = 0;\n",
+                            "            tf_ticks[i] = 0;\n            if (elapsed_ticks) elapsed_ticks[i] = tf_ticks[i];\n"),
     "poly_no_log": ("for (int c = 0; c < 3; ++c) a_prev[3 * i + c] = a_last[3 * i + c];", ";"),
     "adj_mass_sign": ("nadd(&mb, -f * da);", "nadd(&mb, f * da);"),
     "adj_g_term": ("nadd(&xb[c], f * ab[c] + g * d[c] * da);", "nadd(&xb[c], f * ab[c]);"),
