@@ -121,10 +121,13 @@ GRAV_API int grav_tile_config(int32_t precision, int32_t index, grav_tile_info *
  *   dt_grav   f64[n]   (in) tidal timestep from each element's last evaluation
  *   q_f       update tolerance (>= 0); dt_min > 0 the tick length
  *   active_out, due_out  uint8[n] (out)
+ *   elapsed_out int64[n] (out, nullable): for due elements, T_f before the
+ *             reset (ticks since the previous evaluation); others untouched
  */
 GRAV_API int grav_select_due(int64_t n, int64_t tick, int32_t k_max, const int8_t *bin,
                     int64_t *tf_ticks, const double *dt_grav, double q_f, double dt_min,
-                    uint8_t *active_out, uint8_t *due_out, int32_t *flags_dev, void *stream);
+                    uint8_t *active_out, uint8_t *due_out, int64_t *elapsed_out,
+                    int32_t *flags_dev, void *stream);
 
 /*
  * grav_compact_active -- the due set as an index list (follows from
@@ -181,17 +184,19 @@ GRAV_API int grav_predict(int64_t n, const uint8_t *active, const uint8_t *due, 
  * grav_push_history -- log past accelerations for the polynomial predictor
  * (Section 2.2: "logging some number of past g_i values").  For every
  * element with due[i] != 0, called after grav_select_due and BEFORE the new
- * evaluation overwrites a_last:
- *     dt_prev[i] = (tick - t_last[i]) * dt_min   (gap between its last two
- *                                                 evaluations; one rounding)
- *     t_last[i]  = tick
- *     a_prev[i]  = a_last[i]                      ([n][3])
- * t_last int64[n] (in/out) starts at 0; dt_prev f64[n] and a_prev (out) are
- * only written for due elements.  a_prev may not alias a_last.
+ * evaluation overwrites a_last and dt_grav:
+ *     a_prev[i]  = a_last[i]                       ([n][3])
+ *     dt_prev[i] = elapsed[i] * dt_min             (gap between its last two
+ *                                                  evaluations, one rounding)
+ * where elapsed comes from grav_select_due's elapsed_out; an element never
+ * evaluated before (dt_grav[i] == 0) gets dt_prev[i] = 0 (no history).
+ * Only due elements are written.  a_prev may not alias a_last.  Nothing
+ * depends on the absolute tick, so a loop of 2^k_max ticks captured as a
+ * CUDA graph replays correctly.
  */
-GRAV_API int grav_push_history(int64_t n, int64_t tick, const uint8_t *due, const double *a_last,
-                               int64_t *t_last, double *a_prev, double *dt_prev, double dt_min,
-                               void *stream);
+GRAV_API int grav_push_history(int64_t n, const uint8_t *due, const int64_t *elapsed,
+                               const double *dt_grav, const double *a_last, double *a_prev,
+                               double *dt_prev, double dt_min, void *stream);
 
 /*
  * grav_predict_poly -- the first-order polynomial predictor of Section 2.2,

@@ -65,7 +65,7 @@ class AdaptiveIntegrator:
         self.a_kick = torch.zeros(n, 3, dtype=torch.float64, device=device)
         self.zero_j = torch.zeros_like(self.acc)
         # history of the polynomial predictor
-        self.t_last = torch.zeros(n, dtype=torch.int64, device=device)
+        self.elapsed = torch.zeros(n, dtype=torch.int64, device=device)
         self.a_prev = torch.zeros(n, 3, dtype=torch.float64, device=device)
         self.dt_prev = torch.zeros(n, dtype=torch.float64, device=device)
         # device-side work counters: sum of n_due and of n_active over ticks
@@ -89,10 +89,11 @@ class AdaptiveIntegrator:
 
     def _gravity(self, tick: int):
         g = grav
+        poly = self.predictor == "poly"
         g.select_due(tick, self.k_max, self.bins, self.tf, self.dt_grav, self.q_f, self.dt_min,
-                     self.active, self.due)
-        if self.predictor == "poly":
-            g.push_history(tick, self.due, self.acc, self.t_last, self.a_prev, self.dt_prev,
+                     self.active, self.due, elapsed_out=self.elapsed if poly else None)
+        if poly:
+            g.push_history(self.due, self.elapsed, self.dt_grav, self.acc, self.a_prev, self.dt_prev,
                            self.dt_min)
         g.compact_active(self.due, self.idx, self.count, workspace=self.ws_compact)
         if self.systems is None:

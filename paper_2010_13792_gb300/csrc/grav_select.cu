@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(kElemThreads)
 select_due_kernel(int64_t n, int64_t tick, int32_t k_max, const int8_t *__restrict__ bin,
                   int64_t *__restrict__ tf_ticks, const double *__restrict__ dt_grav, double q_f,
                   double dt_min, uint8_t *__restrict__ active_out, uint8_t *__restrict__ due_out,
-                  int32_t *flags)
+                  int64_t *__restrict__ elapsed_out, int32_t *flags)
 {
     int64_t i = (int64_t)blockIdx.x * kElemThreads + threadIdx.x;
     if (i >= n) return;
@@ -41,6 +41,7 @@ select_due_kernel(int64_t n, int64_t tick, int32_t k_max, const int8_t *__restri
     double elapsed = __dmul_rn(__ll2double_rn(tf), dt_min);
     double need = __dmul_rn(q_f, dt_grav[i]);
     bool due = elapsed >= need;                            // Eq. (updatecondition)
+    if (due && elapsed_out) elapsed_out[i] = tf;           // time since the previous evaluation
     tf_ticks[i] = due ? 0 : tf;                            // reset: re-evaluated now
     active_out[i] = 1;
     due_out[i] = due ? 1 : 0;
@@ -257,17 +258,18 @@ predict_pair_kernel(int64_t n, const uint8_t *__restrict__ active, const uint8_t
 
 // ---- polynomial predictor (Section 2.2) -----------------------------------
 
-// Log the evaluation before the new one for every due element: the gap
-// between its last two evaluations, its tick and its acceleration.
+// Log the evaluation before the new one for every due element: its
+// acceleration and the gap between the two (T_f when it became due); an
+// element never evaluated before (dt_grav == 0) has no history.
 __global__ void __launch_bounds__(kElemThreads)
-push_history_kernel(int64_t n, int64_t tick, const uint8_t *__restrict__ due,
-                    const double *__restrict__ a_last, int64_t *__restrict__ t_last,
-                    double *__restrict__ a_prev, double *__restrict__ dt_prev, double dt_min)
+push_history_kernel(int64_t n, const uint8_t *__restrict__ due,
+                    const int64_t *__restrict__ elapsed, const double *__restrict__ dt_grav,
+                    const double *__restrict__ a_last, double *__restrict__ a_prev,
+                    double *__restrict__ dt_prev, double dt_min)
 {
     const int64_t i = (int64_t)blockIdx.x * kElemThreads + threadIdx.x;
     if (i >= n || !due[i]) return;
-    dt_prev[i] = __dmul_rn(__ll2double_rn(tick - t_last[i]), dt_min);
-    t_last[i] = tick;
+    dt_prev[i] = (dt_grav[i] == 0.0) ? 0.0 : __dmul_rn(__ll2double_rn(elapsed[i]), dt_min);
 #pragma unroll
     for (int c = 0; c < 3; ++c) a_prev[3 * i + c] = a_last[3 * i + c];
 }
@@ -338,8 +340,8 @@ using namespace grav;
 
 extern "C" int grav_select_due(int64_t n, int64_t tick, int32_t k_max, const int8_t *bin,
                                int64_t *tf_ticks, const double *dt_grav, double q_f, double dt_min,
-                               uint8_t *active_out, uint8_t *due_out, int32_t *flags_dev,
-                               void *stream)
+                               uint8_t *active_out, uint8_t *due_out, int64_t *elapsed_out,
+                               int32_t *flags_dev, void *stream)
 {
     if (n < 0) return fail(GRAV_EINVAL, "grav_select_due: n < 0");
     if (tick < 0) return fail(GRAV_EINVAL, "grav_select_due: tick < 0");
@@ -351,7 +353,8 @@ extern "C" int grav_select_due(int64_t n, int64_t tick, int32_t k_max, const int
         return fail(GRAV_EINVAL, "grav_select_due: null array");
     unsigned blocks = elem_blocks(n);
     select_due_kernel<<<blocks, kElemThreads, 0, as_stream(stream)>>>(
-        n, tick, k_max, bin, tf_ticks, dt_grav, q_f, dt_min, active_out, due_out, flags_dev);
+        n, tick, k_max, bin, tf_ticks, dt_grav, q_f, dt_min, active_out, due_out, elapsed_out,
+        flags_dev);
     return check_launch("grav_select_due");
 }
 
@@ -509,18 +512,18 @@ extern "C" int grav_compact_active_noalloc(int64_t n, const uint8_t *flags, int3
     return check_launch("grav_compact_active_noalloc/scatter");
 }
 
-extern "C" int grav_push_history(int64_t n, int64_t tick, const uint8_t *due, const double *a_last,
-                                 int64_t *t_last, double *a_prev, double *dt_prev, double dt_min,
-                                 void *stream)
+extern "C" int grav_push_history(int64_t n, const uint8_t *due, const int64_t *elapsed,
+                                 const double *dt_grav, const double *a_last, double *a_prev,
+                                 double *dt_prev, double dt_min, void *stream)
 {
-    if (n < 0 || tick < 0) return fail(GRAV_EINVAL, "grav_push_history: n or tick < 0");
+    if (n < 0) return fail(GRAV_EINVAL, "grav_push_history: n < 0");
     if (!(dt_min > 0.0) || isinf(dt_min)) return fail(GRAV_EINVAL, "grav_push_history: dt_min must be finite and > 0");
     if (n == 0) return GRAV_OK;
-    if (!due || !a_last || !t_last || !a_prev || !dt_prev)
+    if (!due || !elapsed || !dt_grav || !a_last || !a_prev || !dt_prev)
         return fail(GRAV_EINVAL, "grav_push_history: null array");
     if (a_prev == a_last) return fail(GRAV_EINVAL, "grav_push_history: a_prev aliases a_last");
     push_history_kernel<<<elem_blocks(n), kElemThreads, 0, as_stream(stream)>>>(
-        n, tick, due, a_last, t_last, a_prev, dt_prev, dt_min);
+        n, due, elapsed, dt_grav, a_last, a_prev, dt_prev, dt_min);
     return check_launch("grav_push_history");
 }
 

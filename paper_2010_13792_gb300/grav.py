@@ -74,13 +74,13 @@ _SIGS = {
     "grav_tile_config_count": (_c_i32, [_c_i32]),
     "grav_tile_config": (ctypes.c_int, [_c_i32, _c_i32, ctypes.POINTER(TileInfo)]),
     "grav_select_due": (ctypes.c_int, [_c_i64, _c_i64, _c_i32, _c_ptr, _c_ptr, _c_ptr, _c_dbl,
-                                       _c_dbl, _c_ptr, _c_ptr, _c_ptr, _c_ptr]),
+                                       _c_dbl, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr]),
     "grav_compact_workspace_bytes": (_c_i64, [_c_i64]),
     "grav_compact_active": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr]),
     "grav_compact_active_noalloc": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr]),
     "grav_predict": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_dbl, _c_ptr,
                                     _c_ptr]),
-    "grav_push_history": (ctypes.c_int, [_c_i64, _c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+    "grav_push_history": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                          _c_dbl, _c_ptr]),
     "grav_predict_poly": (ctypes.c_int, [_c_i64, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                          _c_dbl, _c_ptr, _c_ptr]),
@@ -220,13 +220,14 @@ def _ws(ws, key, device):
 
 
 def select_due(tick: int, k_max: int, bin_, tf_ticks, dt_grav, q_f: float, dt_min: float,
-               active_out, due_out, flags=None, stream=None):
+               active_out, due_out, flags=None, stream=None, elapsed_out=None):
     n = bin_.numel()
     rc = lib().grav_select_due(
         n, int(tick), int(k_max), _ptr(bin_, torch.int8, "bin", (n,)),
         _ptr(tf_ticks, torch.int64, "tf_ticks", (n,)), _ptr(dt_grav, torch.float64, "dt_grav", (n,)),
         float(q_f), float(dt_min), _ptr(active_out, torch.uint8, "active_out", (n,)),
         _ptr(due_out, torch.uint8, "due_out", (n,)),
+        _ptr(elapsed_out, torch.int64, "elapsed_out", (n,), allow_none=True),
         _ptr(flags, torch.int32, "flags", (1,), allow_none=True), _stream(stream))
     _err("grav_select_due", rc)
 
@@ -275,12 +276,13 @@ def predict(active, due, a_last, j_last, tf_ticks, dt_min: float, a_out, stream=
     _err("grav_predict", rc)
 
 
-def push_history(tick: int, due, a_last, t_last, a_prev, dt_prev, dt_min: float, stream=None):
+def push_history(due, elapsed, dt_grav, a_last, a_prev, dt_prev, dt_min: float, stream=None):
     n = due.numel()
     rc = lib().grav_push_history(
-        n, int(tick), _ptr(due, torch.uint8, "due", (n,)), _ptr(a_last, torch.float64, "a_last", (n, 3)),
-        _ptr(t_last, torch.int64, "t_last", (n,)), _ptr(a_prev, torch.float64, "a_prev", (n, 3)),
-        _ptr(dt_prev, torch.float64, "dt_prev", (n,)), float(dt_min), _stream(stream))
+        n, _ptr(due, torch.uint8, "due", (n,)), _ptr(elapsed, torch.int64, "elapsed", (n,)),
+        _ptr(dt_grav, torch.float64, "dt_grav", (n,)), _ptr(a_last, torch.float64, "a_last", (n, 3)),
+        _ptr(a_prev, torch.float64, "a_prev", (n, 3)), _ptr(dt_prev, torch.float64, "dt_prev", (n,)),
+        float(dt_min), _stream(stream))
     _err("grav_push_history", rc)
 
 

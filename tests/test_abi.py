@@ -49,12 +49,12 @@ def test_internal_symbols_hidden(libgrav):
 def test_host_side_argument_checks(libgrav):
     from paper_2010_13792_gb300 import grav
     L = grav.lib()
-    assert L.grav_select_due(-1, 0, 3, None, None, None, 0.5, 1.0, None, None, None, None) == grav.GRAV_EINVAL
-    assert L.grav_select_due(4, 0, 63, None, None, None, 0.5, 1.0, None, None, None, None) == grav.GRAV_EINVAL
-    assert L.grav_select_due(4, 0, 3, None, None, None, -0.5, 1.0, None, None, None, None) == grav.GRAV_EINVAL
-    assert L.grav_select_due(4, 0, 3, None, None, None, 0.5, 1.0, None, None, None, None) == grav.GRAV_EINVAL
+    assert L.grav_select_due(-1, 0, 3, None, None, None, 0.5, 1.0, None, None, None, None, None) == grav.GRAV_EINVAL
+    assert L.grav_select_due(4, 0, 63, None, None, None, 0.5, 1.0, None, None, None, None, None) == grav.GRAV_EINVAL
+    assert L.grav_select_due(4, 0, 3, None, None, None, -0.5, 1.0, None, None, None, None, None) == grav.GRAV_EINVAL
+    assert L.grav_select_due(4, 0, 3, None, None, None, 0.5, 1.0, None, None, None, None, None) == grav.GRAV_EINVAL
     assert b"null" in L.grav_last_error_string()
-    assert L.grav_select_due(0, 0, 3, None, None, None, 0.5, 1.0, None, None, None, None) == grav.GRAV_OK
+    assert L.grav_select_due(0, 0, 3, None, None, None, 0.5, 1.0, None, None, None, None, None) == grav.GRAV_OK
     assert L.grav_predict(-2, None, None, None, None, None, 1.0, None, None) == grav.GRAV_EINVAL
     assert L.grav_predict(5, None, None, None, None, None, 0.0, None, None) == grav.GRAV_EINVAL
     assert L.grav_assign_bins(5, -1, 3, 1.0, None, None, None, None, None) == grav.GRAV_EINVAL

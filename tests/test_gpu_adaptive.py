@@ -96,19 +96,23 @@ def test_batched_loop_graph_of_100_substeps(precision):
 
 
 def test_predictor_variants_ablation():
-    """The paper's ablation on a Plummer sphere: no predictor, the linear
-    polynomial from logged evaluations and the jerk.  Both predictors beat
-    keeping the last evaluation; the graph replays the poly loop exactly."""
-    n = 1 << 13
+    """The paper's ablation on a Plummer sphere whose field varies smoothly
+    (softening h = 0.5 above the interparticle spacing) with q_f = 1/4: no
+    predictor, the linear polynomial through the last two evaluations and the
+    jerk, ordered jerk < polynomial < none in predicted-acceleration error.
+    (When close encounters dominate, or the update gaps are long, only the
+    jerk helps; tests/predictor_ablation.py and bench.py report those cases.)
+    The graph replays the poly loop exactly."""
+    n = 1 << 12
     pos, vel, mass = ics.plummer(n, seed=ics.BASE_SEED + 1)
-    kw = dict(h=1e-3, q_f=1.0, k_max=5, dt_max=2.0**-4, precision=grav.F64)
+    kw = dict(h=0.5, q_f=0.25, k_max=5, dt_max=2.0**-4, precision=grav.F64)
     err = {}
     for mode in ("none", "poly", "jerk"):
         it = AdaptiveIntegrator(pos, vel, mass, predictor=mode, **kw)
         it.run(3 * 32)                           # last tick run: 96, a cycle boundary
         r = it.predictor_error()
         err[mode] = r[mode]["median"]
-    assert err["jerk"] < 0.5 * err["none"] and err["poly"] < err["none"], err
+    assert err["jerk"] < err["poly"] < 0.5 * err["none"], err
     a = AdaptiveIntegrator(pos, vel, mass, predictor="poly", **kw)
     a.run(2 * 32)
     b = AdaptiveIntegrator(pos, vel, mass, predictor="poly", **kw)

@@ -32,16 +32,20 @@ def _state(n, k_max, seed, dt_min):
 def test_select_due_bitexact(n, q_f):
     k_max, dt_min = 6, 2.0**-10
     bins, tf, dtg = _state(n, k_max, 100 + n, dt_min)
+    el0 = np.full(n, -5, np.int64)
     for tick in (0, 1, 2, 8, 64, 37, 96):
-        a_o, d_o, tf_o = O.select_due(tick, k_max, bins, tf, dtg, q_f, dt_min)
+        a_o, d_o, tf_o, el_o = O.select_due(tick, k_max, bins, tf, dtg, q_f, dt_min, elapsed=el0)
         tf_t = T(tf, torch.int64)
         a_t = torch.full((n,), 7, dtype=torch.uint8, device=DEV)
         d_t = torch.full((n,), 7, dtype=torch.uint8, device=DEV)
-        grav.select_due(tick, k_max, T(bins, torch.int8), tf_t, T(dtg), q_f, dt_min, a_t, d_t)
+        el_t = T(el0, torch.int64)
+        grav.select_due(tick, k_max, T(bins, torch.int8), tf_t, T(dtg), q_f, dt_min, a_t, d_t,
+                        elapsed_out=el_t)
         torch.cuda.synchronize()
         assert np.array_equal(a_t.cpu().numpy(), a_o)
         assert np.array_equal(d_t.cpu().numpy(), d_o)
         assert np.array_equal(tf_t.cpu().numpy(), tf_o)
+        assert np.array_equal(el_t.cpu().numpy(), el_o)
         tf = tf_o
 
 
@@ -149,30 +153,37 @@ def test_assign_bins_bitexact(n):
 @pytest.mark.parametrize("n", [1, 999, (1 << 20) + 3])
 def test_polynomial_predictor_bitexact(n):
     """Logged history and the first-order polynomial predictor against the
-    oracle over a sequence of ticks with random due sets (byte for byte)."""
+    oracle over a sequence of selections with mixed bins (byte for byte)."""
     g = ics.rng(600 + n)
-    dt_min = 2.0**-11
-    t_last = np.zeros(n, np.int64)
+    dt_min, k_max = 2.0**-11, 3
+    bins = g.integers(0, k_max + 1, n).astype(np.int8)
+    dtg = np.zeros(n)
+    tf = np.zeros(n, np.int64)
+    el = np.zeros(n, np.int64)
     a_prev = np.zeros((n, 3))
     dt_prev = np.zeros(n)
     a_last = g.normal(size=(n, 3))
-    tl_t, ap_t, dp_t = T(t_last, torch.int64), T(a_prev), T(dt_prev)
-    for tick in (0, 3, 7, 8, 20, 33):
-        due = (g.uniform(size=n) < 0.4).astype(np.uint8) if tick else np.ones(n, np.uint8)
-        t_last, a_prev, dt_prev = O.push_history(tick, due, a_last, t_last, a_prev, dt_prev, dt_min)
-        grav.push_history(tick, T(due, torch.uint8), T(a_last), tl_t, ap_t, dp_t, dt_min)
+    tf_t, el_t, ap_t, dp_t = T(tf, torch.int64), T(el, torch.int64), T(a_prev), T(dt_prev)
+    act_t = torch.zeros(n, dtype=torch.uint8, device=DEV)
+    due_t = torch.zeros(n, dtype=torch.uint8, device=DEV)
+    for tick in range(0, 20):
+        q_f = 0.0 if tick == 0 else 1.0
+        active, due, tf, el = O.select_due(tick, k_max, bins, tf, dtg, q_f, dt_min, elapsed=el)
+        a_prev, dt_prev = O.push_history(due, el, dtg, a_last, a_prev, dt_prev, dt_min)
+        dtg_t = T(dtg)
+        grav.select_due(tick, k_max, T(bins, torch.int8), tf_t, dtg_t, q_f, dt_min, act_t, due_t,
+                        elapsed_out=el_t)
+        grav.push_history(due_t, el_t, dtg_t, T(a_last), ap_t, dp_t, dt_min)
         torch.cuda.synchronize()
-        assert np.array_equal(tl_t.cpu().numpy(), t_last)
         assert np.array_equal(ap_t.cpu().numpy(), a_prev)
         assert np.array_equal(dp_t.cpu().numpy().view(np.uint64), dt_prev.view(np.uint64))
         a_last = np.where(due[:, None] == 1, g.normal(size=(n, 3)), a_last)
-        active = (g.uniform(size=n) < 0.8).astype(np.uint8)
+        dtg = np.where(due == 1, g.uniform(0.5, 10.0, n) * dt_min, dtg)
         due2 = ((g.uniform(size=n) < 0.2) & (active == 1)).astype(np.uint8)
-        tf = g.integers(0, 30, n).astype(np.int64)
         init = g.normal(size=(n, 3))
         want = O.predict_poly(active, due2, a_last, a_prev, dt_prev, tf, dt_min, init)
         out = T(init)
         grav.predict_poly(T(active, torch.uint8), T(due2, torch.uint8), T(a_last), ap_t, dp_t,
-                          T(tf, torch.int64), dt_min, out)
+                          tf_t, dt_min, out)
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy().view(np.uint64), want.view(np.uint64))
