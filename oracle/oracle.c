@@ -140,11 +140,14 @@ int oracle_max_threads(void)
  * with d = x_j - x_i, v_ji = v_j - v_i, r = |d|.
  */
 int oracle_eval(int64_t n_src, const double *pos, const double *vel, const double *mass,
-                int64_t n_tgt, const int32_t *idx, double G, double h, double eta,
+                int64_t n_tgt, const int32_t *idx, double G, double h, double eta, double box,
                 double *acc, double *jerk, double *tidal, double *pot, double *dt_grav,
                 int nthreads)
 {
-    if (n_src < 0 || n_tgt < 0 || !(h > 0.0)) return -1;
+    /* box > 0: periodic cube of side `box`, every separation taken to its
+     * nearest periodic image, d_c -> d_c - box * nearbyint(d_c / box) (the
+     * paper's Zeldovich runs used only the nearest image for the jerk). */
+    if (n_src < 0 || n_tgt < 0 || !(h > 0.0) || box < 0.0) return -1;
     if (n_tgt > 0 && (!pos || !vel || !mass || !acc || !jerk || !tidal)) return -1;
     set_threads(nthreads);
     int bad = 0;
@@ -162,6 +165,8 @@ int oracle_eval(int64_t n_src, const double *pos, const double *vel, const doubl
         for (int64_t j = 0; j < n_src; ++j) {
             if (j == i) continue;
             double d[3] = {pos[3 * j] - xi, pos[3 * j + 1] - yi, pos[3 * j + 2] - zi};
+            if (box > 0.0)
+                for (int c = 0; c < 3; ++c) d[c] -= box * nearbyint(d[c] / box);
             double v[3] = {vel[3 * j] - ui, vel[3 * j + 1] - vi, vel[3 * j + 2] - wi};
             double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             double f, g, phi;

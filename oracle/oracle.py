@@ -62,7 +62,7 @@ def load(path: str | None = None):
         lib.oracle_max_threads.restype = ctypes.c_int
         lib.oracle_eval.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_int64, _i32p,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                    _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+                                    ctypes.c_double, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
         lib.oracle_eval.restype = ctypes.c_int
         lib.oracle_select_due.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _i8p,
                                           _i64p, _dp, ctypes.c_double, ctypes.c_double, _u8p, _u8p,
@@ -121,8 +121,9 @@ def tidal_dt(t6, eta: float, lib=None) -> float:
 
 
 def eval_active(pos, vel, mass, idx=None, *, G=1.0, h, eta=0.01, want_pot=True,
-                nthreads: int = 0, lib=None):
-    """Direct-sum a, jerk, tidal tensor (6), potential and dt_grav at targets.
+                nthreads: int = 0, lib=None, box=0.0):
+    """Direct-sum a, jerk, tidal tensor (6), potential and dt_grav at targets
+    (box > 0: nearest periodic image in a cube of that side).
 
     Returns a dict of arrays indexed by target slot (row t is element idx[t]).
     """
@@ -141,7 +142,7 @@ def eval_active(pos, vel, mass, idx=None, *, G=1.0, h, eta=0.01, want_pot=True,
         "pot": np.zeros(nt) if want_pot else None, "dt_grav": np.zeros(nt),
     }
     rc = lib.oracle_eval(n, _p(pos, _dp), _p(vel, _dp), _p(mass, _dp), nt, _p(idx, _i32p),
-                         float(G), float(h), float(eta), _p(out["acc"], _dp),
+                         float(G), float(h), float(eta), float(box), _p(out["acc"], _dp),
                          _p(out["jerk"], _dp), _p(out["tidal"], _dp), _p(out["pot"], _dp),
                          _p(out["dt_grav"], _dp), int(nthreads))
     if rc != 0:

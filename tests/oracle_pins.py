@@ -377,6 +377,80 @@ def pin_plummer_field(lib, n=6000):
         assert abs(mean - 1.0) < 4 * se + 0.02, (mean, se)
 
 
+def _periodic_system(seed, n, L, margin):
+    """Uniform points in [0, L)^3 with no pair separation (per axis) within
+    `margin` of L/2, so nearest images do not switch under small moves."""
+    g = ics.rng(seed)
+    while True:
+        pos = g.uniform(0.0, L, (n, 3))
+        d = np.abs(pos[None, :, :] - pos[:, None, :])
+        d = np.minimum(d, L - d)
+        if not np.any(np.abs(d - 0.5 * L) < margin):
+            break
+    vel = g.normal(0.0, 1.0, (n, 3))
+    mass = g.uniform(0.5, 1.5, n)
+    return pos, vel, mass
+
+
+def pin_periodic_translation(lib):
+    """Nearest-image sums depend only on positions modulo the box: shifting
+    every element and wrapping back into the box changes nothing."""
+    L, h = 1.0, 0.08
+    pos, vel, mass = _periodic_system(71, 60, L, 1e-3)
+    a = O.eval_active(pos, vel, mass, h=h, box=L, lib=lib)
+    shift = np.array([0.37, -0.81, 0.123])
+    b = O.eval_active(np.mod(pos + shift, L), vel, mass, h=h, box=L, lib=lib)
+    for k in ("acc", "jerk", "tidal", "pot"):
+        _close(b[k], a[k], 1e-12, "periodic translation " + k)
+    mom = (mass[:, None] * a["acc"]).sum(0)
+    assert np.all(np.abs(mom) <= 1e-13 * np.abs(mass[:, None] * a["acc"]).sum())
+
+
+def pin_periodic_two_body(lib):
+    """Across the boundary the pair interacts through its nearest image."""
+    L, G, h = 2.0, 1.5, 0.05
+    x1 = np.array([0.1, 1.0, 1.9])
+    x2 = np.array([1.95, 0.8, 0.2])
+    d = np.array([-0.15, -0.2, 0.3])             # x2 - x1 reduced to the nearest image
+    r = np.linalg.norm(d)
+    m2 = 0.7
+    o = O.eval_active(np.stack([x1, x2]), np.zeros((2, 3)), np.array([1.3, m2]), G=G, h=h,
+                      box=L, lib=lib)
+    assert np.allclose(o["acc"][0], G * m2 * d / r**3, rtol=1e-13, atol=0)
+    assert abs(o["pot"][0] + G * m2 / r) <= 1e-13 * G * m2 / r
+
+
+def pin_periodic_open_limit(lib):
+    """A box much larger than the system changes nothing, bit for bit."""
+    pos, vel, mass = ics.uniform_sphere(80, seed=72)
+    a = O.eval_active(pos, vel, mass, h=0.1, lib=lib)
+    b = O.eval_active(pos, vel, mass, h=0.1, box=100.0, lib=lib)
+    for k in ("acc", "jerk", "tidal", "pot"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def pin_periodic_derivatives(lib):
+    """Jerk and tidal tensor are the derivatives of the nearest-image
+    acceleration (central differences, no image switches nearby)."""
+    L, h, tau = 1.0, 0.1, 1e-6
+    pos, vel, mass = _periodic_system(73, 40, L, 2e-3)
+    o = O.eval_active(pos, vel, mass, h=h, box=L, lib=lib)
+    p = O.eval_active(pos + tau * vel, vel, mass, h=h, box=L, lib=lib)
+    m = O.eval_active(pos - tau * vel, vel, mass, h=h, box=L, lib=lib)
+    _close(o["jerk"], (p["acc"] - m["acc"]) / (2 * tau), 2e-6, "periodic jerk vs FD")
+    i = 5
+    one = np.array([i], np.int32)
+    full = np.zeros((3, 3))
+    for c in range(3):
+        pp, pm = pos.copy(), pos.copy()
+        pp[i, c] += tau
+        pm[i, c] -= tau
+        full[:, c] = (O.eval_active(pp, vel, mass, one, h=h, box=L, lib=lib)["acc"][0] -
+                      O.eval_active(pm, vel, mass, one, h=h, box=L, lib=lib)["acc"][0]) / (2 * tau)
+    t6 = [full[0, 0], full[1, 1], full[2, 2], full[0, 1], full[0, 2], full[1, 2]]
+    _close(o["tidal"][i][None], np.array(t6)[None], 1e-6, "periodic tidal vs FD")
+
+
 # ---------------------------------------------------------------------------
 # Selection, binning, compaction, predictor
 # ---------------------------------------------------------------------------
@@ -625,6 +699,7 @@ def pin_adjoint_fd(lib):
 ALL_PINS = [
     pin_kernel_vs_cas, pin_kernel_limits, pin_kernel_identity_g, pin_brute_force, pin_two_body,
     pin_momentum_balance, pin_trace_density, pin_cube_symmetry, pin_scaling, pin_jerk_fd,
-    pin_tidal_fd, pin_tidal_dt, pin_update_counts, pin_reverts_exactly, pin_bins, pin_compact,
+    pin_tidal_fd, pin_tidal_dt, pin_periodic_translation, pin_periodic_two_body,
+    pin_periodic_open_limit, pin_periodic_derivatives, pin_update_counts, pin_reverts_exactly, pin_bins, pin_compact,
     pin_predictor, pin_poly_history, pin_poly_predictor, pin_adjoint_fd,
 ]

@@ -51,6 +51,10 @@ MUTANTS = {
     "elapsed_after_reset": ("            if (elapsed_ticks) elapsed_ticks[i] = tf_ticks[i];\n            tf_ticks[i] = 0;\n",
                             "            tf_ticks[i] = 0;\n            if (elapsed_ticks) elapsed_ticks[i] = tf_ticks[i];\n"),
     "poly_no_log": ("for (int c = 0; c < 3; ++c) a_prev[3 * i + c] = a_last[3 * i + c];", ";"),
+    "periodic_floor": ("for (int c = 0; c < 3; ++c) d[c] -= box * nearbyint(d[c] / box);",
+                       "for (int c = 0; c < 3; ++c) d[c] -= box * floor(d[c] / box);"),
+    "periodic_two_axes": ("for (int c = 0; c < 3; ++c) d[c] -= box * nearbyint(d[c] / box);",
+                          "for (int c = 0; c < 2; ++c) d[c] -= box * nearbyint(d[c] / box);"),
     "adj_mass_sign": ("nadd(&mb, -f * da);", "nadd(&mb, f * da);"),
     "adj_g_term": ("nadd(&xb[c], f * ab[c] + g * d[c] * da);", "nadd(&xb[c], f * ab[c]);"),
     "adj_tidal_transposed": ("ta[0] = t6[0] * ak[0] + t6[3] * ak[1] + t6[4] * ak[2];",
