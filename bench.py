@@ -381,6 +381,7 @@ def extras(args, path, dev, sms, peak32, flush):
     bytes_pred = n * (1 + 1 + 8 + 24 + 24 + 24)
     out["predict"] = {"bytes_per_element": 82, "GB_per_s": bytes_pred / tp / 1e9, "us": tp * 1e6}
     out["predict_N16777216"] = predict_bandwidth(dev, 1 << 24)
+    out["periodic_zeldovich_64cubed"] = periodic_extra(dev, flush)
     out["batched_256_systems"] = batched_extra(dev, flush)
     out["adaptive_plummer_131072"] = adaptive_extra(dev)
     try:
@@ -421,6 +422,41 @@ def predict_bandwidth(dev, n):
         ts.append(a.elapsed_time(b) * 1e-3)
     t = statistics.median(ts)
     return {"n": n, "bytes": 82 * n, "us": 1e6 * t, "GB_per_s": 82 * n / t / 1e9}
+
+
+def periodic_extra(dev, flush):
+    """Periodic box (nearest image), 64^3 elements in the pancake shape of the
+    paper's Zeldovich test (one sinusoidal mode), h = 2e-3: mixed with all
+    elements active, FP64 with 5% active, against all sources."""
+    import torch
+
+    from paper_2010_13792_gb300 import grav, ics
+    pos, vel, mass = ics.zeldovich_box(64, 1.0, amplitude=0.8)
+    n = mass.size
+    f64 = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    P, V, M = f64(pos), f64(vel), f64(mass)
+    acc = torch.empty(n, 3, dtype=torch.float64, device=dev)
+    jerk, tid = torch.empty_like(acc), torch.empty(n, 6, dtype=torch.float64, device=dev)
+    res = {"n": n, "box": 1.0, "h": 2e-3}
+    for name, prec, frac in (("mixed", grav.MIXED, 1.0), ("f64", grav.F64, 0.05)):
+        idx_np = ics.active_subset(n, frac, ics.BASE_SEED + 7)
+        idx = torch.as_tensor(idx_np, device=dev)
+        p = grav.params(h=2e-3, precision=prec, box=1.0)
+        ws = grav.Workspace()
+        grav.eval_active(p, P, V, M, idx, None, idx_np.size, acc, jerk, tid, workspace=ws)
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            grav.eval_active(p, P, V, M, idx, None, idx_np.size, acc, jerk, tid, workspace=ws)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) * 1e-3)
+        t = statistics.median(ts)
+        res[name] = {"active_fraction": frac, "interactions_per_s": idx_np.size * n / t,
+                     "ms": 1e3 * t}
+    return res
 
 
 def batched_extra(dev, flush):

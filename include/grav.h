@@ -73,6 +73,8 @@ typedef struct grav_params {
     int32_t want_pot;    /* non-zero: also evaluate the potential Phi_i */
     int32_t tile_config; /* -1 = library default, else an index < grav_tile_config_count(precision) */
     int32_t max_split;   /* upper bound on source splits per target block; 0 = default */
+    double box;          /* > 0: periodic cube [0, box)^3, every pair taken to its nearest
+                            periodic image (the paper's Zeldovich setting); 0: open */
 } grav_params;
 
 /* Describes one tile configuration (for the autotuner). */

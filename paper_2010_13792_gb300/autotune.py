@@ -81,7 +81,7 @@ def tune_eval(params: grav.Params, pos, vel, mass, idx, n_idx: int, *, systems=N
     ms = {}
     for cfg in range(grav.lib().grav_tile_config_count(precision)):
         p = grav.Params(params.G, params.h, params.eta, precision, params.want_pot, cfg,
-                        params.max_split)
+                        params.max_split, params.box)
         ws = grav.Workspace()
         if systems is not None:
             fn = lambda: grav.eval_batched(p, systems, pos, vel, mass, idx, None, n_idx, acc, jerk,

@@ -366,6 +366,7 @@ int check_bwd_params(const grav_params *p, const char *who)
     if (p->precision != GRAV_F64 && p->precision != GRAV_MIXED)
         return fail(GRAV_EINVAL, "%s: precision must be GRAV_F64 or GRAV_MIXED", who);
     if (p->max_split < 0) return fail(GRAV_EINVAL, "%s: max_split < 0", who);
+    if (p->box != 0.0) return fail(GRAV_EINVAL, "%s: the adjoint supports open boundaries only", who);
     return GRAV_OK;
 }
 

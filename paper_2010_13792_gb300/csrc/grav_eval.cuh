@@ -84,6 +84,11 @@ struct EvalArgs {
     float hf, h2f_up, hinvf, pad1;
     double *acc, *jerk, *tidal, *pot, *dt_grav;
     int32_t *flags;
+    double box, box_inv;          // periodic cube side and its inverse (box = 0: open)
+    double box_tie;               // FP64 path: |d_c| above it re-decides the image by division
+    float box_f, box_inv_f;
+    float box_tie_f;              // mixed path: |d_c| above it may be an ambiguous image
+    float pad2;
 };
 
 // Number of source chunks per target block.  Shared by the host, the eval
@@ -575,6 +580,145 @@ __device__ __forceinline__ void near_loop_pair(const float *__restrict__ tile, c
 }
 
 // ---------------------------------------------------------------------------
+// Periodic box (nearest periodic image)
+// ---------------------------------------------------------------------------
+
+// Nearest image of an FP64 separation: d - box * rint(d / box).
+__device__ __forceinline__ double wrap_d(double d, double box, double box_inv)
+{
+    return fma(-box, rint(__dmul_rn(d, box_inv)), d);
+}
+
+// Nearest image of a pair separation with the image index decided exactly as
+// a plain FP64 evaluation decides it: d = x_j - x_i, k = rint(d / box) with a
+// correctly rounded division, d - box * k.  The force is discontinuous where
+// a component crosses half a box, so the image index is an integer decision
+// that both evaluations must take in the same precision.
+__device__ __forceinline__ double nearest_image_exact(double xj, double xi, double box)
+{
+    const double d = __dsub_rn(xj, xi);
+    return __dsub_rn(d, __dmul_rn(box, rint(__ddiv_rn(d, box))));
+}
+
+// Same decision at the cost of a multiplication: the product d * (1/box) can
+// round across a half-integer only when the result lies within a few ulp of
+// half a box, so only components beyond `tie` (half a box less 2^-40 box) are
+// redone with the division.
+__device__ __forceinline__ double nearest_image_d(double xj, double xi, double box,
+                                                  double box_inv, double tie)
+{
+    const double w = wrap_d(xj - xi, box, box_inv);
+    return fabs(w) > tie ? nearest_image_exact(xj, xi, box) : w;
+}
+
+// Per target and tile: does the tile need the general loop (softened pairs,
+// or sources that might not lie within `tie` (a little under half a box) of
+// the target's image of the tile centre)?  t is the target's wrapped offset
+// from the tile centre.  Outside the general loop every pair separation is
+// then shorter than half a box by more than the FP32 rounding of the
+// offsets, so its nearest image is unambiguous.
+template <int KT>
+__device__ __forceinline__ bool periodic_special(const float t[KT][3], const int64_t ti[KT],
+                                                 const TileGeom &g, float h2_up, float tie)
+{
+    float e[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) e[c] = __fmul_ru(0.5f, __fsub_ru(g.hi[c], g.lo[c]));
+    bool special = false;
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        if (ti[q] < 0) continue;
+        float d2 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float at = fabsf(t[q][c]);
+            if (__fadd_ru(at, e[c]) >= tie) special = true;
+            const float gap = fmaxf(0.0f, __fsub_rd(at, e[c]));
+            d2 = __fmaf_rd(gap, gap, d2);
+        }
+        if (d2 < h2_up) special = true;
+    }
+    return special;
+}
+
+// General loop of the periodic box: every pair taken to its nearest image
+// (FP32), the cubic spline inside h, the self pair excluded by index.  Reads
+// either tile layout one source at a time.  A pair with a component longer
+// than `tie` (half a box less 2^-20 box, several times the FP32 rounding of
+// the offsets) may be equally near two images up to that rounding; its
+// separation is then formed again from the FP64 positions with the image
+// decided as an FP64 evaluation decides it (nearest_image_d).  Padding
+// sources have m = 0 and never take that branch.
+template <int KT, int S, bool POT, bool PAIR>
+__device__ __forceinline__ void periodic_loop_f(const float4 *__restrict__ stage,
+                                                const float tx[KT][3], const int64_t ti[KT],
+                                                int64_t jbase, float h2, float hinv,
+                                                const EvalArgs &a, float acc[KT][kNCPot])
+{
+    const float box = a.box_f, box_inv = a.box_inv_f, tie = a.box_tie_f;
+    const float hinv3 = hinv * hinv * hinv;
+    const float hinv5 = hinv3 * hinv * hinv;
+    const float *tile = reinterpret_cast<const float *>(stage);
+#pragma unroll 2
+    for (int j = 0; j < S; ++j) {
+        float x, y, z, m, vx, vy, vz;
+        if (PAIR) {
+            const int k = j >> 1, h = j & 1;
+            x = tile[4 * k + h];
+            y = tile[4 * k + 2 + h];
+            z = tile[2 * S + 4 * k + h];
+            m = tile[2 * S + 4 * k + 2 + h];
+            vx = tile[4 * S + 4 * k + h];
+            vy = tile[4 * S + 4 * k + 2 + h];
+            vz = tile[6 * S + 2 * k + h];
+        } else {
+            const float4 p = stage[j], v = stage[S + j];
+            x = p.x;
+            y = p.y;
+            z = p.z;
+            m = p.w;
+            vx = v.x;
+            vy = v.y;
+            vz = v.z;
+        }
+        const int64_t jg = jbase + j;
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            float dx = x - tx[q][0], dy = y - tx[q][1], dz = z - tx[q][2];
+            dx = fmaf(-box, rintf(dx * box_inv), dx);
+            dy = fmaf(-box, rintf(dy * box_inv), dy);
+            dz = fmaf(-box, rintf(dz * box_inv), dz);
+            if (fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) > tie && m != 0.0f && ti[q] >= 0) {
+                const double *pi = a.pos + 3 * ti[q], *pj = a.pos + 3 * jg;
+                dx = __double2float_rn(nearest_image_d(pj[0], pi[0], a.box, a.box_inv, a.box_tie));
+                dy = __double2float_rn(nearest_image_d(pj[1], pi[1], a.box, a.box_inv, a.box_tie));
+                dz = __double2float_rn(nearest_image_d(pj[2], pi[2], a.box, a.box_inv, a.box_tie));
+            }
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float ri = rsqrt_sfu(r2);
+            float ri2 = ri * ri;
+            float mp = m * ri;
+            float mf = mp * ri2;
+            float mg = mf * ri2;
+            if (r2 < h2) {
+                float F, Gp, P;
+                spline_kernel<float>(sqrtf(r2) * hinv, F, Gp, P);
+                mf = m * F * hinv3;
+                mg = m * Gp * hinv5;
+                mp = m * P * hinv;
+                if (jg == ti[q]) {
+                    mf = 0.0f;
+                    mg = 0.0f;
+                    mp = 0.0f;
+                }
+                acc[q][ESUM] += fmaf(-mg, r2, mf);
+            }
+            accumulate_f<KT, POT>(acc, q, dx, dy, dz, vx, vy, vz, mf, mg, mp);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Pair loops, FP64
 // ---------------------------------------------------------------------------
 
@@ -604,11 +748,12 @@ __device__ __forceinline__ void accumulate_d(double acc[kNCPot], double dx, doub
     if (POT) acc[PSUM] += mp;
 }
 
-template <int S, bool POT, bool NEAR>
+template <int S, bool POT, bool NEAR, bool PERIODIC = false>
 __device__ __forceinline__ void loop_d(const D4 *__restrict__ sp, const D4 *__restrict__ sv,
                                        const double xi[3], const double vi[3], int64_t ti,
                                        int64_t jbase, double h2, double hinv,
-                                       double acc[kNCPot])
+                                       double acc[kNCPot], double box = 0.0, double box_inv = 0.0,
+                                       double tie = 0.0)
 {
     const double hinv3 = hinv * hinv * hinv;
     const double hinv5 = hinv3 * hinv * hinv;
@@ -616,7 +761,16 @@ __device__ __forceinline__ void loop_d(const D4 *__restrict__ sp, const D4 *__re
     for (int j = 0; j < S; ++j) {
         const D4 p = sp[j];
         const D4 v = sv[j];
-        double dx = p.x - xi[0], dy = p.y - xi[1], dz = p.z - xi[2];
+        double dx, dy, dz;
+        if (PERIODIC) {
+            dx = nearest_image_d(p.x, xi[0], box, box_inv, tie);
+            dy = nearest_image_d(p.y, xi[1], box, box_inv, tie);
+            dz = nearest_image_d(p.z, xi[2], box, box_inv, tie);
+        } else {
+            dx = p.x - xi[0];
+            dy = p.y - xi[1];
+            dz = p.z - xi[2];
+        }
         double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
         double ri = rsqrt(r2);
         double ri2 = ri * ri;
@@ -788,7 +942,7 @@ __device__ __forceinline__ void init_ring(Sm &sm)
 }
 
 // One work item of the mixed kernel; false if a bounded wait gave up.
-template <int NT, int KT, int S, int U, bool POT, bool SACC, bool PAIR>
+template <int NT, int KT, int S, int U, bool POT, bool SACC, bool PAIR, bool PER>
 __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
                                            MixedSmem<NT, KT, S, POT, SACC, PAIR> &sm, Ring &ring,
                                            const ItemSpec &it)
@@ -862,14 +1016,18 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
         }
     }
 
-    // offsets of the targets to a tile's centre (FP64, rounded once)
+    // offsets of the targets to a tile's centre (FP64, rounded once); in a
+    // periodic box, to the image of the centre nearest to the target
+    constexpr bool periodic = PER;
     auto offsets = [&](const TileGeom &g, float out[KT][3]) {
 #pragma unroll
         for (int q = 0; q < KT; ++q)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const double x = SACC ? sm.x[c * BT + q * NT + threadIdx.x] : xr[SACC ? 0 : q][c];
-                out[q][c] = __double2float_rn(__dsub_rn(x, g.c[c]));
+                double d = __dsub_rn(x, g.c[c]);
+                if (periodic) d = wrap_d(d, a.box, a.box_inv);
+                out[q][c] = __double2float_rn(d);
             }
     };
     float tx[KT][3], tx_next[KT][3];
@@ -878,7 +1036,11 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
 
     for (int t = t_begin; t < t_end; ++t) {
         const int s = (t - t_begin) % NSTAGE;
-        const bool near = tile_is_near(blo_r, bhi_r, g, a.h2f_up);
+        // periodic: any target near the tile, or a tile that may reach past
+        // half a box from a target's image of it, takes the general loop
+        const bool near = periodic
+            ? (__syncthreads_or(periodic_special<KT>(tx, ti, g, a.h2f_up, a.box_tie_f)) != 0)
+            : tile_is_near(blo_r, bhi_r, g, a.h2f_up);
         // next tile's geometry and offsets, computed ahead (FP64 latency)
         TileGeom gn = g;
         if (t + 1 < t_end) {
@@ -896,7 +1058,10 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
         for (int q = 0; q < KT; ++q)
 #pragma unroll
             for (int c = 0; c < kNCPot; ++c) acc[q][c] = 0.0f;
-        if (PAIR) {
+        if (periodic && near) {
+            periodic_loop_f<KT, S, POT, PAIR>(sm.stage[s], tx, ti, g.first, a.h2f_up, a.hinvf, a,
+                                              acc);
+        } else if (PAIR) {
             const float *tf = reinterpret_cast<const float *>(sm.stage[s]);
             if (!near) {
                 float2 acc2[kNCPot];
@@ -989,7 +1154,7 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
     return !sm.abort_flag;
 }
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
 __global__ void __launch_bounds__(NT, MINB)
 eval_mixed_kernel(const EvalArgs a)
 {
@@ -1017,7 +1182,7 @@ eval_mixed_kernel(const EvalArgs a)
         it.sp = sp;
         it.split = split;
         it.rows = n_tb * BT;
-        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR>(a, sm, ring, it)) break;
+        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, PER>(a, sm, ring, it)) break;
         __syncthreads();
     }
     drain_ring<2>(sm.bar, ring, a.flags);
@@ -1027,7 +1192,7 @@ eval_mixed_kernel(const EvalArgs a)
 // ticket (no waiting on other CTAs).  Each target is summed by one CTA over
 // its system's tiles in a fixed order, so results do not depend on which CTA
 // takes which item.
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
 __global__ void __launch_bounds__(NT, MINB)
 eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
 {
@@ -1057,7 +1222,7 @@ eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
         it.sp = 0;
         it.split = 1;
         it.rows = 0;
-        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR>(a, sm, ring, it)) break;
+        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, PER>(a, sm, ring, it)) break;
         __syncthreads();
     }
     drain_ring<2>(sm.bar, ring, a.flags);
@@ -1076,7 +1241,7 @@ struct F64Smem {
     long long ticket;
 };
 
-template <int NT, int S, bool POT>
+template <int NT, int S, bool POT, bool PER>
 __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring &ring,
                                          const ItemSpec &it)
 {
@@ -1121,10 +1286,22 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
             }
         }
     }
+    constexpr bool periodic = PER;
     for (int t = t_begin; t < t_end; ++t) {
         const int s = (t - t_begin) % NSTAGE;
         const TileGeom g = a.geo[t];
-        const bool near = tile_is_near(blo_r, bhi_r, g, a.h2f_up);
+        bool near;
+        if (periodic) {
+            float tw[1][3];
+            const int64_t ti1[1] = {i};
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                tw[0][c] = __double2float_rn(wrap_d(__dsub_rn(xi[c], g.c[c]), a.box, a.box_inv));
+            // every FP64 periodic pair is wrapped; this only decides softening
+            near = __syncthreads_or(periodic_special<1>(tw, ti1, g, a.h2f_up, a.box_tie_f)) != 0;
+        } else {
+            near = tile_is_near(blo_r, bhi_r, g, a.h2f_up);
+        }
         const bool got = mbar_wait_bounded(&sm.bar[s], (ring.parity >> s) & 1u, a.flags);
         if (got)
             ring.parity ^= 1u << s;
@@ -1133,10 +1310,18 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
         double acc[kNCPot];
 #pragma unroll
         for (int c = 0; c < kNCPot; ++c) acc[c] = 0.0;
-        if (!near)
+        if (periodic) {
+            if (!near)
+                loop_d<S, POT, false, true>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, h2, hinv,
+                                            acc, a.box, a.box_inv, a.box_tie);
+            else
+                loop_d<S, POT, true, true>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, h2, hinv,
+                                           acc, a.box, a.box_inv, a.box_tie);
+        } else if (!near) {
             loop_d<S, POT, false>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, h2, hinv, acc);
-        else
+        } else {
             loop_d<S, POT, true>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, h2, hinv, acc);
+        }
 #pragma unroll
         for (int c = 0; c < NC; ++c) two_sum_acc(shi[c], slo[c], acc[c]);
         __syncthreads();
@@ -1160,7 +1345,7 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
     return !sm.abort_flag;
 }
 
-template <int NT, int S, bool POT>
+template <int NT, int S, bool POT, bool PER>
 __global__ void __launch_bounds__(NT, 2)
 eval_f64_kernel(const EvalArgs a)
 {
@@ -1185,13 +1370,13 @@ eval_f64_kernel(const EvalArgs a)
         it.sp = sp;
         it.split = split;
         it.rows = n_tb * NT;
-        if (!f64_item<NT, S, POT>(a, sm, ring, it)) break;
+        if (!f64_item<NT, S, POT, PER>(a, sm, ring, it)) break;
         __syncthreads();
     }
     drain_ring<2>(sm.bar, ring, a.flags);
 }
 
-template <int NT, int S, bool POT>
+template <int NT, int S, bool POT, bool PER>
 __global__ void __launch_bounds__(NT, 2)
 eval_f64_batched_kernel(const EvalArgs a, const BatchView b)
 {
@@ -1218,7 +1403,7 @@ eval_f64_batched_kernel(const EvalArgs a, const BatchView b)
         it.sp = 0;
         it.split = 1;
         it.rows = 0;
-        if (!f64_item<NT, S, POT>(a, sm, ring, it)) break;
+        if (!f64_item<NT, S, POT, PER>(a, sm, ring, it)) break;
         __syncthreads();
     }
     drain_ring<2>(sm.bar, ring, a.flags);
@@ -1275,59 +1460,59 @@ typedef void (*batched_pack_fn)(const BatchView &, const double *, const double 
 struct EvalConfig {
     int32_t precision;
     int32_t threads, kt, s, unroll, sacc;
-    eval_launch_fn launch[2];      // [want_pot]
-    occupancy_fn occupancy[2];
+    eval_launch_fn launch[2][2];   // [periodic][want_pot]
+    occupancy_fn occupancy[2][2];
     pack_launch_fn pack;
-    batched_launch_fn launch_batched[2];
-    occupancy_fn occupancy_batched[2];
+    batched_launch_fn launch_batched[2][2];
+    occupancy_fn occupancy_batched[2][2];
     batched_pack_fn pack_batched;
     bool paired;                   // mixed source tiles in the paired (FP32x2) layout
 };
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
 void launch_mixed(const EvalArgs &a, int grid, cudaStream_t st)
 {
     constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
-    eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR><<<grid, NT, bytes, st>>>(a);
+    eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, PER><<<grid, NT, bytes, st>>>(a);
 }
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
 int occupancy_mixed(int *b)
 {
     constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
-    auto k = eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR>;
+    auto k = eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, PER>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, k, NT, bytes);
 }
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
 void launch_mixed_batched(const EvalArgs &a, const BatchView &b, int grid, cudaStream_t st)
 {
     constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
-    eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR><<<grid, NT, bytes, st>>>(a, b);
+    eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, PER><<<grid, NT, bytes, st>>>(a, b);
 }
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
 int occupancy_mixed_batched(int *b)
 {
     constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
-    auto k = eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR>;
+    auto k = eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, PER>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, k, NT, bytes);
 }
 
-template <int NT, int S, bool POT>
+template <int NT, int S, bool POT, bool PER>
 void launch_f64_batched(const EvalArgs &a, const BatchView &b, int grid, cudaStream_t st)
 {
-    eval_f64_batched_kernel<NT, S, POT><<<grid, NT, 0, st>>>(a, b);
+    eval_f64_batched_kernel<NT, S, POT, PER><<<grid, NT, 0, st>>>(a, b);
 }
 
-template <int NT, int S, bool POT>
+template <int NT, int S, bool POT, bool PER>
 int occupancy_f64_batched(int *b)
 {
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_batched_kernel<NT, S, POT>, NT, 0);
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_batched_kernel<NT, S, POT, PER>, NT, 0);
 }
 
 template <int S, bool MIXED, bool VOFF, bool PAIR>
@@ -1337,16 +1522,16 @@ void launch_pack_batched(const BatchView &b, const double *pos, const double *ve
     pack_tiles_batched_kernel<S, MIXED, VOFF, PAIR><<<max_tiles, S, 0, st>>>(b, pos, vel, mass, geo, src, flags);
 }
 
-template <int NT, int S, bool POT>
+template <int NT, int S, bool POT, bool PER>
 void launch_f64(const EvalArgs &a, int grid, cudaStream_t st)
 {
-    eval_f64_kernel<NT, S, POT><<<grid, NT, 0, st>>>(a);
+    eval_f64_kernel<NT, S, POT, PER><<<grid, NT, 0, st>>>(a);
 }
 
-template <int NT, int S, bool POT>
+template <int NT, int S, bool POT, bool PER>
 int occupancy_f64(int *b)
 {
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_kernel<NT, S, POT>, NT, 0);
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_kernel<NT, S, POT, PER>, NT, 0);
 }
 
 template <int S, bool MIXED, bool VOFF, bool PAIR>

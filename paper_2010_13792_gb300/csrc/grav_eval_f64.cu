@@ -3,12 +3,13 @@
 
 namespace grav {
 
-#define GRAV_F64_CFG(NT, S)                                                                   \
-    {GRAV_F64, NT, 1, S, 4, 0, {launch_f64<NT, S, false>, launch_f64<NT, S, true>},          \
-     {occupancy_f64<NT, S, false>, occupancy_f64<NT, S, true>}, launch_pack<S, false, false, false>, \
-     {launch_f64_batched<NT, S, false>, launch_f64_batched<NT, S, true>},                     \
-     {occupancy_f64_batched<NT, S, false>, occupancy_f64_batched<NT, S, true>},               \
-     launch_pack_batched<S, false, false, false>, false}
+#define GRAV_F64_FN2(FN, NT, S) \
+    {{FN<NT, S, false, false>, FN<NT, S, true, false>}, {FN<NT, S, false, true>, FN<NT, S, true, true>}}
+
+#define GRAV_F64_CFG(NT, S)                                                                       \
+    {GRAV_F64, NT, 1, S, 4, 0, GRAV_F64_FN2(launch_f64, NT, S), GRAV_F64_FN2(occupancy_f64, NT, S), \
+     launch_pack<S, false, false, false>, GRAV_F64_FN2(launch_f64_batched, NT, S),                 \
+     GRAV_F64_FN2(occupancy_f64_batched, NT, S), launch_pack_batched<S, false, false, false>, false}
 
 static const EvalConfig kF64Configs[] = {
     GRAV_F64_CFG(128, 128),

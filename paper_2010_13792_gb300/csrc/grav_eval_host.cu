@@ -31,6 +31,9 @@ int check_params(const grav_params *p, const char *who)
     if (p->precision != GRAV_F64 && p->precision != GRAV_MIXED)
         return fail(GRAV_EINVAL, "%s: precision must be GRAV_F64 or GRAV_MIXED", who);
     if (p->max_split < 0) return fail(GRAV_EINVAL, "%s: max_split < 0", who);
+    if (!(p->box >= 0.0) || !std::isfinite(p->box)) return fail(GRAV_EINVAL, "%s: box must be finite and >= 0", who);
+    if (p->box > 0.0 && !(2.0 * p->h < p->box))
+        return fail(GRAV_EINVAL, "%s: a periodic box must be wider than twice the softening", who);
     int n = 0;
     config_table(p->precision, &n);
     if (p->tile_config < -1 || p->tile_config >= n)
@@ -47,10 +50,28 @@ const EvalConfig *resolve(const grav_params *p, int *index)
     return &t[i];
 }
 
-int grid_for(const EvalConfig *c, int index, bool pot, int *grid)
+// Periodic-box fields of the kernel arguments.  Beyond the tie lengths a
+// pair separation component is formed again in FP64 with the image decided
+// by an exact division: half a box less 2^-20 box on the mixed path (an FP32
+// separation there is good to about 4 * 2^-24 box), less 2^-40 box on the
+// FP64 path (1/box rounds once).
+void set_box(EvalArgs &a, double box)
+{
+    a.box = box;
+    a.box_inv = box > 0.0 ? 1.0 / box : 0.0;
+    a.box_tie = box > 0.0 ? box * (0.5 - 0x1p-40) : 0.0;
+    a.box_f = (float)box;
+    a.box_inv_f = (float)a.box_inv;
+    float tie = (float)(box * (0.5 - 0x1p-20));
+    if ((double)tie > box * (0.5 - 0x1p-20)) tie = std::nextafter(tie, 0.0f);
+    a.box_tie_f = box > 0.0 ? tie : 0.0f;
+    a.pad2 = 0.0f;
+}
+
+int grid_for(const EvalConfig *c, int index, bool periodic, bool pot, int *grid)
 {
     static std::mutex mu;
-    static int cache[64][2][16][2];   // [device][precision][config][pot]
+    static int cache[64][2][16][2][2];   // [device][precision][config][periodic][pot]
     int dev = 0;
     int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     if (rc) return rc;
@@ -59,10 +80,10 @@ int grid_for(const EvalConfig *c, int index, bool pot, int *grid)
     if (rc) return rc;
     if (dev >= 64 || index >= 16) return fail(GRAV_ECUDA, "device or config index out of range");
     std::lock_guard<std::mutex> lk(mu);
-    int &slot = cache[dev][c->precision][index][pot ? 1 : 0];
+    int &slot = cache[dev][c->precision][index][periodic ? 1 : 0][pot ? 1 : 0];
     if (slot == 0) {
         int b = 0;
-        rc = check_cuda((cudaError_t)c->occupancy[pot ? 1 : 0](&b), "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        rc = check_cuda((cudaError_t)c->occupancy[periodic ? 1 : 0][pot ? 1 : 0](&b), "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
         if (rc) return rc;
         if (b < 1) return fail(GRAV_ECUDA, "force kernel cannot be resident on an SM");
         slot = b * sms;
@@ -176,7 +197,7 @@ extern "C" int grav_eval_active(const grav_params *p, int64_t n_src, const doubl
                     (long long)L.total);
     const bool want_pot = p->want_pot != 0;
     int grid = 0;
-    rc = grid_for(c, index, want_pot, &grid);
+    rc = grid_for(c, index, p->box > 0.0, want_pot, &grid);
     if (rc) return rc;
 
     char *ws = static_cast<char *>(workspace);
@@ -211,13 +232,14 @@ extern "C" int grav_eval_active(const grav_params *p, int64_t n_src, const doubl
     a.pot = want_pot ? pot : nullptr;
     a.dt_grav = dt_grav;
     a.flags = flags_dev;
+    set_box(a, p->box);
 
     cudaStream_t st = as_stream(stream);
     c->pack(n_src, pos, vel, mass, const_cast<TileGeom *>(a.geo), const_cast<void *>(a.src), flags_dev,
             (int)L.n_tiles, st);
     rc = check_launch("grav_eval_active/pack");
     if (rc) return rc;
-    c->launch[want_pot ? 1 : 0](a, grid, st);
+    c->launch[p->box > 0.0 ? 1 : 0][want_pot ? 1 : 0](a, grid, st);
     rc = check_launch("grav_eval_active/eval");
     if (rc) return rc;
     const int32_t BT = c->threads * c->kt;
@@ -381,10 +403,10 @@ BatchLayout batch_layout(const EvalConfig *c, int32_t n_sys, int64_t n_total)
     return L;
 }
 
-int batch_grid_for(const EvalConfig *c, int index, bool pot, int *grid)
+int batch_grid_for(const EvalConfig *c, int index, bool periodic, bool pot, int *grid)
 {
     static std::mutex mu;
-    static int cache[64][2][16][2];
+    static int cache[64][2][16][2][2];
     int dev = 0, sms = 0;
     int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     if (rc) return rc;
@@ -392,10 +414,10 @@ int batch_grid_for(const EvalConfig *c, int index, bool pot, int *grid)
     if (rc) return rc;
     if (dev >= 64 || index >= 16) return fail(GRAV_ECUDA, "device or config index out of range");
     std::lock_guard<std::mutex> lk(mu);
-    int &slot = cache[dev][c->precision][index][pot ? 1 : 0];
+    int &slot = cache[dev][c->precision][index][periodic ? 1 : 0][pot ? 1 : 0];
     if (slot == 0) {
         int b = 0;
-        rc = check_cuda((cudaError_t)c->occupancy_batched[pot ? 1 : 0](&b),
+        rc = check_cuda((cudaError_t)c->occupancy_batched[periodic ? 1 : 0][pot ? 1 : 0](&b),
                         "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
         if (rc) return rc;
         if (b < 1) return fail(GRAV_ECUDA, "batched force kernel cannot be resident on an SM");
@@ -447,7 +469,7 @@ extern "C" int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav
                     (long long)L.total);
     const bool want_pot = p->want_pot != 0;
     int grid = 0;
-    rc = batch_grid_for(c, index, want_pot, &grid);
+    rc = batch_grid_for(c, index, p->box > 0.0, want_pot, &grid);
     if (rc) return rc;
 
     char *ws = static_cast<char *>(workspace);
@@ -494,6 +516,7 @@ extern "C" int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav
     a.pot = want_pot ? pot : nullptr;
     a.dt_grav = dt_grav;
     a.flags = flags_dev;
+    set_box(a, p->box);
 
     cudaStream_t st = as_stream(stream);
     const int32_t BT = c->threads * c->kt;
@@ -505,6 +528,6 @@ extern "C" int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav
                     flags_dev, (int)L.max_tiles, st);
     rc = check_launch("grav_eval_batched/pack");
     if (rc) return rc;
-    c->launch_batched[want_pot ? 1 : 0](a, b, grid, st);
+    c->launch_batched[p->box > 0.0 ? 1 : 0][want_pot ? 1 : 0](a, b, grid, st);
     return check_launch("grav_eval_batched/eval");
 }

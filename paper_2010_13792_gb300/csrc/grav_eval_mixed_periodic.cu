@@ -1,0 +1,12 @@
+// Periodic-box (nearest image) instantiations of the mixed-precision force
+// kernel (K5), one per tile configuration; the table that points at them is
+// built in grav_eval_mixed.cu.
+#include "grav_eval_mixed_cfg.cuh"
+
+namespace grav {
+
+#define GRAV_MIXED_DEFINE(NT, KT, S, MINB, U, SACC, PAIR) \
+    GRAV_MIXED_PERIODIC_FNS(template, NT, KT, S, MINB, U, SACC, PAIR)
+GRAV_MIXED_CONFIG_LIST(GRAV_MIXED_DEFINE)
+
+}  // namespace grav

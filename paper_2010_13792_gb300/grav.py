@@ -51,7 +51,8 @@ class GravError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("G", _c_dbl), ("h", _c_dbl), ("eta", _c_dbl), ("precision", _c_i32),
-                ("want_pot", _c_i32), ("tile_config", _c_i32), ("max_split", _c_i32)]
+                ("want_pot", _c_i32), ("tile_config", _c_i32), ("max_split", _c_i32),
+                ("box", _c_dbl)]
 
 
 class TileInfo(ctypes.Structure):
@@ -60,9 +61,11 @@ class TileInfo(ctypes.Structure):
 
 
 def params(*, G: float = 1.0, h: float, eta: float = 0.01, precision: int = MIXED,
-           want_pot: bool = False, tile_config: int = -1, max_split: int = 0) -> Params:
+           want_pot: bool = False, tile_config: int = -1, max_split: int = 0,
+           box: float = 0.0) -> Params:
+    """box > 0: periodic cube of that side, nearest periodic image."""
     return Params(float(G), float(h), float(eta), int(precision), int(bool(want_pot)),
-                  int(tile_config), int(max_split))
+                  int(tile_config), int(max_split), float(box))
 
 
 _lock = threading.Lock()

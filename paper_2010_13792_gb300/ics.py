@@ -17,6 +17,9 @@ Stand-ins (the paper's own initial conditions are not published):
     [-R, R]^3 (no Helmholtz projection), trilinearly interpolated, mean removed
     and scaled to virial parameter alpha = 2K/|W| = 2.  Stands in for the
     STARFORGE giant-molecular-cloud runs of Section 3.
+  * ``zeldovich_box``   -- periodic cube [0, L)^3: a lattice displaced by one
+    sinusoidal mode along x (the shape of the Zeldovich pancake of Section 3,
+    without the cosmology), velocities along the displacement.
   * ``morton_order``    -- stable sort by 63-bit Morton key so that consecutive
     index ranges are spatially compact (applied once at creation time).
 """
@@ -156,6 +159,30 @@ def turbulent_cloud(n: int, seed: int = BASE_SEED + 2, R: float = 1.0, grid: int
     k = 0.5 * (1.0 / max(n, 1)) * float((vel * vel).sum())
     if k > 0:
         vel *= np.sqrt(0.5 * alpha_vir * w_abs / k)
+    return _finish(pos, vel, sort)
+
+
+def zeldovich_box(n_side: int = 64, L: float = 1.0, amplitude: float = 0.1, jitter: float = 0.01,
+                  seed: int = BASE_SEED + 6, sort: bool = True):
+    """n_side^3 equal masses in the periodic cube [0, L)^3: a cubic lattice,
+    displaced along x by amplitude * L / (2 pi) * sin(2 pi q_x / L) (one
+    sinusoidal mode; amplitude < 1 before shell crossing) plus a small random
+    jitter (fraction of the lattice spacing), with velocities along the
+    displacement; positions wrapped into the box."""
+    g = rng(seed)
+    n = n_side**3
+    spacing = L / n_side
+    k = (np.arange(n_side) + 0.5) * spacing
+    qx, qy, qz = np.meshgrid(k, k, k, indexing="ij")
+    q = np.stack([qx.ravel(), qy.ravel(), qz.ravel()], axis=1)
+    disp = amplitude * L / (2.0 * np.pi) * np.sin(2.0 * np.pi * q[:, 0] / L)
+    pos = q.copy()
+    pos[:, 0] += disp
+    pos += g.uniform(-0.5, 0.5, (n, 3)) * jitter * spacing
+    pos = np.mod(pos, L)
+    vel = np.zeros((n, 3))
+    vel[:, 0] = -disp                      # converging flow toward the pancake plane
+    vel += g.normal(0.0, 1e-3, (n, 3))
     return _finish(pos, vel, sort)
 
 

@@ -420,6 +420,21 @@ def pin_periodic_two_body(lib):
     assert abs(o["pot"][0] + G * m2 / r) <= 1e-13 * G * m2 / r
 
 
+def pin_periodic_half_box_tie(lib):
+    """At exactly half a box the two images are equally near; the reading
+    taken keeps the separation as it is (d/L = +-1/2 rounds to image 0,
+    halves to even), so each element of the pair sees the other through a
+    different image, and total momentum is still conserved."""
+    L, G, h = 2.0, 1.0, 0.05
+    x = np.array([[0.25, 0.5, 0.5], [1.25, 0.7, 0.5]])     # x2 - x1 = (L/2, 0.2, 0)
+    m = np.array([0.6, 0.9])
+    o = O.eval_active(x, np.zeros((2, 3)), m, G=G, h=h, box=L, lib=lib)
+    d = np.array([1.0, 0.2, 0.0])
+    r = np.linalg.norm(d)
+    assert np.allclose(o["acc"][0], G * m[1] * d / r**3, rtol=1e-14, atol=0)
+    assert np.allclose(o["acc"][1], -G * m[0] * d / r**3, rtol=1e-14, atol=0)
+
+
 def pin_periodic_open_limit(lib):
     """A box much larger than the system changes nothing, bit for bit."""
     pos, vel, mass = ics.uniform_sphere(80, seed=72)
@@ -700,6 +715,7 @@ ALL_PINS = [
     pin_kernel_vs_cas, pin_kernel_limits, pin_kernel_identity_g, pin_brute_force, pin_two_body,
     pin_momentum_balance, pin_trace_density, pin_cube_symmetry, pin_scaling, pin_jerk_fd,
     pin_tidal_fd, pin_tidal_dt, pin_periodic_translation, pin_periodic_two_body,
-    pin_periodic_open_limit, pin_periodic_derivatives, pin_update_counts, pin_reverts_exactly, pin_bins, pin_compact,
+    pin_periodic_half_box_tie, pin_periodic_open_limit, pin_periodic_derivatives,
+    pin_update_counts, pin_reverts_exactly, pin_bins, pin_compact,
     pin_predictor, pin_poly_history, pin_poly_predictor, pin_adjoint_fd,
 ]

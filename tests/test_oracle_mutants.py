@@ -53,6 +53,8 @@ MUTANTS = {
     "poly_no_log": ("for (int c = 0; c < 3; ++c) a_prev[3 * i + c] = a_last[3 * i + c];", ";"),
     "periodic_floor": ("for (int c = 0; c < 3; ++c) d[c] -= box * nearbyint(d[c] / box);",
                        "for (int c = 0; c < 3; ++c) d[c] -= box * floor(d[c] / box);"),
+    "periodic_half_up": ("for (int c = 0; c < 3; ++c) d[c] -= box * nearbyint(d[c] / box);",
+                         "for (int c = 0; c < 3; ++c) d[c] -= box * floor(d[c] / box + 0.5);"),
     "periodic_two_axes": ("for (int c = 0; c < 3; ++c) d[c] -= box * nearbyint(d[c] / box);",
                           "for (int c = 0; c < 2; ++c) d[c] -= box * nearbyint(d[c] / box);"),
     "adj_mass_sign": ("nadd(&mb, -f * da);", "nadd(&mb, f * da);"),
