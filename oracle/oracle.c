@@ -20,7 +20,12 @@
  *     the first-order polynomial predictor from logged accelerations
  *     (Section 2.2);
  *   - the adjoint (reverse-mode) sums for a loss on a and on the potential
- *     energy (not in the paper; derived from Eq. 4 and the tidal tensor).
+ *     energy (not in the paper; derived from Eq. 4 and the tidal tensor);
+ *   - adaptive softening (Section 3: fully adaptive softening with the
+ *     energy-conserving correction terms of Price & Monaghan 2007): supports
+ *     h_i from a mass-density constraint by safeguarded Newton iterations,
+ *     the correction coefficients zeta_i, and the sums with pair-averaged
+ *     kernels plus the correction term.
  *
  * Readings where the paper is silent (all listed with reasons in the design
  * notes of the repository):
@@ -139,16 +144,15 @@ int oracle_max_threads(void)
  *   dt_grav[t]  sqrt(eta) (||T_i||^2/6)^(-1/4)                    (nullable)
  * with d = x_j - x_i, v_ji = v_j - v_i, r = |d|.
  */
-int oracle_eval(int64_t n_src, const double *pos, const double *vel, const double *mass,
-                int64_t n_tgt, const int32_t *idx, double G, double h, double eta, double box,
-                double *acc, double *jerk, double *tidal, double *pot, double *dt_grav,
-                int nthreads)
+void oracle_kernel_w(double r, double h, double *w, double *w_r, double *w_h, double *psi_h);
+
+/* Shared by oracle_eval (one support h for every pair, hs == NULL) and
+ * oracle_eval_soft (per-element supports hs[], optional zeta). */
+static int eval_core(int64_t n_src, const double *pos, const double *vel, const double *mass,
+                     const double *hs, const double *zeta, int64_t n_tgt, const int32_t *idx,
+                     double G, double h, double eta, double box, double *acc, double *jerk,
+                     double *tidal, double *pot, double *dt_grav, int nthreads)
 {
-    /* box > 0: periodic cube of side `box`, every separation taken to its
-     * nearest periodic image, d_c -> d_c - box * nearbyint(d_c / box) (the
-     * paper's Zeldovich runs used only the nearest image for the jerk). */
-    if (n_src < 0 || n_tgt < 0 || !(h > 0.0) || box < 0.0) return -1;
-    if (n_tgt > 0 && (!pos || !vel || !mass || !acc || !jerk || !tidal)) return -1;
     set_threads(nthreads);
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(|: bad)
@@ -169,12 +173,30 @@ int oracle_eval(int64_t n_src, const double *pos, const double *vel, const doubl
                 for (int c = 0; c < 3; ++c) d[c] -= box * nearbyint(d[c] / box);
             double v[3] = {vel[3 * j] - ui, vel[3 * j + 1] - vi, vel[3 * j + 2] - wi};
             double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            double f, g, phi;
-            oracle_kernel(r, h, &f, &g, &phi);
+            double f, g, phi, fc = 0.0;
+            if (hs) {
+                /* per-element supports: the mean of the two kernels */
+                double fi, gi, pi_, fj, gj, pj;
+                oracle_kernel(r, hs[i], &fi, &gi, &pi_);
+                oracle_kernel(r, hs[j], &fj, &gj, &pj);
+                f = 0.5 * (fi + fj);
+                g = 0.5 * (gi + gj);
+                phi = 0.5 * (pi_ + pj);
+                /* correction: -(1/2)[zeta_i W_r(r,h_i) + zeta_j W_r(r,h_j)] / r per unit m d */
+                if (zeta && r > 0.0) {
+                    double w, wri, wrj, wh, psh;
+                    oracle_kernel_w(r, hs[i], &w, &wri, &wh, &psh);
+                    oracle_kernel_w(r, hs[j], &w, &wrj, &wh, &psh);
+                    fc = -0.5 * (zeta[i] * wri + zeta[j] * wrj) / r;
+                }
+            } else {
+                oracle_kernel(r, h, &f, &g, &phi);
+            }
             double m = mass[j];
             double dv = d[0] * v[0] + d[1] * v[1] + d[2] * v[2];
             for (int c = 0; c < 3; ++c) {
                 nadd(&a[c], m * f * d[c]);
+                if (fc != 0.0) nadd(&a[c], m * fc * d[c]);
                 nadd(&jk[c], m * (f * v[c] + g * dv * d[c]));
             }
             /* T_ab = -m (f delta_ab + g d_a d_b) */
@@ -199,6 +221,197 @@ int oracle_eval(int64_t n_src, const double *pos, const double *vel, const doubl
         if (dt_grav) dt_grav[t] = oracle_tidal_dt(t6, eta);
     }
     return bad ? -1 : 0;
+}
+
+int oracle_eval(int64_t n_src, const double *pos, const double *vel, const double *mass,
+                int64_t n_tgt, const int32_t *idx, double G, double h, double eta, double box,
+                double *acc, double *jerk, double *tidal, double *pot, double *dt_grav,
+                int nthreads)
+{
+    /* box > 0: periodic cube of side `box`, every separation taken to its
+     * nearest periodic image, d_c -> d_c - box * nearbyint(d_c / box) (the
+     * paper's Zeldovich runs used only the nearest image for the jerk). */
+    if (n_src < 0 || n_tgt < 0 || !(h > 0.0) || box < 0.0) return -1;
+    if (n_tgt > 0 && (!pos || !vel || !mass || !acc || !jerk || !tidal)) return -1;
+    return eval_core(n_src, pos, vel, mass, NULL, NULL, n_tgt, idx, G, h, eta, box, acc, jerk,
+                     tidal, pot, dt_grav, nthreads);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adaptive softening (Section 3: fully adaptive softening with the extra     */
+/* force terms of Price & Monaghan 2007 that keep energy conserved).          */
+/*                                                                            */
+/* Readings (the paper gives no formulas):                                    */
+/*  - each element i has its own support h_i, fixed by the mass-density       */
+/*    constraint (4 pi / 3) h_i^3 rho_i = n_ngb m_i with                       */
+/*    rho_i = sum_j m_j W(r_ij, h_i), the self term j = i included;           */
+/*  - the potential energy is U = -(G/2) sum_i sum_{j != i} m_i m_j           */
+/*    (psi(r_ij, h_i) + psi(r_ij, h_j)) / 2 (self terms excluded, as in the    */
+/*    fixed-h evaluation); the pair force is the average of the two kernels; */
+/*  - the acceleration is -grad_i U / m_i with h's dependence on the          */
+/*    positions through the constraint, which adds                            */
+/*      a_i^zeta = -(G/2) sum_j m_j [zeta_i W_r(r,h_i) + zeta_j W_r(r,h_j)] d/r */
+/*    where W_r = dW/dr, zeta_i = (dh_i/drho_i) / Omega_i                     */
+/*    * sum_{j != i} m_j dpsi(r_ij, h_i)/dh, dh/drho = -h / (3 rho),           */
+/*    Omega_i = 1 + h_i / (3 rho_i) * sum_j m_j dW(r_ij, h_i)/dh;             */
+/*  - jerk and tidal tensor are those of the averaged pair force at fixed    */
+/*    h_i, h_j (the correction term and the motion of h are not              */
+/*    differentiated).                                                        */
+/* ------------------------------------------------------------------------- */
+
+/* Density kernel W(r,h) = 8/(pi h^3) w(r/h) and the derivatives the adaptive
+ * terms need: dW/dr, dW/dh and dpsi/dh of the potential kernel psi
+ * (psi = phi of oracle_kernel, psi(r,h) = p(r/h)/h, dpsi/dh = -(u p)'(u)/h^2). */
+void oracle_kernel_w(double r, double h, double *w, double *w_r, double *w_h, double *psi_h)
+{
+    double u = r / h;
+    double c = 8.0 / (ORACLE_PI * h * h * h);
+    double wu, dwu, dup;
+    if (u < 0.5) {
+        wu = 1.0 + u * u * (-6.0 + 6.0 * u);
+        dwu = u * (-12.0 + 18.0 * u);
+        double u2 = u * u;
+        dup = 14.0 / 5.0 + u2 * (-16.0 + u2 * (48.0 - 192.0 / 5.0 * u));
+    } else if (u < 1.0) {
+        double q = 1.0 - u;
+        wu = 2.0 * q * q * q;
+        dwu = -6.0 * q * q;
+        double u2 = u * u;
+        dup = 16.0 / 5.0 + u2 * (-32.0 + u * (64.0 + u * (-48.0 + 64.0 / 5.0 * u)));
+    } else {
+        wu = 0.0;
+        dwu = 0.0;
+        dup = 0.0;
+    }
+    *w = c * wu;
+    *w_r = c * dwu / h;
+    *w_h = -c * (3.0 * wu + u * dwu) / h;
+    *psi_h = -dup / (h * h);
+}
+
+/* Per element, at the given supports h_i:
+ *   rho[i]   = sum_j m_j W(r_ij, h_i)              (j = i included)
+ *   rho_h[i] = sum_j m_j dW(r_ij, h_i)/dh          (j = i included)
+ *   psi_h[i] = sum_{j != i} m_j dpsi(r_ij, h_i)/dh
+ */
+int oracle_soft_sums(int64_t n, const double *pos, const double *mass, const double *hs,
+                     double *rho, double *rho_h, double *psi_h, int nthreads)
+{
+    if (n < 0 || (n > 0 && (!pos || !mass || !hs || !rho || !rho_h || !psi_h))) return -1;
+    set_threads(nthreads);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(|: bad)
+    for (int64_t i = 0; i < n; ++i) {
+        double h = hs[i];
+        if (!(h > 0.0)) { bad = 1; continue; }
+        nsum sr, srh, sp;
+        memset(&sr, 0, sizeof sr);
+        memset(&srh, 0, sizeof srh);
+        memset(&sp, 0, sizeof sp);
+        for (int64_t j = 0; j < n; ++j) {
+            double d[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1],
+                           pos[3 * j + 2] - pos[3 * i + 2]};
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (r >= h) continue;
+            double w, wr, wh, ph;
+            oracle_kernel_w(r, h, &w, &wr, &wh, &ph);
+            nadd(&sr, mass[j] * w);
+            nadd(&srh, mass[j] * wh);
+            if (j != i) nadd(&sp, mass[j] * ph);
+        }
+        rho[i] = nval(&sr);
+        rho_h[i] = nval(&srh);
+        psi_h[i] = nval(&sp);
+    }
+    return bad ? -1 : 0;
+}
+
+/* Solves (4 pi / 3) h_i^3 rho_i(h_i) = n_ngb m_i for every element by Newton
+ * iterations kept inside a bracket [lo, hi] (F(h) is non-decreasing in h);
+ * a step that leaves the bracket doubles h (no upper end yet) or bisects.
+ * h[] holds the starting guesses on entry.  Converged when
+ * |F| <= tol * n_ngb * m_i; the sums of the last iteration are those at the
+ * returned h, from which zeta follows:
+ *   Omega_i = 1 + h_i rho_h_i / (3 rho_i),
+ *   zeta_i  = -h_i psi_h_i / (3 rho_i Omega_i).
+ * iters[i] (nullable) = iterations used, -1 where max_iter ran out.
+ * Returns 0, or 1 when some element did not converge, -1 on bad arguments. */
+int oracle_soft_solve(int64_t n, const double *pos, const double *mass, double n_ngb, double tol,
+                      int32_t max_iter, double *hs, double *zeta, double *omega, int32_t *iters,
+                      int nthreads)
+{
+    if (n < 0 || !(n_ngb > 32.0 / 3.0) || !(tol > 0.0) || max_iter < 1) return -1;
+    if (n > 0 && (!pos || !mass || !hs)) return -1;
+    set_threads(nthreads);
+    int bad = 0, stuck = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(|: bad, stuck)
+    for (int64_t i = 0; i < n; ++i) {
+        double h = hs[i];
+        if (!(h > 0.0) || !(mass[i] > 0.0)) { bad = 1; continue; }
+        const double target = n_ngb * mass[i];
+        double lo = 0.0, hi = INFINITY;
+        int32_t it = 0;
+        int done = 0;
+        double rho = 0.0, rho_h = 0.0, psi_h = 0.0;
+        for (; it < max_iter; ++it) {
+            nsum sr, srh, sp;
+            memset(&sr, 0, sizeof sr);
+            memset(&srh, 0, sizeof srh);
+            memset(&sp, 0, sizeof sp);
+            for (int64_t j = 0; j < n; ++j) {
+                double d[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1],
+                               pos[3 * j + 2] - pos[3 * i + 2]};
+                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                if (r >= h) continue;
+                double w, wr, wh, ph;
+                oracle_kernel_w(r, h, &w, &wr, &wh, &ph);
+                nadd(&sr, mass[j] * w);
+                nadd(&srh, mass[j] * wh);
+                if (j != i) nadd(&sp, mass[j] * ph);
+            }
+            rho = nval(&sr);
+            rho_h = nval(&srh);
+            psi_h = nval(&sp);
+            double vol = 4.0 * ORACLE_PI / 3.0 * h * h * h;
+            double F = vol * rho - target;
+            if (fabs(F) <= tol * target) { done = 1; break; }
+            if (F < 0.0) lo = h; else hi = h;
+            double dF = 4.0 * ORACLE_PI * h * h * rho + vol * rho_h;
+            double hn = (dF > 0.0) ? h - F / dF : -1.0;
+            if (!(hn > lo && hn < hi)) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
+            h = hn;
+        }
+        hs[i] = h;
+        double om = 1.0 + h * rho_h / (3.0 * rho);
+        if (omega) omega[i] = om;
+        if (zeta) zeta[i] = -h * psi_h / (3.0 * rho * om);
+        if (iters) iters[i] = done ? it : -1;
+        if (!done) stuck = 1;
+    }
+    if (bad) return -1;
+    return stuck ? 1 : 0;
+}
+
+/*
+ * Force evaluation with per-element supports hs[] (and, when zeta is not
+ * NULL, the correction term of the adaptive-softening readings above):
+ *   a_i   = G sum_j m_j fbar d + a_i^zeta,  fbar = (f(r,h_i) + f(r,h_j)) / 2
+ *   j_i   = G sum_j m_j [fbar v_ji + gbar (d . v_ji) d]
+ *   T_i   = -G sum_j m_j [fbar I + gbar d d^T]
+ *   Phi_i = -G sum_j m_j (psi(r,h_i) + psi(r,h_j)) / 2
+ * Output slots and nullability as in oracle_eval (open boundaries only).
+ */
+int oracle_eval_soft(int64_t n_src, const double *pos, const double *vel, const double *mass,
+                     const double *hs, const double *zeta, int64_t n_tgt, const int32_t *idx,
+                     double G, double eta, double *acc, double *jerk, double *tidal, double *pot,
+                     double *dt_grav, int nthreads)
+{
+    if (n_src < 0 || n_tgt < 0) return -1;
+    if (n_tgt > 0 && (!pos || !vel || !mass || !hs || !acc || !jerk || !tidal)) return -1;
+    for (int64_t j = 0; j < n_src; ++j)
+        if (!(hs[j] > 0.0)) return -1;
+    return eval_core(n_src, pos, vel, mass, hs, zeta, n_tgt, idx, G, 1.0, eta, 0.0, acc, jerk,
+                     tidal, pot, dt_grav, nthreads);
 }
 
 /* ------------------------------------------------------------------------- */

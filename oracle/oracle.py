@@ -86,6 +86,18 @@ def load(path: str | None = None):
                                         _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                         _i32p, _dp, _dp, ctypes.c_int]
         lib.oracle_backward.restype = ctypes.c_int
+        lib.oracle_kernel_w.argtypes = [ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp]
+        lib.oracle_kernel_w.restype = None
+        lib.oracle_soft_sums.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+        lib.oracle_soft_sums.restype = ctypes.c_int
+        lib.oracle_soft_solve.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int32, _dp, _dp, _dp, _i32p,
+                                          ctypes.c_int]
+        lib.oracle_soft_solve.restype = ctypes.c_int
+        lib.oracle_eval_soft.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, ctypes.c_int64,
+                                         _i32p, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp,
+                                         _dp, _dp, ctypes.c_int]
+        lib.oracle_eval_soft.restype = ctypes.c_int
         if path is None:
             _lib = lib
         return lib
@@ -147,6 +159,76 @@ def eval_active(pos, vel, mass, idx=None, *, G=1.0, h, eta=0.01, want_pot=True,
                          _p(out["dt_grav"], _dp), int(nthreads))
     if rc != 0:
         raise ValueError("oracle_eval: bad arguments")
+    return out
+
+
+def kernel_w(r: float, h: float, lib=None):
+    """(W, dW/dr, dW/dh, dpsi/dh) of the cubic-spline kernel (psi = the
+    potential kernel phi of `kernel`)."""
+    v = [ctypes.c_double() for _ in range(4)]
+    (lib or load()).oracle_kernel_w(float(r), float(h), *[ctypes.byref(x) for x in v])
+    return tuple(x.value for x in v)
+
+
+def soft_sums(pos, mass, h, *, nthreads: int = 0, lib=None):
+    """(rho, rho_h, psi_h) per element at supports h: sum_j m_j W(r_ij, h_i) and
+    sum_j m_j dW/dh (j = i included), sum_{j != i} m_j dpsi(r_ij, h_i)/dh."""
+    pos = _c(pos, np.float64)
+    mass = _c(mass, np.float64)
+    h = _c(h, np.float64)
+    n = mass.shape[0]
+    rho, rho_h, psi_h = np.zeros(n), np.zeros(n), np.zeros(n)
+    rc = (lib or load()).oracle_soft_sums(n, _p(pos, _dp), _p(mass, _dp), _p(h, _dp), _p(rho, _dp),
+                                          _p(rho_h, _dp), _p(psi_h, _dp), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_soft_sums: bad arguments")
+    return rho, rho_h, psi_h
+
+
+def soft_solve(pos, mass, h0, *, n_ngb: float, tol: float = 1e-13, max_iter: int = 100,
+               nthreads: int = 0, lib=None):
+    """Supports h_i with (4 pi/3) h_i^3 rho_i = n_ngb m_i, and the correction
+    coefficients; returns a dict h, zeta, omega, iters (-1: not converged)."""
+    pos = _c(pos, np.float64)
+    mass = _c(mass, np.float64)
+    n = mass.shape[0]
+    h = np.array(np.broadcast_to(np.asarray(h0, np.float64), (n,)), dtype=np.float64, copy=True)
+    zeta, omega = np.zeros(n), np.zeros(n)
+    iters = np.zeros(n, np.int32)
+    rc = (lib or load()).oracle_soft_solve(n, _p(pos, _dp), _p(mass, _dp), float(n_ngb), float(tol),
+                                           int(max_iter), _p(h, _dp), _p(zeta, _dp),
+                                           _p(omega, _dp), _p(iters, _i32p), int(nthreads))
+    if rc < 0:
+        raise ValueError("oracle_soft_solve: bad arguments")
+    return {"h": h, "zeta": zeta, "omega": omega, "iters": iters, "converged": rc == 0}
+
+
+def eval_soft(pos, vel, mass, h, zeta=None, idx=None, *, G=1.0, eta=0.01, want_pot=True,
+              nthreads: int = 0, lib=None):
+    """Direct sums with per-element supports h (kernels averaged over the
+    pair) and, when zeta is given, the adaptive-softening correction to a."""
+    lib = lib or load()
+    pos = _c(pos, np.float64)
+    vel = _c(vel, np.float64)
+    mass = _c(mass, np.float64)
+    h = _c(h, np.float64)
+    zeta = None if zeta is None else _c(zeta, np.float64)
+    n = mass.shape[0]
+    if idx is not None:
+        idx = _c(idx, np.int32)
+        nt = idx.shape[0]
+    else:
+        nt = n
+    out = {
+        "acc": np.zeros((nt, 3)), "jerk": np.zeros((nt, 3)), "tidal": np.zeros((nt, 6)),
+        "pot": np.zeros(nt) if want_pot else None, "dt_grav": np.zeros(nt),
+    }
+    rc = lib.oracle_eval_soft(n, _p(pos, _dp), _p(vel, _dp), _p(mass, _dp), _p(h, _dp),
+                              _p(zeta, _dp), nt, _p(idx, _i32p), float(G), float(eta),
+                              _p(out["acc"], _dp), _p(out["jerk"], _dp), _p(out["tidal"], _dp),
+                              _p(out["pot"], _dp), _p(out["dt_grav"], _dp), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_eval_soft: bad arguments")
     return out
 
 

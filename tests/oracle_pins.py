@@ -22,7 +22,13 @@ or the mathematics fixes:
   the last update reconstructed from the update history; bins by exact
   rational enumeration; compaction by ``numpy.flatnonzero``;
 * the predictor exact on a field linear in time, and equal to the paper's
-  incremental update applied step by step.
+  incremental update applied step by step;
+* adaptive softening: W, dW/dr, dW/dh and dpsi/dh against sympy
+  derivatives; the density constraint, Omega and zeta against mpmath brute
+  force sums; the corrected acceleration equal to -grad U / m with every
+  support re-solved (central differences), the uncorrected one not; equal
+  supports reducing to the fixed-h sums bit for bit; momentum balance;
+  jerk and tidal tensor as derivatives at fixed supports.
 
 The mutation test runs these pins against copies of the oracle with planted
 mistakes and requires every mutant to fail at least one pin.
@@ -471,6 +477,196 @@ def pin_periodic_derivatives(lib):
 # ---------------------------------------------------------------------------
 
 
+# ---------------------------------------------------------------------------
+# Adaptive softening (per-element supports and the correction terms)
+# ---------------------------------------------------------------------------
+
+
+@lru_cache(maxsize=1)
+def cas_kernel_h():
+    """mpmath callables of (r, h) from sympy, for u = r/h < 1/2 and 1/2 <= u < 1:
+    W, dW/dr, dW/dh and dpsi/dh, psi(r, h) = p(r/h)/h the potential kernel
+    (p from integrating the CAS force kernel, as in cas_kernel)."""
+    import sympy as sp
+    s, u, r, h = sp.symbols("s u r h", positive=True)
+    c = sp.Rational(8) / sp.pi
+    w_in = 1 - 6 * s**2 + 6 * s**3
+    w_out = 2 * (1 - s) ** 3
+    m_in = sp.integrate(4 * sp.pi * s**2 * c * w_in, (s, 0, u))
+    m_out = m_in.subs(u, sp.Rational(1, 2)) + sp.integrate(4 * sp.pi * s**2 * c * w_out,
+                                                          (s, sp.Rational(1, 2), u))
+    f_in, f_out = m_in / u**3, m_out / u**3
+    p_out = 1 + sp.integrate(s * f_out.subs(u, s), (s, u, 1))
+    p_in = p_out.subs(u, sp.Rational(1, 2)) + sp.integrate(s * f_in.subs(u, s),
+                                                           (s, u, sp.Rational(1, 2)))
+    out = []
+    for w, pk in ((w_in, p_in), (w_out, p_out)):
+        W = c / h**3 * w.subs(s, r / h)
+        psi = pk.subs(u, r / h) / h
+        exprs = (W, sp.diff(W, r), sp.diff(W, h), sp.diff(psi, h))
+        out.append([sp.lambdify((r, h), sp.simplify(e), "mpmath") for e in exprs])
+    return out
+
+
+def kernel_h_mp(r, h):
+    """(W, dW/dr, dW/dh, dpsi/dh) at (r, h) in mpmath, zero beyond the support."""
+    import mpmath as mp
+    r = mp.mpf(r)
+    h = mp.mpf(h)
+    if r >= h:
+        return mp.mpf(0), mp.mpf(0), mp.mpf(0), mp.mpf(0)
+    fns = cas_kernel_h()[0 if r < h / 2 else 1]
+    return tuple(fn(r, h) for fn in fns)
+
+
+def pin_soft_kernel_vs_cas(lib):
+    """W, dW/dr, dW/dh and dpsi/dh against sympy derivatives of W and of the
+    integrated potential kernel, at 40 digits."""
+    import mpmath as mp
+    mp.mp.dps = 40
+    for h in (0.37, 2.5):
+        for u in (1e-6, 0.1, 0.3, 0.4999, 0.5, 0.5001, 0.7, 0.95, 0.9999, 1.0, 1.7):
+            r = u * h
+            got = O.kernel_w(r, h, lib=lib)
+            ref = [float(x) for x in kernel_h_mp(r, h)]
+            scale = [8.0 / (np.pi * h**3), 8.0 / (np.pi * h**4), 8.0 / (np.pi * h**4), 1.0 / h**2]
+            for name, a, b, sc in zip(("W", "W_r", "W_h", "psi_h"), got, ref, scale):
+                assert abs(a - b) <= 1e-13 * sc, (name, h, u, a, b)
+
+
+def _soft_system(seed, n):
+    g = ics.rng(seed)
+    pos = g.normal(0.0, 1.0, (n, 3))
+    vel = g.normal(0.0, 1.0, (n, 3))
+    mass = g.uniform(0.5, 1.5, n)
+    return pos, vel, mass
+
+
+def pin_soft_constant_h(lib):
+    """Equal supports and no correction reduce to the fixed-h sums bit for bit
+    (the average of two equal kernels is exact)."""
+    pos, vel, mass = ics.plummer(90, seed=41)
+    a = O.eval_active(pos, vel, mass, h=0.3, lib=lib)
+    b = O.eval_soft(pos, vel, mass, np.full(90, 0.3), lib=lib)
+    for k in ("acc", "jerk", "tidal", "pot", "dt_grav"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def pin_soft_two_body(lib):
+    """Two elements with different supports: the pair force uses the mean of
+    the two CAS kernels (Newton's third law holds with both masses)."""
+    import mpmath as mp
+    mp.mp.dps = 40
+    G, m1, m2 = 1.3, 0.8, 0.7
+    x = np.array([[0.1, 0.2, -0.1], [0.25, 0.05, 0.1]])
+    h = np.array([0.5, 0.3])
+    o = O.eval_soft(x, np.zeros((2, 3)), np.array([m1, m2]), h, lib=lib, G=G)
+    d = x[1] - x[0]
+    r = float(np.linalg.norm(d))
+    k1, k2 = kernel_mp(r, h[0]), kernel_mp(r, h[1])
+    f = float((k1[0] + k2[0]) / 2)
+    g = float((k1[1] + k2[1]) / 2)
+    p = float((k1[2] + k2[2]) / 2)
+    _close(o["acc"][0], G * m2 * f * d, 1e-14, "soft two-body a1")
+    _close(o["acc"][1], -G * m1 * f * d, 1e-14, "soft two-body a2")
+    assert abs(o["pot"][0] + G * m2 * p) <= 1e-14 * G * m2 * p
+    T = -G * m2 * (f * np.eye(3) + g * np.outer(d, d))
+    t6 = np.array([T[0, 0], T[1, 1], T[2, 2], T[0, 1], T[0, 2], T[1, 2]])
+    assert np.allclose(o["tidal"][0], t6, rtol=1e-13, atol=1e-13 * np.abs(t6).max())
+
+
+def pin_soft_solve(lib):
+    """The supports solve (4 pi/3) h^3 rho = n_ngb m with rho summed by brute
+    force over the CAS kernel (self term included); Omega and zeta equal their
+    definitions summed the same way."""
+    import mpmath as mp
+    mp.mp.dps = 30
+    pos, vel, mass = _soft_system(51, 60)
+    n_ngb = 20.0
+    sol = O.soft_solve(pos, mass, 0.4, n_ngb=n_ngb, tol=1e-14, max_iter=200, lib=lib)
+    assert sol["converged"]
+    for i in (0, 7, 33, 59):
+        h = sol["h"][i]
+        rho = rho_h = psi_h = mp.mpf(0)
+        for j in range(60):
+            r = mp.sqrt(sum((mp.mpf(pos[j, c]) - mp.mpf(pos[i, c])) ** 2 for c in range(3)))
+            w, _, wh, ph = kernel_h_mp(r, h)
+            rho += mass[j] * w
+            rho_h += mass[j] * wh
+            if j != i:
+                psi_h += mass[j] * ph
+        F = 4 * mp.pi / 3 * mp.mpf(h) ** 3 * rho - n_ngb * mass[i]
+        assert abs(float(F)) <= 1e-12 * n_ngb * mass[i], (i, float(F))
+        omega = 1 + h * rho_h / (3 * rho)
+        zeta = -h * psi_h / (3 * rho * omega)
+        assert abs(sol["omega"][i] - float(omega)) <= 1e-11 * abs(float(omega)), i
+        assert abs(sol["zeta"][i] - float(zeta)) <= 1e-11 * abs(float(zeta)), i
+
+
+def pin_soft_energy_gradient(lib):
+    """With the correction the acceleration is -grad_i U / m_i, U the potential
+    energy with every support re-solved from the constraint (central
+    differences); without it the difference is at the per-cent level."""
+    pos, vel, mass = _soft_system(52, 40)
+    n_ngb, tau = 20.0, 1e-6
+
+    def energy(p):
+        s = O.soft_solve(p, mass, 1.0, n_ngb=n_ngb, tol=1e-15, max_iter=300, lib=lib)
+        assert s["converged"]
+        return 0.5 * float((mass * O.eval_soft(p, vel, mass, s["h"], lib=lib)["pot"]).sum())
+
+    sol = O.soft_solve(pos, mass, 1.0, n_ngb=n_ngb, tol=1e-15, max_iter=300, lib=lib)
+    full = O.eval_soft(pos, vel, mass, sol["h"], sol["zeta"], lib=lib)["acc"]
+    plain = O.eval_soft(pos, vel, mass, sol["h"], lib=lib)["acc"]
+    worst_plain = 0.0
+    for i in (0, 11, 25, 39):
+        fd = np.zeros(3)
+        for c in range(3):
+            pp = pos.copy()
+            pm = pos.copy()
+            pp[i, c] += tau
+            pm[i, c] -= tau
+            fd[c] = -(energy(pp) - energy(pm)) / (2 * tau) / mass[i]
+        _close(full[i], fd, 1e-6, "adaptive-softening force vs -grad U")
+        worst_plain = max(worst_plain, np.linalg.norm(plain[i] - fd) / np.linalg.norm(fd))
+    assert worst_plain > 1e-3, worst_plain
+
+
+def pin_soft_momentum(lib):
+    """The averaged pair force and the correction are antisymmetric in the pair:
+    sum m a = 0 and sum m j = 0."""
+    pos, vel, mass = ics.plummer(300, seed=53)
+    sol = O.soft_solve(pos, mass, 0.1, n_ngb=32.0, lib=lib)
+    o = O.eval_soft(pos, vel, mass, sol["h"], sol["zeta"], lib=lib)
+    for k in ("acc", "jerk"):
+        mom = (mass[:, None] * o[k]).sum(0)
+        assert np.all(np.abs(mom) <= 1e-13 * np.abs(mass[:, None] * o[k]).sum()), k
+
+
+def pin_soft_derivatives(lib):
+    """At fixed supports, jerk = d a / dt along the drift and T = d a_i / d x_i
+    (central differences; the correction term is not differentiated)."""
+    pos, vel, mass = ics.plummer(120, seed=54)
+    sol = O.soft_solve(pos, mass, 0.1, n_ngb=24.0, lib=lib)
+    h, tau = sol["h"], 1e-6
+    o = O.eval_soft(pos, vel, mass, h, lib=lib)
+    p = O.eval_soft(pos + tau * vel, vel, mass, h, lib=lib)
+    m = O.eval_soft(pos - tau * vel, vel, mass, h, lib=lib)
+    _close(o["jerk"], (p["acc"] - m["acc"]) / (2 * tau), 2e-6, "soft jerk vs FD")
+    i = 17
+    one = np.array([i], np.int32)
+    full = np.zeros((3, 3))
+    for c in range(3):
+        pp = pos.copy()
+        pm = pos.copy()
+        pp[i, c] += tau
+        pm[i, c] -= tau
+        full[:, c] = (O.eval_soft(pp, vel, mass, h, idx=one, lib=lib)["acc"][0]
+                      - O.eval_soft(pm, vel, mass, h, idx=one, lib=lib)["acc"][0]) / (2 * tau)
+    t6 = np.array([full[0, 0], full[1, 1], full[2, 2], full[0, 1], full[0, 2], full[1, 2]])
+    assert np.allclose(o["tidal"][i], t6, rtol=0, atol=2e-6 * np.abs(t6).max())
+
+
 def pin_update_counts(lib):
     """With fixed bins and dt_grav, an element of step s ticks is updated every
     ceil(q_f dt_grav / (s dt_min)) of its active steps (Eq. updatecondition),
@@ -716,6 +912,8 @@ ALL_PINS = [
     pin_momentum_balance, pin_trace_density, pin_cube_symmetry, pin_scaling, pin_jerk_fd,
     pin_tidal_fd, pin_tidal_dt, pin_periodic_translation, pin_periodic_two_body,
     pin_periodic_half_box_tie, pin_periodic_open_limit, pin_periodic_derivatives,
+    pin_soft_kernel_vs_cas, pin_soft_constant_h, pin_soft_two_body, pin_soft_solve,
+    pin_soft_energy_gradient, pin_soft_momentum, pin_soft_derivatives,
     pin_update_counts, pin_reverts_exactly, pin_bins, pin_compact,
     pin_predictor, pin_poly_history, pin_poly_predictor, pin_adjoint_fd,
 ]

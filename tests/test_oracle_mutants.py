@@ -57,6 +57,22 @@ MUTANTS = {
                          "for (int c = 0; c < 3; ++c) d[c] -= box * floor(d[c] / box + 0.5);"),
     "periodic_two_axes": ("for (int c = 0; c < 3; ++c) d[c] -= box * nearbyint(d[c] / box);",
                           "for (int c = 0; c < 2; ++c) d[c] -= box * nearbyint(d[c] / box);"),
+    "soft_corr_sign": ("fc = -0.5 * (zeta[i] * wri + zeta[j] * wrj) / r;",
+                       "fc = 0.5 * (zeta[i] * wri + zeta[j] * wrj) / r;"),
+    "soft_corr_drop_source": ("fc = -0.5 * (zeta[i] * wri + zeta[j] * wrj) / r;",
+                              "fc = -0.5 * (zeta[i] * wri) / r;"),
+    "soft_omega_one": ("double om = 1.0 + h * rho_h / (3.0 * rho);", "double om = 1.0;"),
+    "soft_dh_drho": ("if (zeta) zeta[i] = -h * psi_h / (3.0 * rho * om);",
+                     "if (zeta) zeta[i] = -h * psi_h / (2.0 * rho * om);"),
+    "soft_rho_no_self": ("                nadd(&sr, mass[j] * w);",
+                         "                if (j != i) nadd(&sr, mass[j] * w);"),
+    "soft_psi_with_self": ("                if (j != i) nadd(&sp, mass[j] * ph);",
+                           "                nadd(&sp, mass[j] * ph);"),
+    "soft_force_own_h": ("f = 0.5 * (fi + fj);", "f = fi;"),
+    "soft_g_own_h": ("g = 0.5 * (gi + gj);", "g = gi;"),
+    "soft_pot_own_h": ("phi = 0.5 * (pi_ + pj);", "phi = pi_;"),
+    "soft_w_h_term": ("*w_h = -c * (3.0 * wu + u * dwu) / h;", "*w_h = -c * (3.0 * wu - u * dwu) / h;"),
+    "soft_psi_h_power": ("*psi_h = -dup / (h * h);", "*psi_h = -dup / h;"),
     "adj_mass_sign": ("nadd(&mb, -f * da);", "nadd(&mb, f * da);"),
     "adj_g_term": ("nadd(&xb[c], f * ab[c] + g * d[c] * da);", "nadd(&xb[c], f * ab[c]);"),
     "adj_tidal_transposed": ("ta[0] = t6[0] * ak[0] + t6[3] * ak[1] + t6[4] * ak[2];",
