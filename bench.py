@@ -382,6 +382,7 @@ def extras(args, path, dev, sms, peak32, flush):
     out["predict"] = {"bytes_per_element": 82, "GB_per_s": bytes_pred / tp / 1e9, "us": tp * 1e6}
     out["predict_N16777216"] = predict_bandwidth(dev, 1 << 24)
     out["periodic_zeldovich_64cubed"] = periodic_extra(dev, flush)
+    out["adaptive_softening_N1048576"] = soft_extra(path, dev, flush)
     out["batched_256_systems"] = batched_extra(dev, flush)
     out["adaptive_plummer_131072"] = adaptive_extra(dev)
     try:
@@ -456,6 +457,56 @@ def periodic_extra(dev, flush):
         t = statistics.median(ts)
         res[name] = {"active_fraction": frac, "interactions_per_s": idx_np.size * n / t,
                      "ms": 1e3 * t}
+    return res
+
+
+def soft_extra(path, dev, flush):
+    """Adaptive softening on the headline cloud (2^20 elements): the support
+    solve for 32 neighbours from a uniform guess, then the mixed force sums of
+    every element with per-element supports and the correction term."""
+    import torch
+
+    from paper_2010_13792_gb300 import grav
+    n = path.n
+    f64 = lambda: torch.empty(n, dtype=torch.float64, device=dev)
+    h, zeta, omega = f64(), f64(), f64()
+    iters = torch.empty(n, dtype=torch.int32, device=dev)
+    flags = torch.zeros(1, dtype=torch.int32, device=dev)
+    sp = grav.soft_params(n_ngb=32.0, tol=1e-12, max_iter=100)
+    ws_s = grav.Workspace()
+    ts = []
+    for _ in range(3):
+        h.fill_(2e-2)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        grav.soft_solve(sp, path.pos, path.mass, h, zeta, omega, iters, flags, workspace=ws_s)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    it = iters.to(torch.float64)
+    res = {"n": n, "n_ngb": 32.0, "solve_ms": 1e3 * statistics.median(ts),
+           "iterations_median": float(it.median()), "iterations_max": int(iters.max()),
+           "flags": int(flags.item()), "h_median": float(h.median()),
+           "h_range": [float(h.min()), float(h.max())]}
+    acc = torch.empty(n, 3, dtype=torch.float64, device=dev)
+    jerk, tid = torch.empty_like(acc), torch.empty(n, 6, dtype=torch.float64, device=dev)
+    p = grav.params(h=1.0, precision=grav.MIXED)
+    ws_e = grav.Workspace()
+    grav.eval_soft(p, path.pos, path.vel, path.mass, h, zeta, None, None, n, acc, jerk, tid,
+                   workspace=ws_e)
+    ts = []
+    for _ in range(3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        grav.eval_soft(p, path.pos, path.vel, path.mass, h, zeta, None, None, n, acc, jerk, tid,
+                       workspace=ws_e)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    t = statistics.median(ts)
+    res["eval_mixed"] = {"interactions_per_s": n * n / t, "ms": 1e3 * t}
     return res
 
 

@@ -59,6 +59,7 @@ extern "C" {
 #define GRAV_FLAG_NONFINITE 1  /* a position, velocity, mass or a_bar was NaN or Inf */
 #define GRAV_FLAG_TIMEOUT   2  /* a bounded wait on a shared-memory copy gave up */
 #define GRAV_FLAG_BADINDEX  4  /* a target index outside [0, n_src), or a bin outside [0, k_max] */
+#define GRAV_FLAG_NOCONVERGE 8 /* a support iteration of grav_soft_solve ran out of iterations */
 
 /* Arithmetic of the force sums. */
 #define GRAV_F64   0  /* all pair arithmetic and sums in FP64 */
@@ -303,6 +304,71 @@ GRAV_API int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav_s
                                int64_t n_idx_max, double *acc, double *jerk, double *tidal,
                                double *pot, double *dt_grav, int32_t *flags_dev, void *workspace,
                                int64_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Adaptive softening: Section 3 runs every problem with fully adaptive       */
+/* softening and the extra force terms of Price & Monaghan (2007) that keep   */
+/* the energy conserved.  Readings (the paper gives no formulas): each        */
+/* element i has its own support h_i, fixed by the mass-density constraint    */
+/* (4 pi/3) h_i^3 rho_i = n_ngb m_i, rho_i = sum_j m_j W(r_ij, h_i) with the  */
+/* self term; a pair uses the mean of the kernels of supports h_i and h_j;    */
+/* the correction term makes a_i = -grad_i U / m_i for the potential energy   */
+/* U = (1/2) sum_i m_i Phi_i with every h following the constraint.           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct grav_soft_params {
+    double n_ngb;        /* effective neighbour number of the constraint (> 32/3, e.g. 32) */
+    double tol;          /* stop when |(4 pi/3) h^3 rho - n_ngb m| <= tol n_ngb m (>= 1e-15) */
+    int32_t max_iter;    /* iterations per element (1..10000); then GRAV_FLAG_NOCONVERGE */
+    int32_t pad;
+} grav_soft_params;
+
+/*
+ * grav_soft_solve -- supports and correction coefficients of n elements.
+ * Per element: safeguarded Newton iterations on h (starting from h_inout[i]
+ * > 0, kept in a bracket; a step leaving it doubles h or bisects) until the
+ * constraint holds to tol; then from the sums at that h
+ *   Omega_i = 1 + h_i / (3 rho_i) sum_j m_j dW(r_ij, h_i)/dh      (j = i included)
+ *   zeta_i  = -h_i / (3 rho_i Omega_i) sum_{j != i} m_j dpsi(r_ij, h_i)/dh
+ * (psi the potential kernel; dh/drho = -h/(3 rho)).  All FP64.
+ *   pos [n][3], mass [n] (> 0): device, in
+ *   h_inout [n]: device, in: starting guesses, out: supports
+ *   zeta_out, omega_out [n], iters_out [n] (iterations, -1 if the limit ran
+ *   out): device, out, each nullable
+ * A mass or guess that is not positive and finite sets GRAV_FLAG_NONFINITE
+ * and leaves that element's outputs unwritten.
+ * workspace: >= grav_soft_workspace_bytes(n) bytes, 256-byte aligned.
+ */
+GRAV_API int64_t grav_soft_workspace_bytes(int64_t n);
+GRAV_API int grav_soft_solve(const grav_soft_params *sp, int64_t n, const double *pos,
+                             const double *mass, double *h_inout, double *zeta_out,
+                             double *omega_out, int32_t *iters_out, int32_t *flags_dev,
+                             void *workspace, int64_t workspace_bytes, void *stream);
+
+/*
+ * grav_eval_soft -- grav_eval_active with per-element supports h_elem [n_src]
+ * (device, > 0; p->h is only validated) and, when zeta (device [n_src],
+ * nullable) is given, the correction term:
+ *   a_i   = G sum_j m_j fbar d
+ *           - (G/2) sum_j m_j [zeta_i W_r(r,h_i) + zeta_j W_r(r,h_j)] d / r
+ *   j_i   = G sum_j m_j [ fbar v_ji + gbar (d . v_ji) d ]
+ *   T_i   = -G sum_j m_j [ fbar I + gbar d d^T ]
+ *   Phi_i = -G sum_j m_j (phi(r,h_i) + phi(r,h_j)) / 2
+ * with fbar = (f(r,h_i) + f(r,h_j))/2, gbar likewise and W_r = dW/dr; jerk and
+ * tidal tensor are those of the averaged pair force at fixed supports.  Open
+ * boundaries only (p->box must be 0); targets, outputs, precisions and tile
+ * configurations as in grav_eval_active.  A support that is not positive and
+ * finite sets GRAV_FLAG_NONFINITE.
+ * workspace: >= grav_eval_soft_workspace_bytes(p, n_src, n_idx_max) bytes.
+ */
+GRAV_API int64_t grav_eval_soft_workspace_bytes(const grav_params *p, int64_t n_src,
+                                                int64_t n_idx_max);
+GRAV_API int grav_eval_soft(const grav_params *p, int64_t n_src, const double *pos,
+                            const double *vel, const double *mass, const double *h_elem,
+                            const double *zeta, const int32_t *idx, const int32_t *n_idx_dev,
+                            int64_t n_idx_max, double *acc, double *jerk, double *tidal,
+                            double *pot, double *dt_grav, int32_t *flags_dev, void *workspace,
+                            int64_t workspace_bytes, void *stream);
 
 /*
  * grav_selftest_wait_timeout -- failure-detection self-test (not part of the

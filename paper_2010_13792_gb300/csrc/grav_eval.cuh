@@ -65,6 +65,13 @@ struct __align__(16) D4 {
     double x, y, z, w;
 };
 
+// Boundary and softening mode of a force-kernel instantiation.
+enum : int {
+    kModeOpen = 0,       // open boundaries, one support h for every pair
+    kModePeriodic = 1,   // nearest periodic image in a cube of side box
+    kModeSoft = 2,       // per-element supports and the adaptive-softening correction
+};
+
 struct EvalArgs {
     int64_t n_src;
     const int32_t *idx;        // nullable: targets are 0..n_idx_max-1
@@ -89,6 +96,14 @@ struct EvalArgs {
     float box_f, box_inv_f;
     float box_tie_f;              // mixed path: |d_c| above it may be an ambiguous image
     float pad2;
+    // adaptive softening (kModeSoft): per-element supports h and correction
+    // coefficients zeta (zeta nullable: no correction), FP64 by element; the
+    // mixed kernels read them per source as (1/h, zeta) in FP32 from hz and
+    // the outward-rounded largest support of each source tile from geo_h
+    const double *h_elem;
+    const double *zeta;
+    const float2 *hz;
+    const float *geo_h;
 };
 
 // Number of source chunks per target block.  Shared by the host, the eval
@@ -719,6 +734,112 @@ __device__ __forceinline__ void periodic_loop_f(const float4 *__restrict__ stage
 }
 
 // ---------------------------------------------------------------------------
+// Adaptive softening: per-element supports (Section 3's fully adaptive
+// softening) with the energy-conserving correction term of Price & Monaghan
+// (2007).  A pair takes the mean of the kernels of support h_i (target) and
+// h_j (source); the acceleration gains
+//   -(1/2) m_j [zeta_i W_r(r, h_i) + zeta_j W_r(r, h_j)] d / r,
+// W_r = dW/dr, zeta the per-element coefficient from the support solve.  The
+// jerk and tidal sums use the averaged kernels at fixed supports.
+// ---------------------------------------------------------------------------
+
+// One side of a pair: force, g' and potential kernels of support 1/hinv at
+// separation r (Newtonian from ri beyond the support) and W_r.
+template <typename T>
+__device__ __forceinline__ void soft_side(T r, T ri, T hinv, T &f, T &gp, T &p, T &wr)
+{
+    const T u = r * hinv;
+    if (u < T(1)) {
+        T F, Gp, P;
+        spline_kernel<T>(u, F, Gp, P);
+        const T h2 = hinv * hinv;
+        const T h3 = h2 * hinv;
+        f = F * h3;
+        gp = Gp * h3 * h2;
+        p = P * hinv;
+        const T q = T(1) - u;
+        const T dw = (u < T(0.5)) ? u * (T(-12) + T(18) * u) : T(-6) * q * q;
+        wr = T(8.0 / 3.14159265358979323846) * (h2 * h2) * dw;
+    } else {
+        const T ri2 = ri * ri;
+        f = ri * ri2;
+        gp = f * ri2;
+        p = ri;
+        wr = T(0);
+    }
+}
+
+// Near tiles with per-element supports (mixed path).  hz: the tile's
+// (1/h_j, zeta_j) in shared memory; thinv, tzeta: the targets' 1/h_i, zeta_i.
+// Reads either tile layout one source at a time.
+template <int KT, int S, bool POT, bool PAIR>
+__device__ __forceinline__ void soft_loop_f(const float4 *__restrict__ stage,
+                                            const float2 *__restrict__ hz, const float tx[KT][3],
+                                            const int64_t ti[KT], int64_t jbase,
+                                            const float thinv[KT], const float tzeta[KT],
+                                            float acc[KT][kNCPot])
+{
+    const float *tile = reinterpret_cast<const float *>(stage);
+#pragma unroll 1
+    for (int j = 0; j < S; ++j) {
+        float x, y, z, m, vx, vy, vz;
+        if (PAIR) {
+            const int k = j >> 1, h = j & 1;
+            x = tile[4 * k + h];
+            y = tile[4 * k + 2 + h];
+            z = tile[2 * S + 4 * k + h];
+            m = tile[2 * S + 4 * k + 2 + h];
+            vx = tile[4 * S + 4 * k + h];
+            vy = tile[4 * S + 4 * k + 2 + h];
+            vz = tile[6 * S + 2 * k + h];
+        } else {
+            const float4 p = stage[j], v = stage[S + j];
+            x = p.x;
+            y = p.y;
+            z = p.z;
+            m = p.w;
+            vx = v.x;
+            vy = v.y;
+            vz = v.z;
+        }
+        const float2 sh = hz[j];
+        const int64_t jg = jbase + j;
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const float dx = x - tx[q][0], dy = y - tx[q][1], dz = z - tx[q][2];
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = rsqrt_sfu(r2);
+            const float ri2 = ri * ri;
+            float mp = m * ri;
+            float mf = mp * ri2;
+            float mg = mf * ri2;
+            if (r2 * (thinv[q] * thinv[q]) < 1.0f || r2 * (sh.x * sh.x) < 1.0f) {
+                const float r = sqrtf(r2);
+                float fi, gi, pi, wi, fj, gj, pj, wj;
+                soft_side<float>(r, ri, thinv[q], fi, gi, pi, wi);
+                soft_side<float>(r, ri, sh.x, fj, gj, pj, wj);
+                const float hm = 0.5f * m;
+                mf = hm * (fi + fj);
+                mg = hm * (gi + gj);
+                mp = hm * (pi + pj);
+                float ca = r > 0.0f ? -hm * fmaf(tzeta[q], wi, sh.y * wj) / r : 0.0f;
+                if (jg == ti[q]) {
+                    mf = 0.0f;
+                    mg = 0.0f;
+                    mp = 0.0f;
+                    ca = 0.0f;
+                }
+                acc[q][ESUM] += fmaf(-mg, r2, mf);
+                acc[q][A0 + 0] = fmaf(ca, dx, acc[q][A0 + 0]);
+                acc[q][A0 + 1] = fmaf(ca, dy, acc[q][A0 + 1]);
+                acc[q][A0 + 2] = fmaf(ca, dz, acc[q][A0 + 2]);
+            }
+            accumulate_f<KT, POT>(acc, q, dx, dy, dz, vx, vy, vz, mf, mg, mp);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Pair loops, FP64
 // ---------------------------------------------------------------------------
 
@@ -791,6 +912,76 @@ __device__ __forceinline__ void loop_d(const D4 *__restrict__ sp, const D4 *__re
         }
         accumulate_d<POT>(acc, dx, dy, dz, v.x - vi[0], v.y - vi[1], v.z - vi[2], mf, mg, mp);
     }
+}
+
+
+// Near tiles with per-element supports (FP64 path): the source supports and
+// coefficients are read from the caller's arrays (padding sources, j >= n_src,
+// have m = 0 and take h = 1, zeta = 0).
+template <int S, bool POT>
+__device__ __forceinline__ void soft_loop_d(const D4 *__restrict__ sp, const D4 *__restrict__ sv,
+                                            const double xi[3], const double vi[3], int64_t ti,
+                                            int64_t jbase, double hinv_i, double zeta_i,
+                                            const EvalArgs &a, double acc[kNCPot])
+{
+    const double h2i = 1.0 / (hinv_i * hinv_i);
+#pragma unroll 1
+    for (int j = 0; j < S; ++j) {
+        const D4 p = sp[j];
+        const D4 v = sv[j];
+        const int64_t jg = jbase + j;
+        const bool real = jg < a.n_src;
+        const double hj = real ? a.h_elem[jg] : 1.0;
+        const double zj = (real && a.zeta) ? a.zeta[jg] : 0.0;
+        const double dx = p.x - xi[0], dy = p.y - xi[1], dz = p.z - xi[2];
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const double ri = rsqrt(r2);
+        const double ri2 = ri * ri;
+        double mp = p.w * ri;
+        double mf = mp * ri2;
+        double mg = mf * ri2;
+        double ca = 0.0;
+        if (r2 < h2i || r2 < hj * hj) {
+            const double r = sqrt(r2);
+            double fi, gi, pi, wi, fj, gj, pj, wj;
+            soft_side<double>(r, ri, hinv_i, fi, gi, pi, wi);
+            soft_side<double>(r, ri, 1.0 / hj, fj, gj, pj, wj);
+            const double hm = 0.5 * p.w;
+            mf = hm * (fi + fj);
+            mg = hm * (gi + gj);
+            mp = hm * (pi + pj);
+            ca = r > 0.0 ? -hm * fma(zeta_i, wi, zj * wj) / r : 0.0;
+            if (jg == ti) {
+                mf = 0.0;
+                mg = 0.0;
+                mp = 0.0;
+                ca = 0.0;
+            }
+        }
+        accumulate_d<POT>(acc, dx, dy, dz, v.x - vi[0], v.y - vi[1], v.z - vi[2], mf, mg, mp);
+        acc[A0 + 0] = fma(ca, dx, acc[A0 + 0]);
+        acc[A0 + 1] = fma(ca, dy, acc[A0 + 1]);
+        acc[A0 + 2] = fma(ca, dz, acc[A0 + 2]);
+    }
+}
+
+// Largest value over the block (every thread passes one; all get the result).
+template <int NT>
+__device__ __forceinline__ float block_max(float v)
+{
+    __shared__ float wmax[NT / 32];
+    __shared__ float result;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = wmax[0];
+        for (int w = 1; w < NT / 32; ++w) m = fmaxf(m, wmax[w]);
+        result = m;
+    }
+    __syncthreads();
+    return result;
 }
 
 
@@ -942,7 +1133,7 @@ __device__ __forceinline__ void init_ring(Sm &sm)
 }
 
 // One work item of the mixed kernel; false if a bounded wait gave up.
-template <int NT, int KT, int S, int U, bool POT, bool SACC, bool PAIR, bool PER>
+template <int NT, int KT, int S, int U, bool POT, bool SACC, bool PAIR, int MODE>
 __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
                                            MixedSmem<NT, KT, S, POT, SACC, PAIR> &sm, Ring &ring,
                                            const ItemSpec &it)
@@ -952,6 +1143,7 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
     constexpr int NSTAGE = 2;
     constexpr int NC = Sm::NC;
     static_assert(!PAIR || KT == 1, "the paired layout serves one target per thread");
+    constexpr bool soft = MODE == kModeSoft;
     constexpr uint32_t kTileBytes = PAIR ? S * 28 : S * 2 * sizeof(float4);
     const float4 *src = static_cast<const float4 *>(a.src);
     const int t_begin = it.t_begin, t_end = it.t_end;
@@ -990,6 +1182,27 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
     const float blo_r[3] = {sm.blo[0], sm.blo[1], sm.blo[2]};
     const float bhi_r[3] = {sm.bhi[0], sm.bhi[1], sm.bhi[2]};
 
+    // adaptive softening: the targets' 1/h_i and zeta_i, the block's largest
+    // support, and the shared copy of a near tile's (1/h_j, zeta_j)
+    float thinv[soft ? KT : 1], tzeta[soft ? KT : 1];
+    float h_block = 0.0f;
+    __shared__ float2 soft_hz[soft ? S : 1];
+    if (soft) {
+        float hb = 0.0f;
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            thinv[soft ? q : 0] = 1.0f;
+            tzeta[soft ? q : 0] = 0.0f;
+            if (ti[q] >= 0) {
+                const double h = a.h_elem[ti[q]];
+                thinv[soft ? q : 0] = __double2float_rn(1.0 / h);
+                tzeta[soft ? q : 0] = a.zeta ? __double2float_rn(a.zeta[ti[q]]) : 0.0f;
+                hb = fmaxf(hb, __double2float_ru(h));
+            }
+        }
+        h_block = block_max<NT>(hb);
+    }
+
     float rhi[SACC ? 1 : KT][SACC ? 1 : kNCPot], rlo[SACC ? 1 : KT][SACC ? 1 : kNCPot];
     if (SACC) {
 #pragma unroll
@@ -1018,7 +1231,7 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
 
     // offsets of the targets to a tile's centre (FP64, rounded once); in a
     // periodic box, to the image of the centre nearest to the target
-    constexpr bool periodic = PER;
+    constexpr bool periodic = MODE == kModePeriodic;
     auto offsets = [&](const TileGeom &g, float out[KT][3]) {
 #pragma unroll
         for (int q = 0; q < KT; ++q)
@@ -1038,9 +1251,14 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
         const int s = (t - t_begin) % NSTAGE;
         // periodic: any target near the tile, or a tile that may reach past
         // half a box from a target's image of it, takes the general loop
+        float h2_tile = a.h2f_up;
+        if (soft) {
+            const float hm = fmaxf(h_block, a.geo_h[t]);
+            h2_tile = __fmul_ru(hm, hm);
+        }
         const bool near = periodic
             ? (__syncthreads_or(periodic_special<KT>(tx, ti, g, a.h2f_up, a.box_tie_f)) != 0)
-            : tile_is_near(blo_r, bhi_r, g, a.h2f_up);
+            : tile_is_near(blo_r, bhi_r, g, h2_tile);
         // next tile's geometry and offsets, computed ahead (FP64 latency)
         TileGeom gn = g;
         if (t + 1 < t_end) {
@@ -1058,7 +1276,12 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
         for (int q = 0; q < KT; ++q)
 #pragma unroll
             for (int c = 0; c < kNCPot; ++c) acc[q][c] = 0.0f;
-        if (periodic && near) {
+        if (soft && near) {
+            // the previous tile's reads of soft_hz ended at its closing barrier
+            for (int k = threadIdx.x; k < S; k += NT) soft_hz[k] = a.hz[(int64_t)t * S + k];
+            __syncthreads();
+            soft_loop_f<KT, S, POT, PAIR>(sm.stage[s], soft_hz, tx, ti, g.first, thinv, tzeta, acc);
+        } else if (periodic && near) {
             periodic_loop_f<KT, S, POT, PAIR>(sm.stage[s], tx, ti, g.first, a.h2f_up, a.hinvf, a,
                                               acc);
         } else if (PAIR) {
@@ -1154,7 +1377,7 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
     return !sm.abort_flag;
 }
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 __global__ void __launch_bounds__(NT, MINB)
 eval_mixed_kernel(const EvalArgs a)
 {
@@ -1182,7 +1405,7 @@ eval_mixed_kernel(const EvalArgs a)
         it.sp = sp;
         it.split = split;
         it.rows = n_tb * BT;
-        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, PER>(a, sm, ring, it)) break;
+        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }
     drain_ring<2>(sm.bar, ring, a.flags);
@@ -1192,7 +1415,7 @@ eval_mixed_kernel(const EvalArgs a)
 // ticket (no waiting on other CTAs).  Each target is summed by one CTA over
 // its system's tiles in a fixed order, so results do not depend on which CTA
 // takes which item.
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 __global__ void __launch_bounds__(NT, MINB)
 eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
 {
@@ -1222,7 +1445,7 @@ eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
         it.sp = 0;
         it.split = 1;
         it.rows = 0;
-        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, PER>(a, sm, ring, it)) break;
+        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }
     drain_ring<2>(sm.bar, ring, a.flags);
@@ -1241,7 +1464,7 @@ struct F64Smem {
     long long ticket;
 };
 
-template <int NT, int S, bool POT, bool PER>
+template <int NT, int S, bool POT, int MODE>
 __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring &ring,
                                          const ItemSpec &it)
 {
@@ -1270,6 +1493,18 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
     block_bbox<NT>(lo, hi, sm.blo, sm.bhi);
     const float blo_r[3] = {sm.blo[0], sm.blo[1], sm.blo[2]};
     const float bhi_r[3] = {sm.bhi[0], sm.bhi[1], sm.bhi[2]};
+    double hinv_i = 1.0, zeta_i = 0.0;
+    float h_block = 0.0f;
+    if (MODE == kModeSoft) {
+        float hb = 0.0f;
+        if (i >= 0) {
+            const double h = a.h_elem[i];
+            hinv_i = 1.0 / h;
+            zeta_i = a.zeta ? a.zeta[i] : 0.0;
+            hb = __double2float_ru(h);
+        }
+        h_block = block_max<NT>(hb);
+    }
 
     double shi[kNCPot], slo[kNCPot];
 #pragma unroll
@@ -1286,7 +1521,8 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
             }
         }
     }
-    constexpr bool periodic = PER;
+    constexpr bool periodic = MODE == kModePeriodic;
+    constexpr bool soft = MODE == kModeSoft;
     for (int t = t_begin; t < t_end; ++t) {
         const int s = (t - t_begin) % NSTAGE;
         const TileGeom g = a.geo[t];
@@ -1299,6 +1535,9 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
                 tw[0][c] = __double2float_rn(wrap_d(__dsub_rn(xi[c], g.c[c]), a.box, a.box_inv));
             // every FP64 periodic pair is wrapped; this only decides softening
             near = __syncthreads_or(periodic_special<1>(tw, ti1, g, a.h2f_up, a.box_tie_f)) != 0;
+        } else if (soft) {
+            const float hm = fmaxf(h_block, a.geo_h[t]);
+            near = tile_is_near(blo_r, bhi_r, g, __fmul_ru(hm, hm));
         } else {
             near = tile_is_near(blo_r, bhi_r, g, a.h2f_up);
         }
@@ -1310,7 +1549,10 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
         double acc[kNCPot];
 #pragma unroll
         for (int c = 0; c < kNCPot; ++c) acc[c] = 0.0;
-        if (periodic) {
+        if (soft && near) {
+            soft_loop_d<S, POT>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, hinv_i, zeta_i, a,
+                                acc);
+        } else if (periodic) {
             if (!near)
                 loop_d<S, POT, false, true>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, h2, hinv,
                                             acc, a.box, a.box_inv, a.box_tie);
@@ -1345,7 +1587,7 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
     return !sm.abort_flag;
 }
 
-template <int NT, int S, bool POT, bool PER>
+template <int NT, int S, bool POT, int MODE>
 __global__ void __launch_bounds__(NT, 2)
 eval_f64_kernel(const EvalArgs a)
 {
@@ -1370,13 +1612,13 @@ eval_f64_kernel(const EvalArgs a)
         it.sp = sp;
         it.split = split;
         it.rows = n_tb * NT;
-        if (!f64_item<NT, S, POT, PER>(a, sm, ring, it)) break;
+        if (!f64_item<NT, S, POT, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }
     drain_ring<2>(sm.bar, ring, a.flags);
 }
 
-template <int NT, int S, bool POT, bool PER>
+template <int NT, int S, bool POT, int MODE>
 __global__ void __launch_bounds__(NT, 2)
 eval_f64_batched_kernel(const EvalArgs a, const BatchView b)
 {
@@ -1403,7 +1645,7 @@ eval_f64_batched_kernel(const EvalArgs a, const BatchView b)
         it.sp = 0;
         it.split = 1;
         it.rows = 0;
-        if (!f64_item<NT, S, POT, PER>(a, sm, ring, it)) break;
+        if (!f64_item<NT, S, POT, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }
     drain_ring<2>(sm.bar, ring, a.flags);
@@ -1460,59 +1702,59 @@ typedef void (*batched_pack_fn)(const BatchView &, const double *, const double 
 struct EvalConfig {
     int32_t precision;
     int32_t threads, kt, s, unroll, sacc;
-    eval_launch_fn launch[2][2];   // [periodic][want_pot]
-    occupancy_fn occupancy[2][2];
+    eval_launch_fn launch[3][2];   // [mode][want_pot]
+    occupancy_fn occupancy[3][2];
     pack_launch_fn pack;
-    batched_launch_fn launch_batched[2][2];
+    batched_launch_fn launch_batched[2][2];   // [mode: open, periodic][want_pot]
     occupancy_fn occupancy_batched[2][2];
     batched_pack_fn pack_batched;
     bool paired;                   // mixed source tiles in the paired (FP32x2) layout
 };
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 void launch_mixed(const EvalArgs &a, int grid, cudaStream_t st)
 {
     constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
-    eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, PER><<<grid, NT, bytes, st>>>(a);
+    eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE><<<grid, NT, bytes, st>>>(a);
 }
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 int occupancy_mixed(int *b)
 {
     constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
-    auto k = eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, PER>;
+    auto k = eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, k, NT, bytes);
 }
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 void launch_mixed_batched(const EvalArgs &a, const BatchView &b, int grid, cudaStream_t st)
 {
     constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
-    eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, PER><<<grid, NT, bytes, st>>>(a, b);
+    eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE><<<grid, NT, bytes, st>>>(a, b);
 }
 
-template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, bool PER>
+template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 int occupancy_mixed_batched(int *b)
 {
     constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
-    auto k = eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, PER>;
+    auto k = eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, k, NT, bytes);
 }
 
-template <int NT, int S, bool POT, bool PER>
+template <int NT, int S, bool POT, int MODE>
 void launch_f64_batched(const EvalArgs &a, const BatchView &b, int grid, cudaStream_t st)
 {
-    eval_f64_batched_kernel<NT, S, POT, PER><<<grid, NT, 0, st>>>(a, b);
+    eval_f64_batched_kernel<NT, S, POT, MODE><<<grid, NT, 0, st>>>(a, b);
 }
 
-template <int NT, int S, bool POT, bool PER>
+template <int NT, int S, bool POT, int MODE>
 int occupancy_f64_batched(int *b)
 {
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_batched_kernel<NT, S, POT, PER>, NT, 0);
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_batched_kernel<NT, S, POT, MODE>, NT, 0);
 }
 
 template <int S, bool MIXED, bool VOFF, bool PAIR>
@@ -1522,16 +1764,16 @@ void launch_pack_batched(const BatchView &b, const double *pos, const double *ve
     pack_tiles_batched_kernel<S, MIXED, VOFF, PAIR><<<max_tiles, S, 0, st>>>(b, pos, vel, mass, geo, src, flags);
 }
 
-template <int NT, int S, bool POT, bool PER>
+template <int NT, int S, bool POT, int MODE>
 void launch_f64(const EvalArgs &a, int grid, cudaStream_t st)
 {
-    eval_f64_kernel<NT, S, POT, PER><<<grid, NT, 0, st>>>(a);
+    eval_f64_kernel<NT, S, POT, MODE><<<grid, NT, 0, st>>>(a);
 }
 
-template <int NT, int S, bool POT, bool PER>
+template <int NT, int S, bool POT, int MODE>
 int occupancy_f64(int *b)
 {
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_kernel<NT, S, POT, PER>, NT, 0);
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, eval_f64_kernel<NT, S, POT, MODE>, NT, 0);
 }
 
 template <int S, bool MIXED, bool VOFF, bool PAIR>

@@ -3,11 +3,17 @@
 
 namespace grav {
 
-#define GRAV_F64_FN2(FN, NT, S) \
-    {{FN<NT, S, false, false>, FN<NT, S, true, false>}, {FN<NT, S, false, true>, FN<NT, S, true, true>}}
+#define GRAV_F64_FN3(FN, NT, S)                                                                   \
+    {{FN<NT, S, false, kModeOpen>, FN<NT, S, true, kModeOpen>},                                      \
+     {FN<NT, S, false, kModePeriodic>, FN<NT, S, true, kModePeriodic>},                              \
+     {FN<NT, S, false, kModeSoft>, FN<NT, S, true, kModeSoft>}}
+
+#define GRAV_F64_FN2(FN, NT, S)                                                                   \
+    {{FN<NT, S, false, kModeOpen>, FN<NT, S, true, kModeOpen>},                                      \
+     {FN<NT, S, false, kModePeriodic>, FN<NT, S, true, kModePeriodic>}}
 
 #define GRAV_F64_CFG(NT, S)                                                                       \
-    {GRAV_F64, NT, 1, S, 4, 0, GRAV_F64_FN2(launch_f64, NT, S), GRAV_F64_FN2(occupancy_f64, NT, S), \
+    {GRAV_F64, NT, 1, S, 4, 0, GRAV_F64_FN3(launch_f64, NT, S), GRAV_F64_FN3(occupancy_f64, NT, S), \
      launch_pack<S, false, false, false>, GRAV_F64_FN2(launch_f64_batched, NT, S),                 \
      GRAV_F64_FN2(occupancy_f64_batched, NT, S), launch_pack_batched<S, false, false, false>, false}
 

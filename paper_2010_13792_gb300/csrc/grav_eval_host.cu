@@ -50,6 +50,35 @@ const EvalConfig *resolve(const grav_params *p, int *index)
     return &t[i];
 }
 
+// Per source tile for adaptive softening: (1/h_j, zeta_j) in FP32 in tile
+// order, padding (1, 0), and the tile's largest support rounded up.  One CTA
+// of 256 threads per tile of S sources; flags non-positive or non-finite h.
+__global__ void __launch_bounds__(256)
+pack_soft_kernel(int64_t n_src, int S, const double *__restrict__ h_elem,
+                 const double *__restrict__ zeta, float2 *__restrict__ hz, float *__restrict__ geo_h,
+                 int32_t *flags)
+{
+    const int64_t t = blockIdx.x;
+    float hmax = 0.0f;
+    for (int k = threadIdx.x; k < S; k += 256) {
+        const int64_t j = t * S + k;
+        float2 v = make_float2(1.0f, 0.0f);
+        if (j < n_src) {
+            const double h = h_elem[j];
+            const double z = zeta ? zeta[j] : 0.0;
+            if (!(h > 0.0) || !isfinite(h) || !isfinite(z)) {
+                flag_or(flags, GRAV_FLAG_NONFINITE);
+            } else {
+                v = make_float2(__double2float_rn(1.0 / h), __double2float_rn(z));
+                hmax = fmaxf(hmax, __double2float_ru(h));
+            }
+        }
+        hz[t * S + k] = v;
+    }
+    hmax = block_max<256>(hmax);
+    if (threadIdx.x == 0) geo_h[t] = hmax;
+}
+
 // Periodic-box fields of the kernel arguments.  Beyond the tie lengths a
 // pair separation component is formed again in FP64 with the image decided
 // by an exact division: half a box less 2^-20 box on the mixed path (an FP32
@@ -68,10 +97,10 @@ void set_box(EvalArgs &a, double box)
     a.pad2 = 0.0f;
 }
 
-int grid_for(const EvalConfig *c, int index, bool periodic, bool pot, int *grid)
+int grid_for(const EvalConfig *c, int index, int mode, bool pot, int *grid)
 {
     static std::mutex mu;
-    static int cache[64][2][16][2][2];   // [device][precision][config][periodic][pot]
+    static int cache[64][2][16][3][2];   // [device][precision][config][mode][pot]
     int dev = 0;
     int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     if (rc) return rc;
@@ -80,10 +109,10 @@ int grid_for(const EvalConfig *c, int index, bool periodic, bool pot, int *grid)
     if (rc) return rc;
     if (dev >= 64 || index >= 16) return fail(GRAV_ECUDA, "device or config index out of range");
     std::lock_guard<std::mutex> lk(mu);
-    int &slot = cache[dev][c->precision][index][periodic ? 1 : 0][pot ? 1 : 0];
+    int &slot = cache[dev][c->precision][index][mode][pot ? 1 : 0];
     if (slot == 0) {
         int b = 0;
-        rc = check_cuda((cudaError_t)c->occupancy[periodic ? 1 : 0][pot ? 1 : 0](&b), "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        rc = check_cuda((cudaError_t)c->occupancy[mode][pot ? 1 : 0](&b), "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
         if (rc) return rc;
         if (b < 1) return fail(GRAV_ECUDA, "force kernel cannot be resident on an SM");
         slot = b * sms;
@@ -96,11 +125,12 @@ struct Layout {
     int64_t n_tiles;
     int64_t geo_off, src_off, part_off, total;
     int64_t part_cap_rows;
+    int64_t hz_off, geo_h_off;     // adaptive softening only (else 0)
     int32_t max_split;
 };
 
 int make_layout(const grav_params *p, const EvalConfig *c, int64_t n_src, int64_t n_idx_max,
-                Layout *L)
+                Layout *L, bool soft = false)
 {
     int sms = 0;
     int rc = device_sm_count(&sms);
@@ -120,6 +150,12 @@ int make_layout(const grav_params *p, const EvalConfig *c, int64_t n_src, int64_
         blocks = std::min<int64_t>(n_tb_max * L->max_split, kSplitRowsPerSM * sms);
     L->part_cap_rows = blocks * BT;
     L->total = L->part_off + round_up(L->part_cap_rows * NC * 8, 256);
+    L->hz_off = L->geo_h_off = 0;
+    if (soft) {
+        L->hz_off = L->total;
+        L->geo_h_off = L->hz_off + round_up(L->n_tiles * S * (int64_t)sizeof(float2), 256);
+        L->total = L->geo_h_off + round_up(L->n_tiles * (int64_t)sizeof(float), 256);
+    }
     if (L->total < 256) L->total = 256;
     return GRAV_OK;
 }
@@ -153,36 +189,45 @@ extern "C" int grav_tile_config(int32_t precision, int32_t index, grav_tile_info
     return GRAV_OK;
 }
 
-extern "C" int64_t grav_eval_workspace_bytes(const grav_params *p, int64_t n_src, int64_t n_idx_max)
+namespace grav {
+namespace {
+
+int64_t workspace_bytes_for(const grav_params *p, int64_t n_src, int64_t n_idx_max, bool soft,
+                            const char *who)
 {
-    int rc = check_params(p, "grav_eval_workspace_bytes");
+    int rc = check_params(p, who);
     if (rc) return rc;
+    if (soft && p->box != 0.0)
+        return fail(GRAV_EINVAL, "%s: adaptive softening supports open boundaries only", who);
     if (n_src < 0 || n_idx_max < 0 || n_src > INT32_MAX || n_idx_max > INT32_MAX)
-        return fail(GRAV_EINVAL, "grav_eval_workspace_bytes: sizes outside [0, 2^31)");
+        return fail(GRAV_EINVAL, "%s: sizes outside [0, 2^31)", who);
     int index = 0;
     const EvalConfig *c = resolve(p, &index);
     Layout L;
-    rc = make_layout(p, c, n_src, n_idx_max, &L);
+    rc = make_layout(p, c, n_src, n_idx_max, &L, soft);
     if (rc) return rc;
     return L.total;
 }
 
-extern "C" int grav_eval_active(const grav_params *p, int64_t n_src, const double *pos,
-                                const double *vel, const double *mass, const int32_t *idx,
-                                const int32_t *n_idx_dev, int64_t n_idx_max, double *acc,
-                                double *jerk, double *tidal, double *pot, double *dt_grav,
-                                int32_t *flags_dev, void *workspace, int64_t workspace_bytes,
-                                void *stream)
+// One system: open boundaries, periodic box (p->box > 0) or per-element
+// adaptive softening (h_elem not NULL).
+int eval_single(const char *who, const grav_params *p, bool soft, int64_t n_src, const double *pos,
+                const double *vel, const double *mass, const double *h_elem, const double *zeta,
+                const int32_t *idx, const int32_t *n_idx_dev, int64_t n_idx_max, double *acc,
+                double *jerk, double *tidal, double *pot, double *dt_grav, int32_t *flags_dev,
+                void *workspace, int64_t workspace_bytes, void *stream)
 {
-    static const char *who = "grav_eval_active";
+    const int mode = soft ? kModeSoft : (p->box > 0.0 ? kModePeriodic : kModeOpen);
     int rc = check_params(p, who);
     if (rc) return rc;
+    if (soft && p->box != 0.0)
+        return fail(GRAV_EINVAL, "%s: adaptive softening supports open boundaries only", who);
     if (n_src < 0 || n_idx_max < 0 || n_src > INT32_MAX || n_idx_max > INT32_MAX)
         return fail(GRAV_EINVAL, "%s: sizes outside [0, 2^31)", who);
     if (!idx && n_idx_max != n_src)
         return fail(GRAV_EINVAL, "%s: idx is NULL but n_idx_max != n_src", who);
     if (n_src == 0 || n_idx_max == 0) return GRAV_OK;
-    if (!pos || !vel || !mass || !acc || !jerk || !tidal)
+    if (!pos || !vel || !mass || !acc || !jerk || !tidal || (soft && !h_elem))
         return fail(GRAV_EINVAL, "%s: null input or output array", who);
     if (p->want_pot && !pot) return fail(GRAV_EINVAL, "%s: want_pot set but pot is NULL", who);
     if (!workspace) return fail(GRAV_EINVAL, "%s: null workspace", who);
@@ -190,18 +235,18 @@ extern "C" int grav_eval_active(const grav_params *p, int64_t n_src, const doubl
     int index = 0;
     const EvalConfig *c = resolve(p, &index);
     Layout L;
-    rc = make_layout(p, c, n_src, n_idx_max, &L);
+    rc = make_layout(p, c, n_src, n_idx_max, &L, soft);
     if (rc) return rc;
     if (workspace_bytes < L.total)
         return fail(GRAV_ENOMEM, "%s: workspace of %lld bytes < %lld", who, (long long)workspace_bytes,
                     (long long)L.total);
     const bool want_pot = p->want_pot != 0;
     int grid = 0;
-    rc = grid_for(c, index, p->box > 0.0, want_pot, &grid);
+    rc = grid_for(c, index, mode, want_pot, &grid);
     if (rc) return rc;
 
     char *ws = static_cast<char *>(workspace);
-    EvalArgs a;
+    EvalArgs a{};
     a.n_src = n_src;
     a.idx = idx;
     a.n_idx_dev = n_idx_dev;
@@ -233,14 +278,27 @@ extern "C" int grav_eval_active(const grav_params *p, int64_t n_src, const doubl
     a.dt_grav = dt_grav;
     a.flags = flags_dev;
     set_box(a, p->box);
+    if (soft) {
+        a.h_elem = h_elem;
+        a.zeta = zeta;
+        a.hz = reinterpret_cast<const float2 *>(ws + L.hz_off);
+        a.geo_h = reinterpret_cast<const float *>(ws + L.geo_h_off);
+    }
 
     cudaStream_t st = as_stream(stream);
     c->pack(n_src, pos, vel, mass, const_cast<TileGeom *>(a.geo), const_cast<void *>(a.src), flags_dev,
             (int)L.n_tiles, st);
-    rc = check_launch("grav_eval_active/pack");
+    rc = check_launch("grav_eval/pack");
     if (rc) return rc;
-    c->launch[p->box > 0.0 ? 1 : 0][want_pot ? 1 : 0](a, grid, st);
-    rc = check_launch("grav_eval_active/eval");
+    if (soft) {
+        pack_soft_kernel<<<(unsigned)L.n_tiles, 256, 0, st>>>(
+            n_src, c->s, h_elem, zeta, const_cast<float2 *>(a.hz), const_cast<float *>(a.geo_h),
+            flags_dev);
+        rc = check_launch("grav_eval_soft/pack_soft");
+        if (rc) return rc;
+    }
+    c->launch[mode][want_pot ? 1 : 0](a, grid, st);
+    rc = check_launch("grav_eval/eval");
     if (rc) return rc;
     const int32_t BT = c->threads * c->kt;
     bool need_reduce = L.part_cap_rows > 0;
@@ -251,10 +309,48 @@ extern "C" int grav_eval_active(const grav_params *p, int64_t n_src, const doubl
     if (need_reduce) {
         int blocks = (int)((n_idx_max + 255) / 256);
         launch_reduce(a, BT, want_pot, c->precision == GRAV_MIXED, blocks, st);
-        rc = check_launch("grav_eval_active/reduce");
+        rc = check_launch("grav_eval/reduce");
         if (rc) return rc;
     }
     return GRAV_OK;
+}
+
+}  // namespace
+}  // namespace grav
+
+extern "C" int64_t grav_eval_workspace_bytes(const grav_params *p, int64_t n_src, int64_t n_idx_max)
+{
+    return workspace_bytes_for(p, n_src, n_idx_max, false, "grav_eval_workspace_bytes");
+}
+
+extern "C" int grav_eval_active(const grav_params *p, int64_t n_src, const double *pos,
+                                const double *vel, const double *mass, const int32_t *idx,
+                                const int32_t *n_idx_dev, int64_t n_idx_max, double *acc,
+                                double *jerk, double *tidal, double *pot, double *dt_grav,
+                                int32_t *flags_dev, void *workspace, int64_t workspace_bytes,
+                                void *stream)
+{
+    return eval_single("grav_eval_active", p, false, n_src, pos, vel, mass, nullptr, nullptr, idx,
+                       n_idx_dev, n_idx_max, acc, jerk, tidal, pot, dt_grav, flags_dev, workspace,
+                       workspace_bytes, stream);
+}
+
+extern "C" int64_t grav_eval_soft_workspace_bytes(const grav_params *p, int64_t n_src,
+                                                  int64_t n_idx_max)
+{
+    return workspace_bytes_for(p, n_src, n_idx_max, true, "grav_eval_soft_workspace_bytes");
+}
+
+extern "C" int grav_eval_soft(const grav_params *p, int64_t n_src, const double *pos,
+                              const double *vel, const double *mass, const double *h_elem,
+                              const double *zeta, const int32_t *idx, const int32_t *n_idx_dev,
+                              int64_t n_idx_max, double *acc, double *jerk, double *tidal,
+                              double *pot, double *dt_grav, int32_t *flags_dev, void *workspace,
+                              int64_t workspace_bytes, void *stream)
+{
+    return eval_single("grav_eval_soft", p, true, n_src, pos, vel, mass, h_elem, zeta, idx,
+                       n_idx_dev, n_idx_max, acc, jerk, tidal, pot, dt_grav, flags_dev, workspace,
+                       workspace_bytes, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -485,7 +581,7 @@ extern "C" int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav
     b.n_sys = n_sys;
     b.pad = 0;
 
-    EvalArgs a;
+    EvalArgs a{};
     a.n_src = n_total;
     a.idx = idx;
     a.n_idx_dev = n_idx_dev;

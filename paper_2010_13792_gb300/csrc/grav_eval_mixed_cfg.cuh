@@ -1,8 +1,9 @@
 // Tile configurations of the mixed-precision force kernel (K5), listed once
-// for the two translation units that instantiate them: open boundaries in
-// grav_eval_mixed.cu, the periodic box in grav_eval_mixed_periodic.cu (its
-// kernels are a separate instantiation, so the open kernels carry none of the
-// periodic code and keep their register allocation).
+// for the translation units that instantiate them: open boundaries in
+// grav_eval_mixed.cu, the periodic box in grav_eval_mixed_periodic.cu and
+// per-element adaptive softening in grav_eval_mixed_soft.cu (each mode is a
+// separate instantiation, so the open kernels carry none of the other modes'
+// code and keep their register allocation).
 #pragma once
 
 #include "grav_eval.cuh"
@@ -26,18 +27,21 @@
 // (512-source tiles were measured 2% faster but their longer FP32 partial
 // sums take the jerk's worst-case error past 1e-4 on dense inputs.)
 
-// The periodic-box launchers of one configuration: declared `extern` where
-// the table is built, defined in the periodic translation unit.
-#define GRAV_MIXED_PERIODIC_FNS(PREFIX, NT, KT, S, MINB, U, SACC, PAIR)                              \
-    PREFIX void launch_mixed<NT, KT, S, MINB, U, false, SACC, PAIR, true>(const EvalArgs &, int,      \
+// The launchers of one configuration in one mode (kModePeriodic with the
+// batched launch, kModeSoft without): declared `extern` where the table is
+// built, defined in the mode's own translation unit.
+#define GRAV_MIXED_MODE_FNS(PREFIX, MODE, NT, KT, S, MINB, U, SACC, PAIR)                           \
+    PREFIX void launch_mixed<NT, KT, S, MINB, U, false, SACC, PAIR, MODE>(const EvalArgs &, int,      \
                                                                            cudaStream_t);             \
-    PREFIX void launch_mixed<NT, KT, S, MINB, U, true, SACC, PAIR, true>(const EvalArgs &, int,       \
+    PREFIX void launch_mixed<NT, KT, S, MINB, U, true, SACC, PAIR, MODE>(const EvalArgs &, int,       \
                                                                           cudaStream_t);              \
-    PREFIX int occupancy_mixed<NT, KT, S, MINB, U, false, SACC, PAIR, true>(int *);                   \
-    PREFIX int occupancy_mixed<NT, KT, S, MINB, U, true, SACC, PAIR, true>(int *);                    \
-    PREFIX void launch_mixed_batched<NT, KT, S, MINB, U, false, SACC, PAIR, true>(                     \
+    PREFIX int occupancy_mixed<NT, KT, S, MINB, U, false, SACC, PAIR, MODE>(int *);                   \
+    PREFIX int occupancy_mixed<NT, KT, S, MINB, U, true, SACC, PAIR, MODE>(int *);
+
+#define GRAV_MIXED_BATCHED_FNS(PREFIX, MODE, NT, KT, S, MINB, U, SACC, PAIR)                        \
+    PREFIX void launch_mixed_batched<NT, KT, S, MINB, U, false, SACC, PAIR, MODE>(                     \
         const EvalArgs &, const BatchView &, int, cudaStream_t);                                      \
-    PREFIX void launch_mixed_batched<NT, KT, S, MINB, U, true, SACC, PAIR, true>(                      \
+    PREFIX void launch_mixed_batched<NT, KT, S, MINB, U, true, SACC, PAIR, MODE>(                      \
         const EvalArgs &, const BatchView &, int, cudaStream_t);                                      \
-    PREFIX int occupancy_mixed_batched<NT, KT, S, MINB, U, false, SACC, PAIR, true>(int *);           \
-    PREFIX int occupancy_mixed_batched<NT, KT, S, MINB, U, true, SACC, PAIR, true>(int *);
+    PREFIX int occupancy_mixed_batched<NT, KT, S, MINB, U, false, SACC, PAIR, MODE>(int *);           \
+    PREFIX int occupancy_mixed_batched<NT, KT, S, MINB, U, true, SACC, PAIR, MODE>(int *);

@@ -5,8 +5,9 @@
 
 namespace grav {
 
-#define GRAV_MIXED_DEFINE(NT, KT, S, MINB, U, SACC, PAIR) \
-    GRAV_MIXED_PERIODIC_FNS(template, NT, KT, S, MINB, U, SACC, PAIR)
+#define GRAV_MIXED_DEFINE(NT, KT, S, MINB, U, SACC, PAIR)                      \
+    GRAV_MIXED_MODE_FNS(template, kModePeriodic, NT, KT, S, MINB, U, SACC, PAIR) \
+    GRAV_MIXED_BATCHED_FNS(template, kModePeriodic, NT, KT, S, MINB, U, SACC, PAIR)
 GRAV_MIXED_CONFIG_LIST(GRAV_MIXED_DEFINE)
 
 }  // namespace grav

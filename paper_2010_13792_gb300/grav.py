@@ -30,6 +30,7 @@ GRAV_ENOMEM = -5
 FLAG_NONFINITE = 1
 FLAG_TIMEOUT = 2
 FLAG_BADINDEX = 4
+FLAG_NOCONVERGE = 8
 
 F64 = 0
 MIXED = 1
@@ -68,6 +69,15 @@ def params(*, G: float = 1.0, h: float, eta: float = 0.01, precision: int = MIXE
                   int(tile_config), int(max_split), float(box))
 
 
+class SoftParams(ctypes.Structure):
+    _fields_ = [("n_ngb", _c_dbl), ("tol", _c_dbl), ("max_iter", _c_i32), ("pad", _c_i32)]
+
+
+def soft_params(*, n_ngb: float = 32.0, tol: float = 1e-12, max_iter: int = 100) -> SoftParams:
+    """Support constraint (4 pi/3) h^3 rho = n_ngb m and its iteration limits."""
+    return SoftParams(float(n_ngb), float(tol), int(max_iter), 0)
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -101,6 +111,13 @@ _SIGS = {
     "grav_eval_backward": (ctypes.c_int, [ctypes.POINTER(Params), _c_i64, _c_ptr, _c_ptr, _c_ptr,
                                           _c_dbl, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                           _c_ptr, _c_i64, _c_ptr]),
+    "grav_soft_workspace_bytes": (_c_i64, [_c_i64]),
+    "grav_soft_solve": (ctypes.c_int, [ctypes.POINTER(SoftParams), _c_i64, _c_ptr, _c_ptr, _c_ptr,
+                                       _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr]),
+    "grav_eval_soft_workspace_bytes": (_c_i64, [ctypes.POINTER(Params), _c_i64, _c_i64]),
+    "grav_eval_soft": (ctypes.c_int, [ctypes.POINTER(Params), _c_i64, _c_ptr, _c_ptr, _c_ptr,
+                                      _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr, _c_ptr,
+                                      _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr]),
     "grav_measure_fma_peak": (ctypes.c_int, [_c_i32, _c_dbl, ctypes.POINTER(_c_dbl), _c_ptr]),
     "grav_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_uint32, _c_ptr, _c_ptr]),
 }
@@ -341,6 +358,60 @@ def eval_active(p: Params, pos, vel, mass, idx, n_idx_dev, n_idx_max: int, acc, 
         _ptr(flags, torch.int32, "flags", (1,), allow_none=True),
         ctypes.c_void_p(buf.data_ptr()), nb, _stream(stream))
     _err("grav_eval_active", rc)
+
+
+def soft_workspace_bytes(n: int) -> int:
+    nb = int(lib().grav_soft_workspace_bytes(int(n)))
+    if nb < 0:
+        _err("grav_soft_workspace_bytes", nb)
+    return nb
+
+
+def soft_solve(sp: SoftParams, pos, mass, h, zeta=None, omega=None, iters=None, flags=None,
+               workspace: Workspace | None = None, stream=None):
+    """Supports h (in: guesses, out: solution) and the correction coefficients."""
+    n = mass.numel()
+    dev = mass.device
+    nb = soft_workspace_bytes(n)
+    buf = _ws(workspace, "soft", dev).get(nb, dev)
+    rc = lib().grav_soft_solve(
+        ctypes.byref(sp), n, _ptr(pos, torch.float64, "pos", (n, 3)),
+        _ptr(mass, torch.float64, "mass", (n,)), _ptr(h, torch.float64, "h", (n,)),
+        _ptr(zeta, torch.float64, "zeta", (n,), allow_none=True),
+        _ptr(omega, torch.float64, "omega", (n,), allow_none=True),
+        _ptr(iters, torch.int32, "iters", (n,), allow_none=True),
+        _ptr(flags, torch.int32, "flags", (1,), allow_none=True),
+        ctypes.c_void_p(buf.data_ptr()), nb, _stream(stream))
+    _err("grav_soft_solve", rc)
+
+
+def eval_soft_workspace_bytes(p: Params, n_src: int, n_idx_max: int) -> int:
+    nb = int(lib().grav_eval_soft_workspace_bytes(ctypes.byref(p), int(n_src), int(n_idx_max)))
+    if nb < 0:
+        _err("grav_eval_soft_workspace_bytes", nb)
+    return nb
+
+
+def eval_soft(p: Params, pos, vel, mass, h, zeta, idx, n_idx_dev, n_idx_max: int, acc, jerk, tidal,
+              pot=None, dt_grav=None, flags=None, workspace: Workspace | None = None, stream=None):
+    """eval_active with per-element supports h and (zeta not None) the correction term."""
+    n = mass.numel()
+    dev = mass.device
+    nb = eval_soft_workspace_bytes(p, n, n_idx_max)
+    buf = _ws(workspace, "eval_soft", dev).get(nb, dev)
+    rc = lib().grav_eval_soft(
+        ctypes.byref(p), n, _ptr(pos, torch.float64, "pos", (n, 3)),
+        _ptr(vel, torch.float64, "vel", (n, 3)), _ptr(mass, torch.float64, "mass", (n,)),
+        _ptr(h, torch.float64, "h", (n,)), _ptr(zeta, torch.float64, "zeta", (n,), allow_none=True),
+        _ptr(idx, torch.int32, "idx", allow_none=True),
+        _ptr(n_idx_dev, torch.int32, "n_idx_dev", (1,), allow_none=True), int(n_idx_max),
+        _ptr(acc, torch.float64, "acc", (n, 3)), _ptr(jerk, torch.float64, "jerk", (n, 3)),
+        _ptr(tidal, torch.float64, "tidal", (n, 6)),
+        _ptr(pot, torch.float64, "pot", (n,), allow_none=True),
+        _ptr(dt_grav, torch.float64, "dt_grav", (n,), allow_none=True),
+        _ptr(flags, torch.int32, "flags", (1,), allow_none=True),
+        ctypes.c_void_p(buf.data_ptr()), nb, _stream(stream))
+    _err("grav_eval_soft", rc)
 
 
 BATCH_MAX_SYSTEMS = 16384

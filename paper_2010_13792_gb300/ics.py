@@ -20,6 +20,8 @@ Stand-ins (the paper's own initial conditions are not published):
   * ``zeldovich_box``   -- periodic cube [0, L)^3: a lattice displaced by one
     sinusoidal mode along x (the shape of the Zeldovich pancake of Section 3,
     without the cosmology), velocities along the displacement.
+  * ``soft_inputs``     -- seeded per-element supports and correction
+    coefficients for adaptive-softening parity runs at large N.
   * ``morton_order``    -- stable sort by 63-bit Morton key so that consecutive
     index ranges are spatially compact (applied once at creation time).
 """
@@ -122,7 +124,7 @@ def _grf_component(g: np.random.Generator, ng: int, index: float) -> np.ndarray:
     nz = k2 > 0
     amp[nz] = k2[nz] ** (index / 4.0)        # sqrt(P) with P ~ k^index
     noise = g.normal(size=k2.shape) + 1j * g.normal(size=k2.shape)
-    return np.fft.irfftn(noise * amp, s=(ng, ng, ng))
+    return np.fft.irfftn(noise * amp, s=(ng, ng, ng), axes=(0, 1, 2))
 
 
 def _trilinear(field: np.ndarray, pos: np.ndarray, lo: float, hi: float) -> np.ndarray:
@@ -184,6 +186,19 @@ def zeldovich_box(n_side: int = 64, L: float = 1.0, amplitude: float = 0.1, jitt
     vel[:, 0] = -disp                      # converging flow toward the pancake plane
     vel += g.normal(0.0, 1e-3, (n, 3))
     return _finish(pos, vel, sort)
+
+
+def soft_inputs(pos: np.ndarray, h0: float, seed: int = BASE_SEED + 7):
+    """Seeded per-element supports and correction coefficients for parity runs
+    of the adaptive-softening sums at sizes where solving the supports on the
+    CPU is out of reach: h_i = h0 * (1 + |x_i|^2)^(1/2) * U(0.7, 1.3) (larger
+    supports in sparser outskirts) and zeta_i = U(0.02, 0.3) * h_i^2 (the
+    coefficient's scale, h^2).  Inputs only: neither is solved here."""
+    g = rng(seed)
+    n = pos.shape[0]
+    h = h0 * np.sqrt(1.0 + (np.asarray(pos) ** 2).sum(axis=1)) * g.uniform(0.7, 1.3, n)
+    zeta = g.uniform(0.02, 0.3, n) * h * h
+    return h, zeta
 
 
 def active_subset(n: int, fraction: float, seed: int) -> np.ndarray:

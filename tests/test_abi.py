@@ -85,6 +85,36 @@ def test_host_side_argument_checks(libgrav):
     assert L.grav_measure_fma_peak(5, 1.0, None, None) == grav.GRAV_EINVAL
 
 
+def test_adaptive_softening_argument_checks(libgrav):
+    from paper_2010_13792_gb300 import grav
+    L = grav.lib()
+    for sp in (grav.soft_params(n_ngb=10.0), grav.soft_params(n_ngb=float("inf")),
+               grav.soft_params(tol=0.0), grav.soft_params(tol=1e-17), grav.soft_params(max_iter=0),
+               grav.soft_params(max_iter=10001)):
+        assert L.grav_soft_solve(ctypes.byref(sp), 10, None, None, None, None, None, None, None,
+                                 None, 0, None) == grav.GRAV_EINVAL
+    sp = grav.soft_params()
+    assert L.grav_soft_solve(ctypes.byref(sp), -1, None, None, None, None, None, None, None, None,
+                             0, None) == grav.GRAV_EINVAL
+    assert L.grav_soft_solve(ctypes.byref(sp), 0, None, None, None, None, None, None, None, None,
+                             0, None) == grav.GRAV_OK
+    assert L.grav_soft_solve(ctypes.byref(sp), 10, None, None, None, None, None, None, None, None,
+                             0, None) == grav.GRAV_EINVAL
+    assert L.grav_soft_workspace_bytes(-1) == grav.GRAV_EINVAL
+    assert L.grav_soft_workspace_bytes(1000) >= 1000 * 32
+    # adaptive softening is for open boundaries only
+    p = grav.params(h=0.1, box=1.0)
+    assert L.grav_eval_soft_workspace_bytes(ctypes.byref(p), 10, 10) == grav.GRAV_EINVAL
+    assert L.grav_eval_soft(ctypes.byref(p), 10, None, None, None, None, None, None, None, 10, None,
+                            None, None, None, None, None, None, 0, None) == grav.GRAV_EINVAL
+    p = grav.params(h=0.1)
+    assert L.grav_eval_soft(ctypes.byref(p), 0, None, None, None, None, None, None, None, 0, None,
+                            None, None, None, None, None, None, 0, None) == grav.GRAV_OK
+    # per-element supports are required
+    assert L.grav_eval_soft(ctypes.byref(p), 10, None, None, None, None, None, None, None, 10, None,
+                            None, None, None, None, None, None, 0, None) == grav.GRAV_EINVAL
+
+
 def test_python_binding_rejects_cpu_tensors():
     import torch
     from paper_2010_13792_gb300 import grav
