@@ -327,8 +327,9 @@ int oracle_soft_sums(int64_t n, const double *pos, const double *mass, const dou
 }
 
 /* Solves (4 pi / 3) h_i^3 rho_i(h_i) = n_ngb m_i for every element by Newton
- * iterations kept inside a bracket [lo, hi] (F(h) is non-decreasing in h);
- * a step that leaves the bracket doubles h (no upper end yet) or bisects.
+ * iterations limited to a factor of 2 in h and kept inside a bracket
+ * [lo, hi] (F(h) is non-decreasing in h); a step that leaves the bracket
+ * doubles h (no upper end yet) or bisects.
  * h[] holds the starting guesses on entry.  Converged when
  * |F| <= tol * n_ngb * m_i; the sums of the last iteration are those at the
  * returned h, from which zeta follows:
@@ -377,7 +378,14 @@ int oracle_soft_solve(int64_t n, const double *pos, const double *mass, double n
             if (fabs(F) <= tol * target) { done = 1; break; }
             if (F < 0.0) lo = h; else hi = h;
             double dF = 4.0 * ORACLE_PI * h * h * rho + vol * rho_h;
-            double hn = (dF > 0.0) ? h - F / dF : -1.0;
+            /* Newton step, limited to a factor of 2 in h (with only the self
+             * term inside, F is flat and the plain step would be huge) */
+            double hn = (F < 0.0) ? 2.0 * h : 0.5 * h;
+            if (dF > 0.0) {
+                hn = h - F / dF;
+                if (hn > 2.0 * h) hn = 2.0 * h;
+                if (hn < 0.5 * h) hn = 0.5 * h;
+            }
             if (!(hn > lo && hn < hi)) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
             h = hn;
         }
