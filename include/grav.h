@@ -326,8 +326,9 @@ typedef struct grav_soft_params {
 /*
  * grav_soft_solve -- supports and correction coefficients of n elements.
  * Per element: safeguarded Newton iterations on h (starting from h_inout[i]
- * > 0, kept in a bracket; a step leaving it doubles h or bisects) until the
- * constraint holds to tol; then from the sums at that h
+ * > 0, each step limited to a factor of 2 and kept in a bracket; a step
+ * leaving it doubles h or bisects) until the constraint holds to tol; then
+ * from the sums at that h
  *   Omega_i = 1 + h_i / (3 rho_i) sum_j m_j dW(r_ij, h_i)/dh      (j = i included)
  *   zeta_i  = -h_i / (3 rho_i Omega_i) sum_{j != i} m_j dpsi(r_ij, h_i)/dh
  * (psi the potential kernel; dh/drho = -h/(3 rho)).  All FP64.

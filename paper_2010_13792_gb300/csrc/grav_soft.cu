@@ -13,11 +13,15 @@
 // the coefficient of the correction term the force kernels add.
 //
 // One thread per element, 128 per CTA.  Sources are packed once into tiles
-// of 128 (FP64 position and mass) with outward-rounded FP32 bounding boxes;
-// in every pass a CTA tests all tile boxes against its own box grown by the
-// largest support still iterating (one tile per thread, compacted by ballot)
-// and sums only the tiles that can hold a neighbour.  All arithmetic is FP64
-// and every loop is bounded by max_iter passes.
+// of 128: FP64 position and mass, FP32 offsets from the tile's centre, and an
+// outward-rounded FP32 bounding box.  In every pass a CTA tests all tile boxes
+// against its own box grown by the largest support still iterating (one tile
+// per thread, compacted by ballot); for each such tile a thread skips it when
+// its own element is farther than h from the box, and otherwise pre-filters
+// every source with an FP32 distance test that carries an explicit bound on
+// its rounding, so the FP64 sums (the distance test that decides, W, dW/dh,
+// dpsi/dh) run only for candidate neighbours.  Newton steps are limited to a
+// factor of 2 in h.  Every loop is bounded by max_iter passes.
 #include <cmath>
 
 #include "grav_common.cuh"
@@ -31,6 +35,9 @@ static_assert(kSoftNT == kSoftS, "each thread stages one source of a tile");
 
 struct SoftBox {
     float lo[3], hi[3];
+    double c[3];      // centre of the FP64 box; the FP32 offsets are taken from it
+    float ext;        // largest |x - c| component over the tile, rounded up
+    float pad;
 };
 
 struct SoftArgs {
@@ -39,6 +46,7 @@ struct SoftArgs {
     const double *mass;
     const SoftBox *box;
     const double4 *src;        // [tile][S] (x, y, z, m)
+    const float4 *src32;       // [tile][S] FP32 (x - c, y - c, z - c, 0)
     int64_t n_tiles;
     double n_ngb, tol;
     int32_t max_iter;
@@ -51,6 +59,9 @@ struct SoftArgs {
 __global__ void __launch_bounds__(kSoftS) soft_pack_kernel(SoftArgs a)
 {
     __shared__ float slo[3][kSoftS / 32], shi[3][kSoftS / 32];
+    __shared__ double dlo[3][kSoftS / 32], dhi[3][kSoftS / 32];
+    __shared__ double cen[3];
+    __shared__ float sext[kSoftS / 32];
     const int64_t t = blockIdx.x;
     const int64_t j = t * kSoftS + threadIdx.x;
     double4 v = make_double4(0.0, 0.0, 0.0, 0.0);
@@ -74,28 +85,65 @@ __global__ void __launch_bounds__(kSoftS) soft_pack_kernel(SoftArgs a)
         v.x = 1.0e300;          // padding: m = 0, never within a support
     }
     const_cast<double4 *>(a.src)[j] = v;
+    const bool real = j < a.n;
+    const double x[3] = {v.x, v.y, v.z};
+    double xl[3], xh[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+        xl[c] = real ? x[c] : 1.0e300;
+        xh[c] = real ? x[c] : -1.0e300;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
             hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+            xl[c] = fmin(xl[c], __shfl_xor_sync(0xffffffffu, xl[c], o));
+            xh[c] = fmax(xh[c], __shfl_xor_sync(0xffffffffu, xh[c], o));
         }
         if ((threadIdx.x & 31) == 0) {
             slo[c][threadIdx.x >> 5] = lo[c];
             shi[c][threadIdx.x >> 5] = hi[c];
+            dlo[c][threadIdx.x >> 5] = xl[c];
+            dhi[c][threadIdx.x >> 5] = xh[c];
         }
     }
     __syncthreads();
+    SoftBox *b = const_cast<SoftBox *>(a.box) + t;
     if (threadIdx.x < 3) {
         float l = slo[threadIdx.x][0], h = shi[threadIdx.x][0];
+        double L = dlo[threadIdx.x][0], H = dhi[threadIdx.x][0];
         for (int w = 1; w < kSoftS / 32; ++w) {
             l = fminf(l, slo[threadIdx.x][w]);
             h = fmaxf(h, shi[threadIdx.x][w]);
+            L = fmin(L, dlo[threadIdx.x][w]);
+            H = fmax(H, dhi[threadIdx.x][w]);
         }
-        SoftBox *b = const_cast<SoftBox *>(a.box) + t;
         b->lo[threadIdx.x] = l;
         b->hi[threadIdx.x] = h;
+        const double cc = 0.5 * (L + H);
+        b->c[threadIdx.x] = cc;
+        cen[threadIdx.x] = cc;
+    }
+    __syncthreads();
+    // FP32 offsets from the centre and the largest offset component
+    float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float e = 0.0f;
+    if (real) {
+        o = make_float4(__double2float_rn(v.x - cen[0]), __double2float_rn(v.y - cen[1]),
+                        __double2float_rn(v.z - cen[2]), 0.0f);
+        e = fmaxf(fabsf(o.x), fmaxf(fabsf(o.y), fabsf(o.z)));
+    } else {
+        o.x = 3.0e38f;            // padding: beyond every support
+    }
+    const_cast<float4 *>(a.src32)[j] = o;
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, k));
+    if ((threadIdx.x & 31) == 0) sext[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = sext[0];
+        for (int w = 1; w < kSoftS / 32; ++w) m = fmaxf(m, sext[w]);
+        b->ext = __fmul_ru(m, 1.0f + 0x1p-20f);
+        b->pad = 0.0f;
     }
 }
 
@@ -138,6 +186,7 @@ __device__ __forceinline__ bool box_near(const float blo[3], const float bhi[3],
 __global__ void __launch_bounds__(kSoftNT) soft_solve_kernel(SoftArgs a)
 {
     __shared__ double4 sx[kSoftS];
+    __shared__ float4 sx32[kSoftS];
     __shared__ int32_t list[kSoftNT];
     __shared__ int32_t wcount[kSoftNT / 32];
     __shared__ float rlo[3][kSoftNT / 32], rhi[3][kSoftNT / 32], rh[kSoftNT / 32];
@@ -207,6 +256,8 @@ __global__ void __launch_bounds__(kSoftNT) soft_solve_kernel(SoftArgs a)
         // ---- sums at the current supports over the tiles that can reach ----
         double rho = 0.0, rho_h = 0.0, psi_h = 0.0;
         const double hinv = 1.0 / h, h2 = h * h;
+        const float hf = __double2float_ru(h);
+        const float hlim2 = __fmul_ru(hf, hf);
         for (int64_t t0 = 0; t0 < a.n_tiles; t0 += kSoftNT) {
             const int64_t tt = t0 + threadIdx.x;
             const bool near = tt < a.n_tiles && box_near(B_lo, B_hi, a.box[tt], H);
@@ -223,18 +274,40 @@ __global__ void __launch_bounds__(kSoftNT) soft_solve_kernel(SoftArgs a)
             for (int k = 0; k < total; ++k) {
                 const int64_t t = t0 + list[k];
                 sx[threadIdx.x] = a.src[t * kSoftS + threadIdx.x];   // kSoftNT == kSoftS
+                sx32[threadIdx.x] = a.src32[t * kSoftS + threadIdx.x];
+                const SoftBox tb = a.box[t];
                 __syncthreads();
                 if (!done) {
-                    for (int j = 0; j < kSoftS; ++j) {
-                        const double4 s = sx[j];
-                        const double dx = s.x - xi[0], dy = s.y - xi[1], dz = s.z - xi[2];
-                        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                        if (r2 < h2) {
-                            double w, wh, ph;
-                            density_terms(sqrt(r2) * hinv, hinv, w, wh, ph);
-                            rho = fma(s.w, w, rho);
-                            rho_h = fma(s.w, wh, rho_h);
-                            if (t * kSoftS + j != i) psi_h = fma(s.w, ph, psi_h);
+                    // own offset from the tile centre (FP64, rounded once) and
+                    // a lower bound of the distance to the tile's box
+                    float tq[3], tmax = 0.0f, gap2 = 0.0f;
+                    for (int c = 0; c < 3; ++c) {
+                        tq[c] = __double2float_rn(xi[c] - tb.c[c]);
+                        tmax = fmaxf(tmax, fabsf(tq[c]));
+                        const float gap = fmaxf(0.0f, __fsub_rd(__fsub_rd(fabsf(tq[c]), tb.ext),
+                                                                 __fmul_ru(fabsf(tq[c]), 0x1p-22f)));
+                        gap2 = __fmaf_rd(gap, gap, gap2);
+                    }
+                    if (gap2 < hlim2) {
+                        // |d32 - d| <= err per component: both offsets were
+                        // rounded once and their difference once more
+                        const float err = __fmul_ru(__fadd_ru(tb.ext, tmax), 0x1p-21f);
+                        const float hl = __fadd_ru(hf, __fmul_ru(err, 1.8f));
+                        const float lim = __fmul_ru(__fmul_ru(hl, hl), 1.0f + 0x1p-20f);
+                        for (int j = 0; j < kSoftS; ++j) {
+                            const float4 q = sx32[j];
+                            const float ex = q.x - tq[0], ey = q.y - tq[1], ez = q.z - tq[2];
+                            if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) >= lim) continue;
+                            const double4 s = sx[j];
+                            const double dx = s.x - xi[0], dy = s.y - xi[1], dz = s.z - xi[2];
+                            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                            if (r2 < h2) {
+                                double w, wh, ph;
+                                density_terms(sqrt(r2) * hinv, hinv, w, wh, ph);
+                                rho = fma(s.w, w, rho);
+                                rho_h = fma(s.w, wh, rho_h);
+                                if (t * kSoftS + j != i) psi_h = fma(s.w, ph, psi_h);
+                            }
                         }
                     }
                 }
@@ -262,7 +335,10 @@ __global__ void __launch_bounds__(kSoftNT) soft_solve_kernel(SoftArgs a)
             } else {
                 if (F < 0.0) lo = h; else hi = h;
                 const double dF = 4.0 * 3.14159265358979323846 * h * h * rho + vol * rho_h;
-                double hn = dF > 0.0 ? h - F / dF : -1.0;
+                // Newton step limited to a factor of 2 (flat F when only the
+                // self term lies inside), then kept inside the bracket
+                double hn = F < 0.0 ? 2.0 * h : 0.5 * h;
+                if (dF > 0.0) hn = fmin(fmax(h - F / dF, 0.5 * h), 2.0 * h);
                 if (!(hn > lo && hn < hi)) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
                 h = hn;
                 ++it;
@@ -277,12 +353,13 @@ __global__ void __launch_bounds__(kSoftNT) soft_solve_kernel(SoftArgs a)
     }
 }
 
-int soft_layout(int64_t n, int64_t *box_off, int64_t *src_off, int64_t *total)
+int soft_layout(int64_t n, int64_t *box_off, int64_t *src_off, int64_t *src32_off, int64_t *total)
 {
     const int64_t n_tiles = (n + kSoftS - 1) / kSoftS;
     *box_off = 0;
     *src_off = round_up(n_tiles * (int64_t)sizeof(SoftBox), 256);
-    *total = std::max<int64_t>(256, *src_off + round_up(n_tiles * kSoftS * (int64_t)sizeof(double4), 256));
+    *src32_off = *src_off + round_up(n_tiles * kSoftS * (int64_t)sizeof(double4), 256);
+    *total = std::max<int64_t>(256, *src32_off + round_up(n_tiles * kSoftS * (int64_t)sizeof(float4), 256));
     return GRAV_OK;
 }
 
@@ -294,8 +371,8 @@ using namespace grav;
 extern "C" int64_t grav_soft_workspace_bytes(int64_t n)
 {
     if (n < 0 || n > INT32_MAX) return fail(GRAV_EINVAL, "grav_soft_workspace_bytes: n outside [0, 2^31)");
-    int64_t b, s, t;
-    soft_layout(n, &b, &s, &t);
+    int64_t b, s, s32, t;
+    soft_layout(n, &b, &s, &s32, &t);
     return t;
 }
 
@@ -317,8 +394,8 @@ extern "C" int grav_soft_solve(const grav_soft_params *sp, int64_t n, const doub
     if (!pos || !mass || !h_inout) return fail(GRAV_EINVAL, "%s: null pos, mass or h", who);
     if (!workspace || !aligned(workspace, 256))
         return fail(GRAV_EINVAL, "%s: workspace null or not 256-byte aligned", who);
-    int64_t box_off, src_off, total;
-    soft_layout(n, &box_off, &src_off, &total);
+    int64_t box_off, src_off, src32_off, total;
+    soft_layout(n, &box_off, &src_off, &src32_off, &total);
     if (workspace_bytes < total)
         return fail(GRAV_ENOMEM, "%s: workspace of %lld bytes < %lld", who, (long long)workspace_bytes,
                     (long long)total);
@@ -329,6 +406,7 @@ extern "C" int grav_soft_solve(const grav_soft_params *sp, int64_t n, const doub
     a.mass = mass;
     a.box = reinterpret_cast<const SoftBox *>(ws + box_off);
     a.src = reinterpret_cast<const double4 *>(ws + src_off);
+    a.src32 = reinterpret_cast<const float4 *>(ws + src32_off);
     a.n_tiles = (n + kSoftS - 1) / kSoftS;
     a.n_ngb = sp->n_ngb;
     a.tol = sp->tol;
