@@ -674,3 +674,299 @@ int oracle_backward(int64_t n, const double *pos, const double *mass, const doub
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Approximate solver: the oct-tree code of Section 3 (Barnes & Hut with the  */
+/* geometric opening criterion L/r > Theta always splitting a node, Theta =   */
+/* 0.5; optionally the relative criterion of the tree-code it supplements).   */
+/*                                                                            */
+/* Readings (the paper gives the criterion, not the tree):                    */
+/*  - the root is the cube of side ext = the largest extent of the elements'  */
+/*    bounding box, at its low corner; an element's cell coordinates are      */
+/*    q_c = floor((x_c - lo_c) / ext * 2^21), clamped to [0, 2^21 - 1], its   */
+/*    key the 63-bit interleave (x, y, z from the highest bit down);          */
+/*  - elements are ordered by (key, index); a node at level l holds the run   */
+/*    of elements sharing the key's top 3l bits, side L = ext 2^-l; it is a   */
+/*    leaf when it holds at most leaf_size elements or l = 21, otherwise its  */
+/*    non-empty octants are its children, in octant order;                    */
+/*  - node moments are monopoles: mass M, centre of mass and mean velocity,   */
+/*    summed in order (a leaf over its elements, a node over its children);   */
+/*  - from the root, a node is accepted when L^2 < Theta^2 r^2 (r from the   */
+/*    target to the node's centre of mass) and, if alpha > 0 and a_old is    */
+/*    given, also G M L^2 <= alpha |a_old,i| r^4; an accepted node acts as a  */
+/*    point mass M at its centre of mass moving with its mean velocity (the   */
+/*    same softened pair terms as the direct sum, with h); a leaf that is not */
+/*    accepted is summed element by element (j != i); any other node is       */
+/*    opened, its children visited in octant order.                          */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t first, count;       /* run in the sorted order */
+    int64_t child_first;        /* -1 for a leaf */
+    int32_t n_child, level;
+    double m, com[3], vcom[3];
+} tnode;
+
+typedef struct {
+    uint64_t key;
+    int64_t idx;
+} tkey;
+
+static int tkey_cmp(const void *a, const void *b)
+{
+    const tkey *x = (const tkey *)a, *y = (const tkey *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+static uint64_t spread21(uint64_t v)
+{
+    uint64_t out = 0;
+    for (int b = 0; b < 21; ++b) out |= ((v >> b) & 1u) << (3 * b);
+    return out;
+}
+
+typedef struct {
+    int64_t n;
+    const double *pos, *vel, *mass;
+    int64_t *order;
+    uint64_t *keys;
+    tnode *nodes;
+    int64_t n_nodes, cap;
+    double lo[3], ext;
+    int32_t leaf_size;
+} otree;
+
+/* Children of node k (its run already set), appended contiguously. */
+static int tree_split(otree *t, int64_t k)
+{
+    tnode *nd = &t->nodes[k];
+    nd->child_first = -1;
+    nd->n_child = 0;
+    if (nd->count <= t->leaf_size || nd->level >= 21) return 0;
+    int shift = 3 * (20 - nd->level);
+    int64_t cnt[8] = {0};
+    for (int64_t s = nd->first; s < nd->first + nd->count; ++s) cnt[(t->keys[s] >> shift) & 7u]++;
+    int nc = 0;
+    for (int o = 0; o < 8; ++o) nc += cnt[o] > 0;
+    if (t->n_nodes + nc > t->cap) return -1;
+    int64_t base = t->n_nodes, f = nd->first;
+    int32_t lvl = nd->level;
+    t->n_nodes += nc;
+    nd = &t->nodes[k];
+    nd->child_first = base;
+    nd->n_child = nc;
+    int c = 0;
+    for (int o = 0; o < 8; ++o) {
+        if (!cnt[o]) continue;
+        tnode *ch = &t->nodes[base + c++];
+        ch->first = f;
+        ch->count = cnt[o];
+        ch->level = lvl + 1;
+        f += cnt[o];
+    }
+    return nc;
+}
+
+static void tree_moments(otree *t, int64_t k)
+{
+    tnode *nd = &t->nodes[k];
+    double m = 0.0, mx[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
+    if (nd->child_first < 0) {
+        for (int64_t s = nd->first; s < nd->first + nd->count; ++s) {
+            int64_t j = t->order[s];
+            double mj = t->mass[j];
+            m = m + mj;
+            for (int c = 0; c < 3; ++c) {
+                mx[c] = mx[c] + mj * t->pos[3 * j + c];
+                mv[c] = mv[c] + mj * t->vel[3 * j + c];
+            }
+        }
+    } else {
+        for (int q = 0; q < nd->n_child; ++q) {
+            tnode *ch = &t->nodes[nd->child_first + q];
+            m = m + ch->m;
+            for (int c = 0; c < 3; ++c) {
+                mx[c] = mx[c] + ch->m * ch->com[c];
+                mv[c] = mv[c] + ch->m * ch->vcom[c];
+            }
+        }
+    }
+    nd->m = m;
+    for (int c = 0; c < 3; ++c) {
+        nd->com[c] = m > 0.0 ? mx[c] / m : 0.0;
+        nd->vcom[c] = m > 0.0 ? mv[c] / m : 0.0;
+    }
+}
+
+static int tree_build(otree *t)
+{
+    int64_t n = t->n;
+    double hi[3];
+    for (int c = 0; c < 3; ++c) {
+        t->lo[c] = INFINITY;
+        hi[c] = -INFINITY;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int c = 0; c < 3; ++c) {
+            if (t->pos[3 * i + c] < t->lo[c]) t->lo[c] = t->pos[3 * i + c];
+            if (t->pos[3 * i + c] > hi[c]) hi[c] = t->pos[3 * i + c];
+        }
+    t->ext = 0.0;
+    for (int c = 0; c < 3; ++c)
+        if (hi[c] - t->lo[c] > t->ext) t->ext = hi[c] - t->lo[c];
+    if (!(t->ext > 0.0)) t->ext = 1.0;
+    tkey *kv = (tkey *)malloc((size_t)n * sizeof(tkey));
+    if (!kv) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t q[3];
+        for (int c = 0; c < 3; ++c) {
+            double s = floor((t->pos[3 * i + c] - t->lo[c]) / t->ext * 2097152.0);
+            if (s < 0.0) s = 0.0;
+            if (s > 2097151.0) s = 2097151.0;
+            q[c] = (uint64_t)s;
+        }
+        kv[i].key = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+        kv[i].idx = i;
+    }
+    qsort(kv, (size_t)n, sizeof(tkey), tkey_cmp);
+    for (int64_t s = 0; s < n; ++s) {
+        t->order[s] = kv[s].idx;
+        t->keys[s] = kv[s].key;
+    }
+    free(kv);
+    t->nodes[0].first = 0;
+    t->nodes[0].count = n;
+    t->nodes[0].level = 0;
+    t->n_nodes = 1;
+    for (int64_t k = 0; k < t->n_nodes; ++k)       /* breadth first */
+        if (tree_split(t, k) < 0) return -1;
+    for (int64_t k = t->n_nodes - 1; k >= 0; --k)   /* children come after parents */
+        tree_moments(t, k);
+    return 0;
+}
+
+typedef struct {
+    nsum a[3], jk[3], tt[6], ph;
+    int64_t inter;
+} tacc;
+
+static void tree_pair(tacc *s, double m, const double d[3], const double v[3], double h)
+{
+    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double f, g, phi;
+    oracle_kernel(r, h, &f, &g, &phi);
+    double dv = d[0] * v[0] + d[1] * v[1] + d[2] * v[2];
+    for (int c = 0; c < 3; ++c) {
+        nadd(&s->a[c], m * f * d[c]);
+        nadd(&s->jk[c], m * (f * v[c] + g * dv * d[c]));
+    }
+    nadd(&s->tt[0], -m * (f + g * d[0] * d[0]));
+    nadd(&s->tt[1], -m * (f + g * d[1] * d[1]));
+    nadd(&s->tt[2], -m * (f + g * d[2] * d[2]));
+    nadd(&s->tt[3], -m * (g * d[0] * d[1]));
+    nadd(&s->tt[4], -m * (g * d[0] * d[2]));
+    nadd(&s->tt[5], -m * (g * d[1] * d[2]));
+    nadd(&s->ph, -m * phi);
+    s->inter++;
+}
+
+static void tree_walk(const otree *t, int64_t k, int64_t i, double G, double h, double theta2,
+                      double rel, tacc *s)
+{
+    const tnode *nd = &t->nodes[k];
+    const double *xi = &t->pos[3 * i], *vi = &t->vel[3 * i];
+    double d[3] = {nd->com[0] - xi[0], nd->com[1] - xi[1], nd->com[2] - xi[2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double L = ldexp(t->ext, -nd->level);
+    double L2 = L * L;
+    int accept = L2 < theta2 * r2;
+    if (accept && rel > 0.0) accept = (G * nd->m) * L2 <= (rel * r2) * r2;
+    if (accept) {
+        double v[3] = {nd->vcom[0] - vi[0], nd->vcom[1] - vi[1], nd->vcom[2] - vi[2]};
+        tree_pair(s, nd->m, d, v, h);
+        return;
+    }
+    if (nd->child_first < 0) {
+        for (int64_t q = nd->first; q < nd->first + nd->count; ++q) {
+            int64_t j = t->order[q];
+            if (j == i) continue;
+            double dj[3] = {t->pos[3 * j] - xi[0], t->pos[3 * j + 1] - xi[1], t->pos[3 * j + 2] - xi[2]};
+            double vj[3] = {t->vel[3 * j] - vi[0], t->vel[3 * j + 1] - vi[1], t->vel[3 * j + 2] - vi[2]};
+            tree_pair(s, t->mass[j], dj, vj, h);
+        }
+        return;
+    }
+    for (int q = 0; q < nd->n_child; ++q) tree_walk(t, nd->child_first + q, i, G, h, theta2, rel, s);
+}
+
+/*
+ * Tree-code evaluation at n_tgt targets (idx[t], or t when idx is NULL) over
+ * all n elements: outputs per target slot as in oracle_eval.  theta >= 0;
+ * leaf_size >= 1; alpha > 0 with a_old [n][3] adds the relative criterion.
+ * order_out [n] (nullable): the elements in tree order; n_nodes_out and
+ * interactions_out (nullable): node count and total interactions (accepted
+ * nodes plus leaf pairs).
+ */
+int oracle_tree_eval(int64_t n, const double *pos, const double *vel, const double *mass,
+                     int64_t n_tgt, const int32_t *idx, double G, double h, double eta,
+                     double theta, int32_t leaf_size, double alpha, const double *a_old,
+                     double *acc, double *jerk, double *tidal, double *pot, double *dt_grav,
+                     int64_t *order_out, int64_t *n_nodes_out, int64_t *interactions_out,
+                     int nthreads)
+{
+    if (n < 1 || n_tgt < 0 || !(h > 0.0) || !(theta >= 0.0) || leaf_size < 1 || alpha < 0.0)
+        return -1;
+    if (!pos || !vel || !mass || (n_tgt > 0 && (!acc || !jerk || !tidal))) return -1;
+    otree t;
+    memset(&t, 0, sizeof t);
+    t.n = n;
+    t.pos = pos;
+    t.vel = vel;
+    t.mass = mass;
+    t.leaf_size = leaf_size;
+    t.cap = 2 * n + 22 * (n / (leaf_size + 1) + 1) + 64;
+    t.order = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    t.keys = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    t.nodes = (tnode *)calloc((size_t)t.cap, sizeof(tnode));
+    int rc = (t.order && t.keys && t.nodes) ? tree_build(&t) : -1;
+    if (rc == 0) {
+        if (order_out) memcpy(order_out, t.order, (size_t)n * sizeof(int64_t));
+        if (n_nodes_out) *n_nodes_out = t.n_nodes;
+        set_threads(nthreads);
+        const double theta2 = theta * theta;
+        int bad = 0;
+        int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(|: bad) reduction(+: total)
+        for (int64_t s = 0; s < n_tgt; ++s) {
+            int64_t i = idx ? (int64_t)idx[s] : s;
+            if (i < 0 || i >= n) { bad = 1; continue; }
+            tacc ac;
+            memset(&ac, 0, sizeof ac);
+            double rel = 0.0;
+            if (alpha > 0.0 && a_old) {
+                const double *ao = &a_old[3 * i];
+                rel = alpha * sqrt(ao[0] * ao[0] + ao[1] * ao[1] + ao[2] * ao[2]);
+            }
+            tree_walk(&t, 0, i, G, h, theta2, rel, &ac);
+            total += ac.inter;
+            double t6[6];
+            for (int c = 0; c < 3; ++c) {
+                acc[3 * s + c] = G * nval(&ac.a[c]);
+                jerk[3 * s + c] = G * nval(&ac.jk[c]);
+            }
+            for (int c = 0; c < 6; ++c) {
+                t6[c] = G * nval(&ac.tt[c]);
+                tidal[6 * s + c] = t6[c];
+            }
+            if (pot) pot[s] = G * nval(&ac.ph);
+            if (dt_grav) dt_grav[s] = oracle_tidal_dt(t6, eta);
+        }
+        if (interactions_out) *interactions_out = total;
+        if (bad) rc = -1;
+    }
+    free(t.order);
+    free(t.keys);
+    free(t.nodes);
+    return rc;
+}

@@ -98,6 +98,11 @@ def load(path: str | None = None):
                                          _i32p, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp,
                                          _dp, _dp, ctypes.c_int]
         lib.oracle_eval_soft.restype = ctypes.c_int
+        lib.oracle_tree_eval.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_int64, _i32p,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int32, ctypes.c_double, _dp,
+                                         _dp, _dp, _dp, _dp, _dp, _i64p, _i64p, _i64p, ctypes.c_int]
+        lib.oracle_tree_eval.restype = ctypes.c_int
         if path is None:
             _lib = lib
         return lib
@@ -229,6 +234,41 @@ def eval_soft(pos, vel, mass, h, zeta=None, idx=None, *, G=1.0, eta=0.01, want_p
                               _p(out["pot"], _dp), _p(out["dt_grav"], _dp), int(nthreads))
     if rc != 0:
         raise ValueError("oracle_eval_soft: bad arguments")
+    return out
+
+
+def tree_eval(pos, vel, mass, idx=None, *, G=1.0, h, eta=0.01, theta=0.5, leaf_size=8,
+              alpha=0.0, a_old=None, want_pot=True, nthreads: int = 0, lib=None):
+    """Oct-tree (Barnes-Hut, monopole) a, jerk, tidal, potential and dt_grav at
+    targets; also returns the tree order, node count and interaction count."""
+    lib = lib or load()
+    pos = _c(pos, np.float64)
+    vel = _c(vel, np.float64)
+    mass = _c(mass, np.float64)
+    a_old = None if a_old is None else _c(a_old, np.float64)
+    n = mass.shape[0]
+    if idx is not None:
+        idx = _c(idx, np.int32)
+        nt = idx.shape[0]
+    else:
+        nt = n
+    out = {
+        "acc": np.zeros((nt, 3)), "jerk": np.zeros((nt, 3)), "tidal": np.zeros((nt, 6)),
+        "pot": np.zeros(nt) if want_pot else None, "dt_grav": np.zeros(nt),
+        "order": np.zeros(n, np.int64),
+    }
+    nn = np.zeros(1, np.int64)
+    ni = np.zeros(1, np.int64)
+    rc = lib.oracle_tree_eval(n, _p(pos, _dp), _p(vel, _dp), _p(mass, _dp), nt, _p(idx, _i32p),
+                              float(G), float(h), float(eta), float(theta), int(leaf_size),
+                              float(alpha), _p(a_old, _dp), _p(out["acc"], _dp),
+                              _p(out["jerk"], _dp), _p(out["tidal"], _dp), _p(out["pot"], _dp),
+                              _p(out["dt_grav"], _dp), _p(out["order"], _i64p), _p(nn, _i64p),
+                              _p(ni, _i64p), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_tree_eval: bad arguments")
+    out["n_nodes"] = int(nn[0])
+    out["interactions"] = int(ni[0])
     return out
 
 

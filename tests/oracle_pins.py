@@ -28,7 +28,12 @@ or the mathematics fixes:
   force sums; the corrected acceleration equal to -grad U / m with every
   support re-solved (central differences), the uncorrected one not; equal
   supports reducing to the fixed-h sums bit for bit; momentum balance;
-  jerk and tidal tensor as derivatives at fixed supports.
+  jerk and tidal tensor as derivatives at fixed supports;
+* the oct-tree: Theta = 0 equal to the direct sum; the tree order against
+  Morton keys written out independently; monopole error bounds at Theta =
+  0.5 shrinking with Theta; a far cluster acting as one moving point mass;
+  jerk and tidal tensor as derivatives of the tree field; the relative
+  criterion only opening more nodes.
 
 The mutation test runs these pins against copies of the oracle with planted
 mistakes and requires every mutant to fail at least one pin.
@@ -667,6 +672,143 @@ def pin_soft_derivatives(lib):
     assert np.allclose(o["tidal"][i], t6, rtol=0, atol=2e-6 * np.abs(t6).max())
 
 
+# ---------------------------------------------------------------------------
+# Approximate solver: oct-tree with the geometric opening criterion
+# ---------------------------------------------------------------------------
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+def pin_tree_theta_zero(lib):
+    """Theta = 0 opens every node down to its leaves: the direct sum."""
+    pos, vel, mass = ics.plummer(700, seed=61)
+    d = O.eval_active(pos, vel, mass, h=0.01, lib=lib)
+    t = O.tree_eval(pos, vel, mass, h=0.01, theta=0.0, leaf_size=5, lib=lib)
+    assert t["interactions"] == 700 * 699
+    for k in ("acc", "jerk", "tidal"):
+        assert np.all(_rel(t[k], d[k]) <= 1e-13), k
+    assert np.all(np.abs(t["pot"] - d["pot"]) <= 1e-13 * np.abs(d["pot"]))
+
+
+def pin_tree_order(lib):
+    """Tree order = elements sorted by (63-bit Morton key, index), keys from
+    the bounding cube quantised to 2^21 cells per axis (written out here)."""
+    pos, vel, mass = ics.uniform_sphere(500, seed=62, sort=False)
+    lo = pos.min(axis=0)
+    ext = float((pos.max(axis=0) - lo).max())
+    q = np.clip(np.floor((pos - lo) / ext * 2.0**21), 0, 2**21 - 1).astype(np.int64)
+    keys = []
+    for i in range(500):
+        k = 0
+        for b in range(20, -1, -1):
+            k = (k << 3) | (((q[i, 0] >> b) & 1) << 2) | (((q[i, 1] >> b) & 1) << 1) | ((q[i, 2] >> b) & 1)
+        keys.append((k, i))
+    want = [i for _, i in sorted(keys)]
+    got = O.tree_eval(pos, vel, mass, h=0.01, lib=lib)["order"]
+    assert list(got) == want
+
+
+def pin_tree_error_bounds(lib):
+    """Monopole Barnes-Hut errors: small at Theta = 0.5 and shrinking with Theta."""
+    pos, vel, mass = ics.plummer(4000, seed=63)
+    d = O.eval_active(pos, vel, mass, h=0.01, lib=lib)
+    med = []
+    for th in (0.3, 0.5, 0.7):
+        t = O.tree_eval(pos, vel, mass, h=0.01, theta=th, lib=lib)
+        e = _rel(t["acc"], d["acc"])
+        med.append(np.median(e))
+        if th == 0.5:
+            assert np.median(e) < 5e-3 and np.percentile(e, 99) < 3e-2, (np.median(e), e.max())
+            assert t["interactions"] < 0.3 * 4000 * 3999
+    assert med[0] < med[1] < med[2], med
+
+
+def pin_tree_far_cluster(lib):
+    """A compact cluster B far from cluster A: every element of A sees B as
+    one point mass at B's centre of mass moving with B's mean velocity, and
+    the rest of A element by element."""
+    g = ics.rng(64)
+    na = 6                       # cluster A fits in one leaf (leaf_size 8)
+    a = g.uniform(-0.05, 0.05, (na, 3))
+    b = g.uniform(1.95, 3.6, (30, 3))   # fills the far octant: splits below its top node
+    pos = np.vstack([a, b])
+    vel = g.normal(0.0, 1.0, (na + 30, 3))
+    mass = g.uniform(0.5, 1.5, na + 30)
+    G, h = 1.3, 0.02
+    t = O.tree_eval(pos, vel, mass, G=G, h=h, theta=0.5, leaf_size=8, lib=lib)
+    MB = mass[na:].sum()
+    cB = (mass[na:, None] * pos[na:]).sum(0) / MB
+    vB = (mass[na:, None] * vel[na:]).sum(0) / MB
+    inner = O.eval_active(pos[:na], vel[:na], mass[:na], G=G, h=h, lib=lib)
+    assert t["interactions"] < (na + 30) * (na + 29)
+    for i in range(na):
+        dd = cB - pos[i]
+        vv = vB - vel[i]
+        r = np.linalg.norm(dd)
+        acc = inner["acc"][i] + G * MB * dd / r**3
+        jk = inner["jerk"][i] + G * MB * (vv / r**3 - 3 * np.dot(dd, vv) * dd / r**5)
+        assert np.allclose(t["acc"][i], acc, rtol=1e-12, atol=0), i
+        assert np.allclose(t["jerk"][i], jk, rtol=1e-11, atol=1e-11 * np.abs(jk).max()), i
+    # relative criterion: B's top node (side ext/2) is accepted iff
+    # G M_B L^2 <= alpha |a_old| r^4; put |a_old| just above / below that
+    # (below, B is resolved into its children and the single monopole no
+    # longer holds)
+    ext = float((pos.max(axis=0) - pos.min(axis=0)).max())
+    L = ext / 2
+    alpha = 0.01
+    r = np.linalg.norm(cB - pos[:na], axis=1)
+    thr = G * MB * L**2 / r**4 / alpha
+    for scale, monopole in ((1.5, True), (0.5, False)):
+        a_old = np.zeros((na + 30, 3))
+        a_old[:na, 0] = scale * thr
+        tr = O.tree_eval(pos, vel, mass, G=G, h=h, theta=0.5, leaf_size=8, alpha=alpha,
+                         a_old=a_old, lib=lib)
+        for i in range(na):
+            dd = cB - pos[i]
+            acc = inner["acc"][i] + G * MB * dd / np.linalg.norm(dd) ** 3
+            same = np.allclose(tr["acc"][i], acc, rtol=1e-12, atol=0)
+            assert same == monopole, (scale, i)
+
+
+def pin_tree_derivatives(lib):
+    """Jerk = d a/dt along the drift and T = d a_i/d x_i of the tree field
+    (central differences; the tree's shape does not change at this scale)."""
+    pos, vel, mass = ics.plummer(300, seed=65)
+    h, tau = 0.01, 1e-7
+    o = O.tree_eval(pos, vel, mass, h=h, theta=0.5, lib=lib)
+    p = O.tree_eval(pos + tau * vel, vel, mass, h=h, theta=0.5, lib=lib)
+    m = O.tree_eval(pos - tau * vel, vel, mass, h=h, theta=0.5, lib=lib)
+    _close(o["jerk"], (p["acc"] - m["acc"]) / (2 * tau), 1e-5, "tree jerk vs FD")
+    i = 40
+    one = np.array([i], np.int32)
+    full = np.zeros((3, 3))
+    for c in range(3):
+        pp = pos.copy()
+        pm = pos.copy()
+        pp[i, c] += tau
+        pm[i, c] -= tau
+        full[:, c] = (O.tree_eval(pp, vel, mass, one, h=h, theta=0.5, lib=lib)["acc"][0]
+                      - O.tree_eval(pm, vel, mass, one, h=h, theta=0.5, lib=lib)["acc"][0]) / (2 * tau)
+    t6 = np.array([full[0, 0], full[1, 1], full[2, 2], full[0, 1], full[0, 2], full[1, 2]])
+    assert np.allclose(o["tidal"][i], t6, rtol=0, atol=1e-5 * np.abs(t6).max())
+
+
+def pin_tree_relative_criterion(lib):
+    """The relative criterion only ever opens more nodes: a vanishing alpha
+    gives the direct sum, a finite one at least the geometric-only work."""
+    pos, vel, mass = ics.plummer(600, seed=66)
+    d = O.eval_active(pos, vel, mass, h=0.01, lib=lib)
+    geo = O.tree_eval(pos, vel, mass, h=0.01, theta=0.5, lib=lib)
+    rel = O.tree_eval(pos, vel, mass, h=0.01, theta=0.5, alpha=0.0025, a_old=d["acc"], lib=lib)
+    tiny = O.tree_eval(pos, vel, mass, h=0.01, theta=0.5, alpha=1e-300, a_old=d["acc"], lib=lib)
+    assert rel["interactions"] >= geo["interactions"]
+    assert np.median(_rel(rel["acc"], d["acc"])) <= np.median(_rel(geo["acc"], d["acc"]))
+    assert tiny["interactions"] == 600 * 599
+    assert np.all(_rel(tiny["acc"], d["acc"]) <= 1e-13)
+
+
 def pin_update_counts(lib):
     """With fixed bins and dt_grav, an element of step s ticks is updated every
     ceil(q_f dt_grav / (s dt_min)) of its active steps (Eq. updatecondition),
@@ -914,6 +1056,8 @@ ALL_PINS = [
     pin_periodic_half_box_tie, pin_periodic_open_limit, pin_periodic_derivatives,
     pin_soft_kernel_vs_cas, pin_soft_constant_h, pin_soft_two_body, pin_soft_solve,
     pin_soft_energy_gradient, pin_soft_momentum, pin_soft_derivatives,
+    pin_tree_theta_zero, pin_tree_order, pin_tree_error_bounds, pin_tree_far_cluster,
+    pin_tree_derivatives, pin_tree_relative_criterion,
     pin_update_counts, pin_reverts_exactly, pin_bins, pin_compact,
     pin_predictor, pin_poly_history, pin_poly_predictor, pin_adjoint_fd,
 ]

@@ -20,7 +20,8 @@ MUTANTS = {
                      "*g = (-48.0 / u + 384.0 / 5.0 - 32.0 * u) / h5;"),
     "outer_phi_coeff": ("*phi = (16.0 / 5.0 - 1.0 / (15.0 * u)",
                         "*phi = (16.0 / 5.0 - 1.0 / (5.0 * u)"),
-    "self_term_kept": ("if (j == i) continue;", ";"),
+    "self_term_kept": ("if (j == i) continue;\n            double d[3] = {pos[3 * j] - xi,",
+                       ";\n            double d[3] = {pos[3 * j] - xi,"),
     "jerk_sign": ("nadd(&jk[c], m * (f * v[c] + g * dv * d[c]));",
                   "nadd(&jk[c], m * (f * v[c] - g * dv * d[c]));"),
     "jerk_dropped_term": ("nadd(&jk[c], m * (f * v[c] + g * dv * d[c]));",
@@ -73,6 +74,17 @@ MUTANTS = {
     "soft_pot_own_h": ("phi = 0.5 * (pi_ + pj);", "phi = pi_;"),
     "soft_w_h_term": ("*w_h = -c * (3.0 * wu + u * dwu) / h;", "*w_h = -c * (3.0 * wu - u * dwu) / h;"),
     "soft_psi_h_power": ("*psi_h = -dup / (h * h);", "*psi_h = -dup / h;"),
+    "tree_com_unweighted": ("                mx[c] = mx[c] + mj * t->pos[3 * j + c];",
+                            "                mx[c] = mx[c] + t->pos[3 * j + c];"),
+    "tree_vcom_dropped": ("double v[3] = {nd->vcom[0] - vi[0], nd->vcom[1] - vi[1], nd->vcom[2] - vi[2]};",
+                          "double v[3] = {-vi[0], -vi[1], -vi[2]};"),
+    "tree_half_side": ("double L = ldexp(t->ext, -nd->level);", "double L = ldexp(t->ext, -nd->level - 1);"),
+    "tree_self_in_leaf": ("            if (j == i) continue;\n            double dj[3]", "            double dj[3]"),
+    "tree_wrong_digit": ("int shift = 3 * (20 - nd->level);", "int shift = 3 * (21 - nd->level) % 63;"),
+    "tree_key_axes": ("kv[i].key = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);",
+                      "kv[i].key = (spread21(q[2]) << 2) | (spread21(q[1]) << 1) | spread21(q[0]);"),
+    "tree_rel_power": ("if (accept && rel > 0.0) accept = (G * nd->m) * L2 <= (rel * r2) * r2;",
+                       "if (accept && rel > 0.0) accept = (G * nd->m) * L2 <= rel * r2;"),
     "adj_mass_sign": ("nadd(&mb, -f * da);", "nadd(&mb, f * da);"),
     "adj_g_term": ("nadd(&xb[c], f * ab[c] + g * d[c] * da);", "nadd(&xb[c], f * ab[c]);"),
     "adj_tidal_transposed": ("ta[0] = t6[0] * ak[0] + t6[3] * ak[1] + t6[4] * ak[2];",
