@@ -60,6 +60,7 @@ extern "C" {
 #define GRAV_FLAG_TIMEOUT   2  /* a bounded wait on a shared-memory copy gave up */
 #define GRAV_FLAG_BADINDEX  4  /* a target index outside [0, n_src), or a bin outside [0, k_max] */
 #define GRAV_FLAG_NOCONVERGE 8 /* a support iteration of grav_soft_solve ran out of iterations */
+#define GRAV_FLAG_OVERFLOW  16 /* a tree build or walk exceeded its node bound (not expected) */
 
 /* Arithmetic of the force sums. */
 #define GRAV_F64   0  /* all pair arithmetic and sums in FP64 */
@@ -369,6 +370,49 @@ GRAV_API int grav_eval_soft(const grav_params *p, int64_t n_src, const double *p
                             const double *zeta, const int32_t *idx, const int32_t *n_idx_dev,
                             int64_t n_idx_max, double *acc, double *jerk, double *tidal,
                             double *pot, double *dt_grav, int32_t *flags_dev, void *workspace,
+                            int64_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Approximate solver: Section 3's oct-tree code.  A node of side L is always */
+/* split when it subtends L/r > Theta (Theta = 0.5 in the paper), r the       */
+/* distance from the target to the node's centre of mass; optionally also the */
+/* relative criterion the paper supplements (a node is opened unless          */
+/* G M L^2 <= alpha |a_old| r^4).  Nodes are monopoles: mass, centre of mass  */
+/* and mean velocity, so accepted nodes contribute to a, j, T and Phi as one  */
+/* moving point mass with the same softened pair terms as the direct sum.     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct grav_tree_params {
+    double theta;        /* opening angle (>= 0; 0 opens every node: the direct sum) */
+    double alpha;        /* relative criterion (0 = off; needs a_old) */
+    int32_t leaf_size;   /* a node of at most this many elements is a leaf (1..64) */
+    int32_t pad;
+} grav_tree_params;
+
+/*
+ * grav_eval_tree -- builds the oct-tree of all n elements and evaluates a, j,
+ * T, Phi (if p->want_pot) and dt_grav at the targets (idx / n_idx_dev /
+ * n_idx_max as in grav_eval_active; with idx NULL every element, walked in
+ * tree order), FP64 throughout (p->precision is not used; p->box must be 0).
+ * The tree (root cube, 63-bit Morton keys of 2^21 cells per axis, elements
+ * ordered by (key, index), leaves of at most leaf_size elements or 21 levels
+ * deep, monopole moments summed in order) and every opening decision are
+ * defined so that an FP64 evaluation on any machine builds the same tree and
+ * takes the same branches.
+ *   a_old [n][3]: device, nullable; the previous accelerations for alpha > 0
+ *   order_out [n]: device int32, nullable; the elements in tree order
+ *   stats_dev [2]: device int64, nullable; [0] nodes built, [1] interactions
+ *                  (accepted nodes plus leaf pairs) summed over the targets
+ * Requires n < 2^29 and a node bound below 2^31 (about 13 n / leaf_size).
+ * workspace: >= grav_tree_workspace_bytes(n, leaf_size) bytes, 256-aligned.
+ */
+GRAV_API int64_t grav_tree_workspace_bytes(int64_t n, int32_t leaf_size);
+GRAV_API int grav_eval_tree(const grav_params *p, const grav_tree_params *tp, int64_t n,
+                            const double *pos, const double *vel, const double *mass,
+                            const double *a_old, const int32_t *idx, const int32_t *n_idx_dev,
+                            int64_t n_idx_max, double *acc, double *jerk, double *tidal,
+                            double *pot, double *dt_grav, int32_t *order_out,
+                            long long *stats_dev, int32_t *flags_dev, void *workspace,
                             int64_t workspace_bytes, void *stream);
 
 /*

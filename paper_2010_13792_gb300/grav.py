@@ -31,6 +31,7 @@ FLAG_NONFINITE = 1
 FLAG_TIMEOUT = 2
 FLAG_BADINDEX = 4
 FLAG_NOCONVERGE = 8
+FLAG_OVERFLOW = 16
 
 F64 = 0
 MIXED = 1
@@ -78,6 +79,15 @@ def soft_params(*, n_ngb: float = 32.0, tol: float = 1e-12, max_iter: int = 100)
     return SoftParams(float(n_ngb), float(tol), int(max_iter), 0)
 
 
+class TreeParams(ctypes.Structure):
+    _fields_ = [("theta", _c_dbl), ("alpha", _c_dbl), ("leaf_size", _c_i32), ("pad", _c_i32)]
+
+
+def tree_params(*, theta: float = 0.5, alpha: float = 0.0, leaf_size: int = 8) -> TreeParams:
+    """Opening angle, optional relative criterion and leaf size of the oct-tree."""
+    return TreeParams(float(theta), float(alpha), int(leaf_size), 0)
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -118,6 +128,11 @@ _SIGS = {
     "grav_eval_soft": (ctypes.c_int, [ctypes.POINTER(Params), _c_i64, _c_ptr, _c_ptr, _c_ptr,
                                       _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr, _c_ptr,
                                       _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr]),
+    "grav_tree_workspace_bytes": (_c_i64, [_c_i64, _c_i32]),
+    "grav_eval_tree": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(TreeParams), _c_i64,
+                                      _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr,
+                                      _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+                                      _c_i64, _c_ptr]),
     "grav_measure_fma_peak": (ctypes.c_int, [_c_i32, _c_dbl, ctypes.POINTER(_c_dbl), _c_ptr]),
     "grav_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_uint32, _c_ptr, _c_ptr]),
 }
@@ -412,6 +427,38 @@ def eval_soft(p: Params, pos, vel, mass, h, zeta, idx, n_idx_dev, n_idx_max: int
         _ptr(flags, torch.int32, "flags", (1,), allow_none=True),
         ctypes.c_void_p(buf.data_ptr()), nb, _stream(stream))
     _err("grav_eval_soft", rc)
+
+
+def tree_workspace_bytes(n: int, leaf_size: int) -> int:
+    nb = int(lib().grav_tree_workspace_bytes(int(n), int(leaf_size)))
+    if nb < 0:
+        _err("grav_tree_workspace_bytes", nb)
+    return nb
+
+
+def eval_tree(p: Params, tp: TreeParams, pos, vel, mass, idx, n_idx_dev, n_idx_max: int, acc, jerk,
+              tidal, pot=None, dt_grav=None, a_old=None, order=None, stats=None, flags=None,
+              workspace: Workspace | None = None, stream=None):
+    """Oct-tree a, jerk, tidal tensor (and pot, dt_grav) scattered to rows idx."""
+    n = mass.numel()
+    dev = mass.device
+    nb = tree_workspace_bytes(n, tp.leaf_size)
+    buf = _ws(workspace, "tree", dev).get(nb, dev)
+    rc = lib().grav_eval_tree(
+        ctypes.byref(p), ctypes.byref(tp), n, _ptr(pos, torch.float64, "pos", (n, 3)),
+        _ptr(vel, torch.float64, "vel", (n, 3)), _ptr(mass, torch.float64, "mass", (n,)),
+        _ptr(a_old, torch.float64, "a_old", (n, 3), allow_none=True),
+        _ptr(idx, torch.int32, "idx", allow_none=True),
+        _ptr(n_idx_dev, torch.int32, "n_idx_dev", (1,), allow_none=True), int(n_idx_max),
+        _ptr(acc, torch.float64, "acc", (n, 3)), _ptr(jerk, torch.float64, "jerk", (n, 3)),
+        _ptr(tidal, torch.float64, "tidal", (n, 6)),
+        _ptr(pot, torch.float64, "pot", (n,), allow_none=True),
+        _ptr(dt_grav, torch.float64, "dt_grav", (n,), allow_none=True),
+        _ptr(order, torch.int32, "order", (n,), allow_none=True),
+        _ptr(stats, torch.int64, "stats", (2,), allow_none=True),
+        _ptr(flags, torch.int32, "flags", (1,), allow_none=True),
+        ctypes.c_void_p(buf.data_ptr()), nb, _stream(stream))
+    _err("grav_eval_tree", rc)
 
 
 BATCH_MAX_SYSTEMS = 16384

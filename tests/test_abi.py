@@ -85,6 +85,28 @@ def test_host_side_argument_checks(libgrav):
     assert L.grav_measure_fma_peak(5, 1.0, None, None) == grav.GRAV_EINVAL
 
 
+def test_tree_argument_checks(libgrav):
+    from paper_2010_13792_gb300 import grav
+    L = grav.lib()
+    p = grav.params(h=0.01)
+    args = lambda n, nmax: (n, None, None, None, None, None, None, nmax, None, None, None, None,
+                            None, None, None, None, None, 0, None)
+    for tp in (grav.tree_params(theta=-0.1), grav.tree_params(theta=float("nan")),
+               grav.tree_params(alpha=-1.0), grav.tree_params(leaf_size=0),
+               grav.tree_params(leaf_size=65)):
+        assert L.grav_eval_tree(ctypes.byref(p), ctypes.byref(tp), *args(10, 10)) == grav.GRAV_EINVAL
+    tp = grav.tree_params()
+    assert L.grav_eval_tree(ctypes.byref(p), ctypes.byref(tp), *args(0, 0)) == grav.GRAV_OK
+    assert L.grav_eval_tree(ctypes.byref(p), ctypes.byref(tp), *args(10, 11)) == grav.GRAV_EINVAL
+    assert L.grav_eval_tree(ctypes.byref(p), ctypes.byref(tp), *args(10, 10)) == grav.GRAV_EINVAL
+    pb = grav.params(h=0.01, box=1.0)
+    assert L.grav_eval_tree(ctypes.byref(pb), ctypes.byref(tp), *args(10, 10)) == grav.GRAV_EINVAL
+    assert L.grav_tree_workspace_bytes(-1, 8) == grav.GRAV_EINVAL
+    assert L.grav_tree_workspace_bytes(100, 0) == grav.GRAV_EINVAL
+    assert L.grav_tree_workspace_bytes(1 << 20, 8) > (1 << 20) * 24
+    assert L.grav_tree_workspace_bytes(1 << 28, 1) == grav.GRAV_EINVAL   # node bound >= 2^31
+
+
 def test_adaptive_softening_argument_checks(libgrav):
     from paper_2010_13792_gb300 import grav
     L = grav.lib()
