@@ -315,6 +315,9 @@ def run_ours(args, rank, local, ws):
         result["extras"] = extras(args, path, dev, sms, peak32, flush)
         result["extras"]["fp64_path"]["mixed_over_fp64"] = \
             value / result["extras"]["fp64_path"]["interactions_per_s"]
+        tree = result["extras"]["tree_N1048576"]
+        if args.n == tree["n"] and args.fraction == 1.0:
+            tree["speedup_over_mixed_direct"] = 1e3 * eval_s / tree["mixed"]["ms"]
         result["e2e"] = e2e(args, path, dev, flush)
         result["cpu_baseline"] = cpu_baseline(path, args.cpu_seconds)
     return result
@@ -383,6 +386,7 @@ def extras(args, path, dev, sms, peak32, flush):
     out["predict_N16777216"] = predict_bandwidth(dev, 1 << 24)
     out["periodic_zeldovich_64cubed"] = periodic_extra(dev, flush)
     out["adaptive_softening_N1048576"] = soft_extra(path, dev, flush)
+    out["tree_N1048576"] = tree_extra(path, dev, flush)
     out["batched_256_systems"] = batched_extra(dev, flush)
     out["adaptive_plummer_131072"] = adaptive_extra(dev)
     try:
@@ -507,6 +511,47 @@ def soft_extra(path, dev, flush):
         ts.append(a.elapsed_time(b) * 1e-3)
     t = statistics.median(ts)
     res["eval_mixed"] = {"interactions_per_s": n * n / t, "ms": 1e3 * t}
+    return res
+
+
+def tree_extra(path, dev, flush):
+    """The oct-tree solver (Theta = 0.5, leaves of 8) on the headline cloud
+    with every element a target, mixed walk and FP64 walk: build plus walk,
+    nodes and interactions, and the accuracy of a against the mixed direct
+    sum of the timed steps (the same positions)."""
+    import torch
+
+    from paper_2010_13792_gb300 import grav
+    n = path.n
+    acc = torch.empty(n, 3, dtype=torch.float64, device=dev)
+    jerk, tid = torch.empty_like(acc), torch.empty(n, 6, dtype=torch.float64, device=dev)
+    stats = torch.zeros(2, dtype=torch.int64, device=dev)
+    tp = grav.tree_params(theta=0.5, leaf_size=8)
+    ws = grav.Workspace()
+    res = {"n": n, "theta": 0.5, "leaf_size": 8, "speedup_over_mixed_direct": None}
+    for name, prec in (("mixed", grav.MIXED), ("f64", grav.F64)):
+        p = grav.params(h=H, precision=prec)
+        grav.eval_tree(p, tp, path.pos, path.vel, path.mass, None, None, n, acc, jerk, tid,
+                       stats=stats, workspace=ws)
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            grav.eval_tree(p, tp, path.pos, path.vel, path.mass, None, None, n, acc, jerk, tid,
+                           stats=stats, workspace=ws)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) * 1e-3)
+        t = statistics.median(ts)
+        e = ((acc - path.acc).norm(dim=1) / path.acc.norm(dim=1)).cpu()
+        q = torch.quantile(e[::16], torch.tensor([0.5, 0.99], dtype=e.dtype))
+        inter = int(stats[1].item())
+        res["nodes"] = int(stats[0].item())
+        res["interactions_per_target"] = inter / n
+        res[name] = {"ms": 1e3 * t, "interactions_per_s": inter / t,
+                     "acc_rel_error_vs_direct": {"median": float(q[0]), "p99": float(q[1]),
+                                                 "max": float(e.max())}}
     return res
 
 

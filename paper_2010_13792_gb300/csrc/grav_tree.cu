@@ -28,8 +28,9 @@
 // from run to run, the tree and the walk order do not); moments bottom-up and
 // the "next" links top-down, level by level.  The walk is stackless: after a
 // node is accepted or a leaf is summed the walk continues at the node's next
-// link (its next sibling, else its parent's next link).  Sums are FP64, pair
-// terms as in the FP64 direct kernel, compensated every 32 interactions.
+// link (its next sibling, else its parent's next link).  GRAV_F64: pair terms
+// as in the FP64 direct kernel, sums compensated every 32 interactions;
+// GRAV_MIXED: the same decisions (FP64), pair terms in FP32.
 #include <cmath>
 
 #include "grav_eval.cuh"
@@ -58,6 +59,9 @@ struct TreeView {
     int32_t *first, *count, *child_first, *next;
     int8_t *n_child, *level;
     double *m, *com, *vcom;
+    float4 *vcom32;       // mixed walk: node mean velocity in FP32
+    float4 *soff;         // mixed walk, per tree position: (x_j - com of its leaf, m_j) in FP32
+    float4 *svel;         // mixed walk, per tree position: v_j in FP32
     int32_t *flags;
 };
 
@@ -68,7 +72,7 @@ int64_t max_nodes_for(int64_t n, int32_t leaf)
 
 struct TreeLayout {
     int64_t key_a, key_b, val_a, val_b, hist, part, frame, counters;
-    int64_t first, count, child_first, next, n_child, level, m, com, vcom, total;
+    int64_t first, count, child_first, next, n_child, level, m, com, vcom, vcom32, soff, svel, total;
     int64_t n_sort_blocks, max_nodes;
 };
 
@@ -102,6 +106,9 @@ TreeLayout tree_layout(int64_t n, int32_t leaf)
     L.m = take(mn * 8);
     L.com = take(mn * 24);
     L.vcom = take(mn * 24);
+    L.vcom32 = take(mn * 16);
+    L.soff = take(n * 16);
+    L.svel = take(n * 16);
     L.total = o;
     return L;
 }
@@ -423,6 +430,33 @@ __global__ void __launch_bounds__(256) tree_next_kernel(TreeView t, int lvl)
     }
 }
 
+// FP32 data of the mixed walk: every node's mean velocity, and per tree
+// position the element's offset from its leaf's centre of mass (formed in
+// FP64, rounded once), mass and velocity.
+__global__ void __launch_bounds__(256) tree_mixed_data_kernel(TreeView t, const double *__restrict__ pos,
+                                                              const double *__restrict__ vel,
+                                                              const double *__restrict__ mass)
+{
+    int64_t nn = t.counters[0];
+    if (nn > t.max_nodes) nn = t.max_nodes;
+    for (int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x; k < nn; k += (int64_t)gridDim.x * 256) {
+        const double *vc = t.vcom + 3 * k;
+        t.vcom32[k] = make_float4(__double2float_rn(vc[0]), __double2float_rn(vc[1]),
+                                  __double2float_rn(vc[2]), 0.0f);
+        if (t.child_first[k] >= 0) continue;
+        const double *c = t.com + 3 * k;
+        const int32_t f = t.first[k], cnt = t.count[k];
+        for (int32_t q = f; q < f + cnt; ++q) {
+            const int32_t j = t.order[q];
+            t.soff[q] = make_float4(__double2float_rn(pos[3 * j] - c[0]),
+                                    __double2float_rn(pos[3 * j + 1] - c[1]),
+                                    __double2float_rn(pos[3 * j + 2] - c[2]), __double2float_rn(mass[j]));
+            t.svel[q] = make_float4(__double2float_rn(vel[3 * j]), __double2float_rn(vel[3 * j + 1]),
+                                    __double2float_rn(vel[3 * j + 2]), 0.0f);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Walk
 // ---------------------------------------------------------------------------
@@ -461,7 +495,55 @@ __device__ __forceinline__ void pair_d(double acc[kNCPot], double m, double dx, 
     accumulate_d<true>(acc, dx, dy, dz, ux, uy, uz, mf, mg, mp);
 }
 
-template <bool POT>
+// The same pair terms in FP32 (mixed walk): A, F, J1, J2, Tp, P.
+__device__ __forceinline__ void pair_f(float acc[kNCPot], float m, float dx, float dy, float dz,
+                                       float ux, float uy, float uz, float h2, float hinv, bool self)
+{
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ri = rsqrt_sfu(r2);
+    const float ri2 = ri * ri;
+    float mp = m * ri;
+    float mf = mp * ri2;
+    float mg = mf * ri2;
+    if (r2 < h2) {
+        float F, Gp, P;
+        spline_kernel<float>(sqrtf(r2) * hinv, F, Gp, P);
+        const float hinv3 = hinv * hinv * hinv;
+        mf = m * F * hinv3;
+        mg = m * Gp * hinv3 * hinv * hinv;
+        mp = m * P * hinv;
+    }
+    if (self) {
+        mf = 0.0f;
+        mg = 0.0f;
+        mp = 0.0f;
+    }
+    acc[A0 + 0] = fmaf(mf, dx, acc[A0 + 0]);
+    acc[A0 + 1] = fmaf(mf, dy, acc[A0 + 1]);
+    acc[A0 + 2] = fmaf(mf, dz, acc[A0 + 2]);
+    acc[FSUM] += mf;
+    acc[J10 + 0] = fmaf(mf, ux, acc[J10 + 0]);
+    acc[J10 + 1] = fmaf(mf, uy, acc[J10 + 1]);
+    acc[J10 + 2] = fmaf(mf, uz, acc[J10 + 2]);
+    const float dv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+    const float gx = mg * dx, gy = mg * dy, gz = mg * dz;
+    acc[TXX] = fmaf(gx, dx, acc[TXX]);
+    acc[TYY] = fmaf(gy, dy, acc[TYY]);
+    acc[TZZ] = fmaf(gz, dz, acc[TZZ]);
+    acc[TXY] = fmaf(gx, dy, acc[TXY]);
+    acc[TXZ] = fmaf(gx, dz, acc[TXZ]);
+    acc[TYZ] = fmaf(gy, dz, acc[TYZ]);
+    acc[J20 + 0] = fmaf(gx, dv, acc[J20 + 0]);
+    acc[J20 + 1] = fmaf(gy, dv, acc[J20 + 1]);
+    acc[J20 + 2] = fmaf(gz, dv, acc[J20 + 2]);
+    acc[PSUM] += mp;
+}
+
+// MIXED: decisions and the target-to-node offsets in FP64, every pair term
+// in FP32 (leaf elements from their FP32 offsets to the leaf's centre of mass
+// plus the target's offset to it), FP32 sums of up to 32 interactions added
+// into FP64.
+template <bool POT, bool MIXED>
 __global__ void __launch_bounds__(kWalkNT) tree_walk_kernel(TreeView t, EvalArgs a, WalkArgs w)
 {
     int64_t n_tgt = w.n_idx_max;
@@ -489,12 +571,16 @@ __global__ void __launch_bounds__(kWalkNT) tree_walk_kernel(TreeView t, EvalArgs
                                                       __dmul_rn(ao[2], ao[2]))));
     }
     double acc[kNCPot], shi[kNCPot], slo[kNCPot];
+    float accf[MIXED ? kNCPot : 1];
 #pragma unroll
     for (int c = 0; c < kNCPot; ++c) {
         acc[c] = 0.0;
         shi[c] = 0.0;
         slo[c] = 0.0;
+        if (MIXED) accf[MIXED ? c : 0] = 0.0f;
     }
+    const float h2f = (float)(w.h * w.h), hinvf = (float)(1.0 / w.h);
+    const float vi32[3] = {__double2float_rn(vi[0]), __double2float_rn(vi[1]), __double2float_rn(vi[2])};
     int pending = 0;
     long long inter = 0;
     int32_t node = 0;
@@ -515,7 +601,29 @@ __global__ void __launch_bounds__(kWalkNT) tree_walk_kernel(TreeView t, EvalArgs
         bool accept = L2 < __dmul_rn(w.theta2, r2);
         if (accept && rel > 0.0)
             accept = __dmul_rn(__dmul_rn(a.G, mn), L2) <= __dmul_rn(__dmul_rn(rel, r2), r2);
-        if (accept) {
+        if (MIXED && (accept || t.child_first[node] < 0)) {
+            const float dxf = __double2float_rn(dx), dyf = __double2float_rn(dy),
+                        dzf = __double2float_rn(dz);
+            if (accept) {
+                const float4 vc = t.vcom32[node];
+                pair_f(accf, __double2float_rn(mn), dxf, dyf, dzf, vc.x - vi32[0], vc.y - vi32[1],
+                       vc.z - vi32[2], h2f, hinvf, false);
+                ++inter;
+                ++pending;
+            } else {
+                const int32_t f = t.first[node], c = t.count[node];
+                for (int32_t q = f; q < f + c; ++q) {
+                    const float4 o = t.soff[q];
+                    const float4 v = t.svel[q];
+                    const bool self = t.order[q] == i;
+                    pair_f(accf, o.w, o.x + dxf, o.y + dyf, o.z + dzf, v.x - vi32[0], v.y - vi32[1],
+                           v.z - vi32[2], h2f, hinvf, self);
+                    inter += !self;
+                    ++pending;
+                }
+            }
+            node = t.next[node];
+        } else if (accept) {
             pair_d(acc, mn, dx, dy, dz, t.vcom[3 * (int64_t)node] - vi[0],
                    t.vcom[3 * (int64_t)node + 1] - vi[1], t.vcom[3 * (int64_t)node + 2] - vi[2], h2,
                    hinv, false);
@@ -539,8 +647,13 @@ __global__ void __launch_bounds__(kWalkNT) tree_walk_kernel(TreeView t, EvalArgs
         if (pending >= kFlushEvery) {
 #pragma unroll
             for (int c = 0; c < kNCPot; ++c) {
-                two_sum_acc(shi[c], slo[c], acc[c]);
-                acc[c] = 0.0;
+                if (MIXED) {
+                    shi[c] += (double)accf[MIXED ? c : 0];
+                    accf[MIXED ? c : 0] = 0.0f;
+                } else {
+                    two_sum_acc(shi[c], slo[c], acc[c]);
+                    acc[c] = 0.0;
+                }
             }
             pending = 0;
         }
@@ -548,8 +661,12 @@ __global__ void __launch_bounds__(kWalkNT) tree_walk_kernel(TreeView t, EvalArgs
     double sum[kNCPot];
 #pragma unroll
     for (int c = 0; c < kNCPot; ++c) {
-        two_sum_acc(shi[c], slo[c], acc[c]);
-        sum[c] = __dadd_rn(shi[c], slo[c]);
+        if (MIXED) {
+            sum[c] = shi[c] + (double)accf[MIXED ? c : 0];
+        } else {
+            two_sum_acc(shi[c], slo[c], acc[c]);
+            sum[c] = __dadd_rn(shi[c], slo[c]);
+        }
     }
     write_target<POT, false>(a, i, sum);
     if (w.stats)
@@ -590,6 +707,8 @@ extern "C" int grav_eval_tree(const grav_params *p, const grav_tree_params *tp, 
         !std::isfinite(p->h) || !std::isfinite(p->eta))
         return fail(GRAV_EINVAL, "%s: G, h and eta must be positive and finite", who);
     if (p->box != 0.0) return fail(GRAV_EINVAL, "%s: the tree supports open boundaries only", who);
+    if (p->precision != GRAV_F64 && p->precision != GRAV_MIXED)
+        return fail(GRAV_EINVAL, "%s: precision must be GRAV_F64 or GRAV_MIXED", who);
     if (!(tp->theta >= 0.0) || !std::isfinite(tp->theta) || !(tp->alpha >= 0.0) ||
         !std::isfinite(tp->alpha))
         return fail(GRAV_EINVAL, "%s: theta and alpha must be finite and >= 0", who);
@@ -626,6 +745,9 @@ extern "C" int grav_eval_tree(const grav_params *p, const grav_tree_params *tp, 
     t.m = reinterpret_cast<double *>(ws + L.m);
     t.com = reinterpret_cast<double *>(ws + L.com);
     t.vcom = reinterpret_cast<double *>(ws + L.vcom);
+    t.vcom32 = reinterpret_cast<float4 *>(ws + L.vcom32);
+    t.soff = reinterpret_cast<float4 *>(ws + L.soff);
+    t.svel = reinterpret_cast<float4 *>(ws + L.svel);
     t.flags = flags_dev;
 
     // bounding cube and keys
@@ -665,6 +787,8 @@ extern "C" int grav_eval_tree(const grav_params *p, const grav_tree_params *tp, 
     for (int lvl = kMaxLevel; lvl >= 0; --lvl)
         tree_moment_kernel<<<g, 256, 0, st>>>(t, pos, vel, mass, lvl);
     for (int lvl = 0; lvl < kMaxLevel; ++lvl) tree_next_kernel<<<g, 256, 0, st>>>(t, lvl);
+    const bool mixed = p->precision == GRAV_MIXED;
+    if (mixed) tree_mixed_data_kernel<<<g, 256, 0, st>>>(t, pos, vel, mass);
     rc = check_launch("grav_eval_tree/build");
     if (rc) return rc;
     if (order_out) {
@@ -705,9 +829,13 @@ extern "C" int grav_eval_tree(const grav_params *p, const grav_tree_params *tp, 
     w.alpha = tp->alpha;
     w.stats = stats_dev;
     const unsigned gw = (unsigned)((n_idx_max + kWalkNT - 1) / kWalkNT);
-    if (p->want_pot)
-        tree_walk_kernel<true><<<gw, kWalkNT, 0, st>>>(t, a, w);
+    if (p->want_pot && mixed)
+        tree_walk_kernel<true, true><<<gw, kWalkNT, 0, st>>>(t, a, w);
+    else if (mixed)
+        tree_walk_kernel<false, true><<<gw, kWalkNT, 0, st>>>(t, a, w);
+    else if (p->want_pot)
+        tree_walk_kernel<true, false><<<gw, kWalkNT, 0, st>>>(t, a, w);
     else
-        tree_walk_kernel<false><<<gw, kWalkNT, 0, st>>>(t, a, w);
+        tree_walk_kernel<false, false><<<gw, kWalkNT, 0, st>>>(t, a, w);
     return check_launch("grav_eval_tree/walk");
 }

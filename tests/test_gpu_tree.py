@@ -1,9 +1,10 @@
 """Oct-tree solver on the GPU against the oracle's tree: the same tree order
 (bit for bit), the same number of nodes and interactions (every opening
 decision taken the same way), a, j, T, Phi and dt_grav element by element
-to the FP64 tolerance; Theta = 0 against the direct sum; the relative
-criterion; degenerate inputs; at 2^20 elements sampled rows and the
-accuracy against the direct sum."""
+to the FP64 tolerance (and, for the mixed walk, to the mixed tolerances);
+Theta = 0 against the direct sum; the relative criterion; degenerate
+inputs; at 2^20 elements sampled rows and the accuracy against the direct
+sum."""
 import numpy as np
 import pytest
 import torch
@@ -11,12 +12,13 @@ import torch
 from oracle import oracle as O
 from paper_2010_13792_gb300 import grav, ics
 
-from gpu_util import DEV, T, assert_f64, errors  # noqa: E402
+from gpu_util import DEV, T, assert_f64, assert_mixed, errors  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
 
-def gpu_tree(pos, vel, mass, idx=None, *, h, theta=0.5, leaf=8, alpha=0.0, a_old=None, G=1.0):
+def gpu_tree(pos, vel, mass, idx=None, *, h, theta=0.5, leaf=8, alpha=0.0, a_old=None, G=1.0,
+             precision=grav.F64):
     n = mass.size
     acc = torch.full((n, 3), np.nan, dtype=torch.float64, device=DEV)
     jerk, tid = acc.clone(), torch.full((n, 6), np.nan, dtype=torch.float64, device=DEV)
@@ -25,7 +27,7 @@ def gpu_tree(pos, vel, mass, idx=None, *, h, theta=0.5, leaf=8, alpha=0.0, a_old
     order = torch.full((n,), -1, dtype=torch.int32, device=DEV)
     stats = torch.full((2,), -1, dtype=torch.int64, device=DEV)
     flags = torch.zeros(1, dtype=torch.int32, device=DEV)
-    p = grav.params(G=G, h=h, precision=grav.F64, want_pot=True)
+    p = grav.params(G=G, h=h, precision=precision, want_pot=True)
     tp = grav.tree_params(theta=theta, alpha=alpha, leaf_size=leaf)
     it = None if idx is None else T(idx, torch.int32)
     cnt = None if idx is None else T(np.array([idx.size]), torch.int32)
@@ -110,3 +112,21 @@ def test_tree_2e20_sampled_and_accuracy():
     e = np.linalg.norm(out["acc"][rows] - direct["acc"], axis=1) / np.linalg.norm(direct["acc"], axis=1)
     assert np.median(e) < 5e-3 and e.max() < 5e-2, (np.median(e), e.max())
     assert out["interactions"] < 0.01 * (1 << 20) * (1 << 20)
+
+
+@pytest.mark.parametrize("leaf", [8, 32])
+def test_mixed_walk_matches_oracle_tree(leaf):
+    pos, vel, mass = ics.plummer(5000, seed=117, sort=False)
+    ref = O.tree_eval(pos, vel, mass, h=0.01, theta=0.5, leaf_size=leaf)
+    out = gpu_tree(pos, vel, mass, h=0.01, theta=0.5, leaf=leaf, precision=grav.MIXED)
+    assert out["interactions"] == ref["interactions"]
+    assert_mixed(errors(out, ref, np.arange(5000)))
+
+
+def test_mixed_walk_2e20_sampled():
+    pos, vel, mass = ics.turbulent_cloud(1 << 20)
+    idx = ics.active_subset(1 << 20, 0.5, 118)
+    out = gpu_tree(pos, vel, mass, idx, h=2e-3, theta=0.5, leaf=8, precision=grav.MIXED)
+    rows = np.sort(ics.rng(119).choice(idx, 64, replace=False)).astype(np.int32)
+    ref = O.tree_eval(pos, vel, mass, rows, h=2e-3, theta=0.5, leaf_size=8)
+    assert_mixed(errors(out, ref, rows))
