@@ -507,59 +507,69 @@ __device__ __forceinline__ void near_loop_f(const float4 *__restrict__ sp,
 // Paired layout, Newtonian loop: two sources per packed FP32x2 instruction
 // (fma/add/mul .f32x2), so one issue slot does the work of two pairs; the
 // SFU rsqrt runs per source.  Lane 0 sums the even sources, lane 1 the odd.
-template <int S, int U, bool POT>
-__device__ __forceinline__ void far_loop_pair(const float *__restrict__ tile, float tx, float ty,
-                                              float tz, float2 acc[kNCPot])
+template <int KT, int S, int U, bool POT>
+__device__ __forceinline__ void far_loop_pair(const float *__restrict__ tile, const float tx[KT][3],
+                                              float2 acc[KT][kNCPot])
 {
     const float4 *P0 = reinterpret_cast<const float4 *>(tile);
     const float4 *P1 = P0 + S / 2;
     const float4 *V0 = P1 + S / 2;
     const float2 *V1 = reinterpret_cast<const float2 *>(V0 + S / 2);
-    const float2 ntx = make_float2(-tx, -tx), nty = make_float2(-ty, -ty), ntz = make_float2(-tz, -tz);
+    float2 ntx[KT], nty[KT], ntz[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        ntx[q] = make_float2(-tx[q][0], -tx[q][0]);
+        nty[q] = make_float2(-tx[q][1], -tx[q][1]);
+        ntz[q] = make_float2(-tx[q][2], -tx[q][2]);
+    }
 #pragma unroll U
     for (int k = 0; k < S / 2; ++k) {
         const float4 p0 = P0[k], p1 = P1[k], v0 = V0[k];
         const float2 vz = V1[k];
-        const float2 dx = __fadd2_rn(make_float2(p0.x, p0.y), ntx);
-        const float2 dy = __fadd2_rn(make_float2(p0.z, p0.w), nty);
-        const float2 dz = __fadd2_rn(make_float2(p1.x, p1.y), ntz);
-        float2 r2 = __fmul2_rn(dz, dz);
-        r2 = __ffma2_rn(dy, dy, r2);
-        r2 = __ffma2_rn(dx, dx, r2);
-        const float2 ri = make_float2(rsqrt_sfu(r2.x), rsqrt_sfu(r2.y));
-        const float2 ri2 = __fmul2_rn(ri, ri);
-        const float2 mp = __fmul2_rn(make_float2(p1.z, p1.w), ri);
-        const float2 mf = __fmul2_rn(mp, ri2);
-        const float2 mg = __fmul2_rn(mf, ri2);
         const float2 vx = make_float2(v0.x, v0.y), vy = make_float2(v0.z, v0.w);
-        acc[A0 + 0] = __ffma2_rn(mf, dx, acc[A0 + 0]);
-        acc[A0 + 1] = __ffma2_rn(mf, dy, acc[A0 + 1]);
-        acc[A0 + 2] = __ffma2_rn(mf, dz, acc[A0 + 2]);
-        acc[J10 + 0] = __ffma2_rn(mf, vx, acc[J10 + 0]);
-        acc[J10 + 1] = __ffma2_rn(mf, vy, acc[J10 + 1]);
-        acc[J10 + 2] = __ffma2_rn(mf, vz, acc[J10 + 2]);
-        float2 dv = __fmul2_rn(dz, vz);
-        dv = __ffma2_rn(dy, vy, dv);
-        dv = __ffma2_rn(dx, vx, dv);
-        const float2 gx = __fmul2_rn(mg, dx), gy = __fmul2_rn(mg, dy), gz = __fmul2_rn(mg, dz);
-        acc[TXX] = __ffma2_rn(gx, dx, acc[TXX]);
-        acc[TYY] = __ffma2_rn(gy, dy, acc[TYY]);
-        acc[TZZ] = __ffma2_rn(gz, dz, acc[TZZ]);
-        acc[TXY] = __ffma2_rn(gx, dy, acc[TXY]);
-        acc[TXZ] = __ffma2_rn(gx, dz, acc[TXZ]);
-        acc[TYZ] = __ffma2_rn(gy, dz, acc[TYZ]);
-        acc[J20 + 0] = __ffma2_rn(gx, dv, acc[J20 + 0]);
-        acc[J20 + 1] = __ffma2_rn(gy, dv, acc[J20 + 1]);
-        acc[J20 + 2] = __ffma2_rn(gz, dv, acc[J20 + 2]);
-        if (POT) acc[PSUM] = __fadd2_rn(acc[PSUM], mp);
+        const float2 m = make_float2(p1.z, p1.w);
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const float2 dx = __fadd2_rn(make_float2(p0.x, p0.y), ntx[q]);
+            const float2 dy = __fadd2_rn(make_float2(p0.z, p0.w), nty[q]);
+            const float2 dz = __fadd2_rn(make_float2(p1.x, p1.y), ntz[q]);
+            float2 r2 = __fmul2_rn(dz, dz);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dx, dx, r2);
+            const float2 ri = make_float2(rsqrt_sfu(r2.x), rsqrt_sfu(r2.y));
+            const float2 ri2 = __fmul2_rn(ri, ri);
+            const float2 mp = __fmul2_rn(m, ri);
+            const float2 mf = __fmul2_rn(mp, ri2);
+            const float2 mg = __fmul2_rn(mf, ri2);
+            acc[q][A0 + 0] = __ffma2_rn(mf, dx, acc[q][A0 + 0]);
+            acc[q][A0 + 1] = __ffma2_rn(mf, dy, acc[q][A0 + 1]);
+            acc[q][A0 + 2] = __ffma2_rn(mf, dz, acc[q][A0 + 2]);
+            acc[q][J10 + 0] = __ffma2_rn(mf, vx, acc[q][J10 + 0]);
+            acc[q][J10 + 1] = __ffma2_rn(mf, vy, acc[q][J10 + 1]);
+            acc[q][J10 + 2] = __ffma2_rn(mf, vz, acc[q][J10 + 2]);
+            float2 dv = __fmul2_rn(dz, vz);
+            dv = __ffma2_rn(dy, vy, dv);
+            dv = __ffma2_rn(dx, vx, dv);
+            const float2 gx = __fmul2_rn(mg, dx), gy = __fmul2_rn(mg, dy), gz = __fmul2_rn(mg, dz);
+            acc[q][TXX] = __ffma2_rn(gx, dx, acc[q][TXX]);
+            acc[q][TYY] = __ffma2_rn(gy, dy, acc[q][TYY]);
+            acc[q][TZZ] = __ffma2_rn(gz, dz, acc[q][TZZ]);
+            acc[q][TXY] = __ffma2_rn(gx, dy, acc[q][TXY]);
+            acc[q][TXZ] = __ffma2_rn(gx, dz, acc[q][TXZ]);
+            acc[q][TYZ] = __ffma2_rn(gy, dz, acc[q][TYZ]);
+            acc[q][J20 + 0] = __ffma2_rn(gx, dv, acc[q][J20 + 0]);
+            acc[q][J20 + 1] = __ffma2_rn(gy, dv, acc[q][J20 + 1]);
+            acc[q][J20 + 2] = __ffma2_rn(gz, dv, acc[q][J20 + 2]);
+            if (POT) acc[q][PSUM] = __fadd2_rn(acc[q][PSUM], mp);
+        }
     }
 }
 
 // Paired layout, softened loop: one source at a time (scalar).
-template <int S, bool POT>
-__device__ __forceinline__ void near_loop_pair(const float *__restrict__ tile, const float tx[1][3],
-                                               const int64_t ti[1], int64_t jbase, float h2,
-                                               float hinv, float acc[1][kNCPot])
+template <int KT, int S, bool POT>
+__device__ __forceinline__ void near_loop_pair(const float *__restrict__ tile, const float tx[KT][3],
+                                               const int64_t ti[KT], int64_t jbase, float h2,
+                                               float hinv, float acc[KT][kNCPot])
 {
     const float hinv3 = hinv * hinv * hinv;
     const float hinv5 = hinv3 * hinv * hinv;
@@ -570,27 +580,30 @@ __device__ __forceinline__ void near_loop_pair(const float *__restrict__ tile, c
         const float z = tile[2 * S + 4 * k + h], m = tile[2 * S + 4 * k + 2 + h];
         const float vx = tile[4 * S + 4 * k + h], vy = tile[4 * S + 4 * k + 2 + h];
         const float vz = tile[6 * S + 2 * k + h];
-        float dx = x - tx[0][0], dy = y - tx[0][1], dz = z - tx[0][2];
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float ri = rsqrt_sfu(r2);
-        float ri2 = ri * ri;
-        float mp = m * ri;
-        float mf = mp * ri2;
-        float mg = mf * ri2;
-        if (r2 < h2) {
-            float F, Gp, P;
-            spline_kernel<float>(sqrtf(r2) * hinv, F, Gp, P);
-            mf = m * F * hinv3;
-            mg = m * Gp * hinv5;
-            mp = m * P * hinv;
-            if (jbase + j == ti[0]) {
-                mf = 0.0f;
-                mg = 0.0f;
-                mp = 0.0f;
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            float dx = x - tx[q][0], dy = y - tx[q][1], dz = z - tx[q][2];
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float ri = rsqrt_sfu(r2);
+            float ri2 = ri * ri;
+            float mp = m * ri;
+            float mf = mp * ri2;
+            float mg = mf * ri2;
+            if (r2 < h2) {
+                float F, Gp, P;
+                spline_kernel<float>(sqrtf(r2) * hinv, F, Gp, P);
+                mf = m * F * hinv3;
+                mg = m * Gp * hinv5;
+                mp = m * P * hinv;
+                if (jbase + j == ti[q]) {
+                    mf = 0.0f;
+                    mg = 0.0f;
+                    mp = 0.0f;
+                }
+                acc[q][ESUM] += fmaf(-mg, r2, mf);
             }
-            acc[0][ESUM] += fmaf(-mg, r2, mf);
+            accumulate_f<KT, POT>(acc, q, dx, dy, dz, vx, vy, vz, mf, mg, mp);
         }
-        accumulate_f<1, POT>(acc, 0, dx, dy, dz, vx, vy, vz, mf, mg, mp);
     }
 }
 
@@ -1142,7 +1155,6 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
     constexpr int BT = Sm::BT;
     constexpr int NSTAGE = 2;
     constexpr int NC = Sm::NC;
-    static_assert(!PAIR || KT == 1, "the paired layout serves one target per thread");
     constexpr bool soft = MODE == kModeSoft;
     constexpr uint32_t kTileBytes = PAIR ? S * 28 : S * 2 * sizeof(float4);
     const float4 *src = static_cast<const float4 *>(a.src);
@@ -1287,16 +1299,18 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
         } else if (PAIR) {
             const float *tf = reinterpret_cast<const float *>(sm.stage[s]);
             if (!near) {
-                float2 acc2[kNCPot];
+                float2 acc2[KT][kNCPot];
 #pragma unroll
-                for (int c = 0; c < kNCPot; ++c) acc2[c] = make_float2(0.0f, 0.0f);
-                far_loop_pair<S, U, POT>(tf, tx[0][0], tx[0][1], tx[0][2], acc2);
+                for (int q = 0; q < KT; ++q)
 #pragma unroll
-                for (int c = 0; c < kNCPot; ++c) acc[0][c] = acc2[c].x + acc2[c].y;
+                    for (int c = 0; c < kNCPot; ++c) acc2[q][c] = make_float2(0.0f, 0.0f);
+                far_loop_pair<KT, S, U, POT>(tf, tx, acc2);
+#pragma unroll
+                for (int q = 0; q < KT; ++q)
+#pragma unroll
+                    for (int c = 0; c < kNCPot; ++c) acc[q][c] = acc2[q][c].x + acc2[q][c].y;
             } else {
-                near_loop_pair<S, POT>(tf, reinterpret_cast<const float(*)[3]>(tx),
-                                       ti, g.first, a.h2f_up, a.hinvf,
-                                       reinterpret_cast<float(*)[kNCPot]>(acc));
+                near_loop_pair<KT, S, POT>(tf, tx, ti, g.first, a.h2f_up, a.hinvf, acc);
             }
         } else {
             const float4 *sp_ = sm.stage[s];

@@ -23,7 +23,11 @@
     X(128, 1, 256, 6, 2, true, true)       \
     X(256, 1, 256, 2, 2, false, true)      \
     X(128, 1, 256, 5, 4, true, true)       \
-    X(256, 1, 256, 3, 2, true, true)
+    X(256, 1, 256, 3, 2, true, true)       \
+    X(128, 2, 256, 4, 1, true, true)       \
+    X(128, 2, 256, 4, 2, true, true)       \
+    X(64, 2, 256, 8, 1, true, true)        \
+    X(256, 2, 256, 2, 1, true, true)
 // (512-source tiles were measured 2% faster but their longer FP32 partial
 // sums take the jerk's worst-case error past 1e-4 on dense inputs.)
 
