@@ -38,14 +38,16 @@ H = 2e-3
 K_MAX = 6
 DT_MAX = 2.0**-4
 FLOPS_PER_INTERACTION = 56      # FP32 flops of the Newtonian pair body (FFMA = 2), MUFU not counted
+BWD_FLOPS_PER_INTERACTION = 31  # the adjoint's Newtonian pair body, counted the same way
 WORKLOAD = "turbulent_cloud_N1048576_h2e-3"
 METRIC = "acc+jerk+tidal interactions/s at N=2^20 (mixed precision)"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one force-kernel launch from an ncu capture of
-# the default tile configuration on the turbulent cloud with N = 2^18, all
-# active (profiles/eval_mixed_kernel_default_turbulent_cloud_N262144.md).  The
-# traffic is the sources and targets streamed once, so it scales with N.
-TRAFFIC_CAPTURE = {"tile_config": 11, "n": 262144, "bytes": 21950976 + 15993600}
+# the tile configuration the library picks for this workload (17) on the
+# turbulent cloud with N = 2^18, all active
+# (profiles/eval_mixed_kernel_768x1_warp_release_turbulent_cloud_N262144.md).
+# The traffic is the sources and targets streamed once, so it scales with N.
+TRAFFIC_CAPTURE = {"tile_config": 17, "n": 262144, "bytes": 21778176 + 14417152}
 
 
 def parse():
@@ -276,6 +278,8 @@ def run_ours(args, rank, local, ws):
     value = total_units / t_total
     clocks = clk.summary()
 
+    # the step passes n_idx_max = N (the due count stays on the device)
+    used_cfg = args.tile_config if args.tile_config >= 0 else grav.default_tile_config(grav.MIXED, args.n)
     result = {
         "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
@@ -285,15 +289,12 @@ def run_ours(args, rank, local, ws):
                    "n_due_per_step": n_due, "h": H, "sources": args.n,
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "tile_config": grav.tile_configs(grav.MIXED)[
-                       args.tile_config if args.tile_config >= 0
-                       else grav.default_tile_config(grav.MIXED)]},
+                   "tile_config": grav.tile_configs(grav.MIXED)[used_cfg]},
         "gpu_launches": path.launches_per_step * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
 
-    used_cfg = args.tile_config if args.tile_config >= 0 else grav.default_tile_config(grav.MIXED)
     traffic = None
     if used_cfg == TRAFFIC_CAPTURE["tile_config"] and args.fraction == 1.0:
         traffic = TRAFFIC_CAPTURE["bytes"] * args.n / TRAFFIC_CAPTURE["n"]
@@ -387,6 +388,7 @@ def extras(args, path, dev, sms, peak32, flush):
     out["periodic_zeldovich_64cubed"] = periodic_extra(dev, flush)
     out["adaptive_softening_N1048576"] = soft_extra(path, dev, flush)
     out["tree_N1048576"] = tree_extra(path, dev, flush)
+    out["adjoint"] = backward_extra(path, dev, flush)
     out["batched_256_systems"] = batched_extra(dev, flush)
     out["adaptive_plummer_131072"] = adaptive_extra(dev)
     try:
@@ -552,6 +554,66 @@ def tree_extra(path, dev, flush):
         res[name] = {"ms": 1e3 * t, "interactions_per_s": inter / t,
                      "acc_rel_error_vs_direct": {"median": float(q[0]), "p99": float(q[1]),
                                                  "max": float(e.max())}}
+    return res
+
+
+def backward_extra(path, dev, flush):
+    """The adjoint (grav_eval_backward): gradients of L = sum w |a|^2 with
+    respect to positions and masses, every element a target and a source.
+    On the headline cloud (mixed; a_bar = 2 w a from the timed steps) and on
+    the differentiation workload, a Plummer sphere of 2^16 (mixed and FP64,
+    with the potential-energy term).  Flops per pair from the kernel's
+    Newtonian pair body: 20 FP32 instructions, 11 of them FMAs = 31 flops."""
+    import torch
+
+    from paper_2010_13792_gb300 import grav, ics
+    res = {"flops_per_interaction": BWD_FLOPS_PER_INTERACTION}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) * 1e-3)
+        return statistics.median(ts)
+
+    g = torch.Generator(device=dev).manual_seed(11)
+    n = path.n
+    w = torch.rand(n, 1, dtype=torch.float64, device=dev, generator=g)
+    a_bar = 2.0 * w * path.acc
+    pos_bar = torch.empty(n, 3, dtype=torch.float64, device=dev)
+    mass_bar = torch.empty(n, dtype=torch.float64, device=dev)
+    ws = grav.Workspace()
+    pm = grav.params(h=H, precision=grav.MIXED)
+    t = timed(lambda: grav.eval_backward(pm, path.pos, path.mass, a_bar, 0.0, None, path.tidal,
+                                         None, pos_bar, mass_bar, workspace=ws), 2)
+    res[f"cloud_N{n}_mixed"] = {"ms": 1e3 * t, "interactions_per_s": n * n / t,
+                                "tflops": BWD_FLOPS_PER_INTERACTION * n * n / t / 1e12}
+
+    m = 1 << 16
+    pos, vel, mass = ics.plummer(m)
+    f64 = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
+    P, V, M = f64(pos), f64(vel), f64(mass)
+    wp = f64(ics.rng(ics.BASE_SEED + 4).uniform(size=(m, 1)))
+    for name, prec in (("mixed", grav.MIXED), ("f64", grav.F64)):
+        p = grav.params(h=1e-3, precision=prec, want_pot=True)
+        acc = torch.empty(m, 3, dtype=torch.float64, device=dev)
+        jerk, tid = torch.empty_like(acc), torch.empty(m, 6, dtype=torch.float64, device=dev)
+        pot = torch.empty(m, dtype=torch.float64, device=dev)
+        grav.eval_active(p, P, V, M, None, None, m, acc, jerk, tid, pot, workspace=ws)
+        ab = 2.0 * wp * acc
+        pb = torch.empty(m, 3, dtype=torch.float64, device=dev)
+        mb = torch.empty(m, dtype=torch.float64, device=dev)
+        t = timed(lambda: grav.eval_backward(p, P, M, ab, 1.0, acc, tid, pot, pb, mb,
+                                             workspace=ws), 3)
+        res[f"plummer_N{m}_{name}"] = {"ms": 1e3 * t, "interactions_per_s": m * m / t,
+                                       "tflops": BWD_FLOPS_PER_INTERACTION * m * m / t / 1e12}
     return res
 
 

@@ -73,7 +73,8 @@ typedef struct grav_params {
     double eta;          /* tidal-timestep tolerance of Eq. (tidaltimestep) (> 0), e.g. 0.01 */
     int32_t precision;   /* GRAV_F64 or GRAV_MIXED */
     int32_t want_pot;    /* non-zero: also evaluate the potential Phi_i */
-    int32_t tile_config; /* -1 = library default, else an index < grav_tile_config_count(precision) */
+    int32_t tile_config; /* -1 = library default (grav_default_tile_config), else an
+                            index < grav_tile_config_count(precision) */
     int32_t max_split;   /* upper bound on source splits per target block; 0 = default */
     double box;          /* > 0: periodic cube [0, box)^3, every pair taken to its nearest
                             periodic image (the paper's Zeldovich setting); 0: open */
@@ -100,7 +101,19 @@ typedef struct grav_system {
 GRAV_API const char *grav_last_error_string(void);
 GRAV_API const char *grav_version(void);
 GRAV_API int32_t grav_tile_config_count(int32_t precision);
+/* Describes configuration `index` of a precision; index -1 describes the
+ * default of a small open-boundary evaluation.  GRAV_EINVAL for a bad
+ * precision or index, or a NULL out. */
 GRAV_API int grav_tile_config(int32_t precision, int32_t index, grav_tile_info *out);
+/* The configuration that tile_config = -1 selects for an evaluation of
+ * n_targets targets (the n_idx_max of the call): open boundaries
+ * (periodic = soft = 0), a periodic box (periodic != 0) or adaptive softening
+ * (soft != 0).  Open-boundary evaluations of at least 8192 targets take
+ * 768-thread CTAs, everything else 256-thread CTAs.  Returns
+ * the index (>= 0), or GRAV_EINVAL for a bad precision or n_targets < 0.  A
+ * property of the library's kernels; the paper has no counterpart. */
+GRAV_API int32_t grav_default_tile_config(int32_t precision, int32_t periodic, int32_t soft,
+                                          int64_t n_targets);
 
 /* ------------------------------------------------------------------------ */
 /* Selection: Eq. (3), Eq. (updatecondition) and Section 3's power-of-two     */

@@ -184,8 +184,10 @@ backward_kernel(const BwdArgs a)
             }
         }
         block_bbox<NT>(lo, hi, blo, bhi);
-        const float blo_r[3] = {blo[0], blo[1], blo[2]};
-        const float bhi_r[3] = {bhi[0], bhi[1], bhi[2]};
+        // each warp tests tiles against its own targets' box (lo/hi now hold
+        // it): the near and far loops synchronise nothing
+        const float blo_r[3] = {lo[0], lo[1], lo[2]};
+        const float bhi_r[3] = {hi[0], hi[1], hi[2]};
 
         T shi[KT][kNB], slo[KT][kNB];
 #pragma unroll

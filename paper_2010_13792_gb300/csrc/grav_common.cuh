@@ -99,6 +99,13 @@ __device__ __forceinline__ void fence_barrier_init()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Order this thread's earlier shared-memory accesses (generic proxy) before
+// bulk copies it issues afterwards (async proxy) into the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // One elected thread: arm `bar` for `bytes` and start the 1-D bulk copy
 // global -> shared (16-byte aligned addresses, size a multiple of 16).
 __device__ __forceinline__ void tma_load_1d(void *dst_smem, const void *src_gmem, uint32_t bytes,

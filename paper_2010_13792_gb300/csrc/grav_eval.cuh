@@ -2,11 +2,13 @@
 //
 // Direct summation, target-blocked: a CTA owns a block of BT = NT*KT targets
 // (KT per thread) and streams source tiles of S elements through shared
-// memory with 1-D TMA bulk copies (cp.async.bulk + mbarrier, double
-// buffered).  Every thread evaluates each staged source against its KT
-// targets with the SFU reciprocal square root; all lanes read the same source
-// (shared-memory broadcast).  This is CUDA-core work, not a contraction: no
-// tensor cores.
+// memory with 1-D TMA bulk copies (cp.async.bulk + mbarrier, a ring of two or
+// three stages; in the open-boundary mixed kernels each warp releases a stage
+// on its own and the last warp to release it issues the refill, so no block
+// barrier separates the tiles).  Every thread evaluates each staged source
+// against its KT targets with the SFU reciprocal square root; all lanes read
+// the same source (shared-memory broadcast).  This is CUDA-core work, not a
+// contraction: no tensor cores.
 //
 // Accumulated sums per target (d = x_j - x_i, g' = -g/3 = r^-5 beyond h):
 //   A  = sum m f d          Tp = sum m g' d d^T       P = sum m phi (optional)
@@ -1121,18 +1123,42 @@ pack_tiles_batched_kernel(const BatchView b, const double *__restrict__ pos,
 // thread); otherwise in registers.
 // ---------------------------------------------------------------------------
 
-template <int NT, int KT, int S, bool POT, bool SACC, bool PAIR = false>
+template <int NT, int KT, int S, bool POT, bool SACC, bool PAIR = false, int NST = 2>
 struct MixedSmem {
     static constexpr int BT = NT * KT;
     static constexpr int NC = POT ? kNCPot : kNC;
-    float4 stage[2][PAIR ? 7 * S / 4 : 2 * S];   // 28 or 32 bytes per source
+    static constexpr int kStages = NST;
+    float4 stage[NST][PAIR ? 7 * S / 4 : 2 * S];   // 28 or 32 bytes per source
     float acc[SACC ? NC * 2 * BT : 1];     // [c][hi, lo][BT]
     double x[SACC ? 3 * BT : 1];           // [c][BT]
-    uint64_t bar[2];
+    uint64_t bar[NST];
+    int done[NST];                         // warps finished with the tile in each stage
+    unsigned issued[NST];                  // copies issued into each stage
     float blo[3], bhi[3];
     int abort_flag;
     long long ticket;
 };
+
+// Stages of the mixed kernels' source ring: open-boundary kernels release a
+// stage per warp (no block barrier per tile), so they keep one more stage in
+// flight to let warps drift apart by up to two tiles.
+template <int MODE>
+constexpr int mixed_stages() { return MODE == kModeOpen ? 3 : 2; }
+
+template <typename Sm>
+__device__ __forceinline__ void init_mixed_ring(Sm &sm)
+{
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Sm::kStages; ++s) {
+            mbar_init(&sm.bar[s], 1);
+            sm.done[s] = 0;
+            sm.issued[s] = 0;
+        }
+        sm.abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+}
 
 template <typename Sm>
 __device__ __forceinline__ void init_ring(Sm &sm)
@@ -1145,15 +1171,38 @@ __device__ __forceinline__ void init_ring(Sm &sm)
     __syncthreads();
 }
 
+// Before a mixed kernel exits: wait (bounded) for any copy still in flight
+// into its shared memory.  With per-warp release a copy is outstanding in
+// stage s exactly when thread 0 has seen fewer completions there than were
+// issued (at most one: a refill needs every warp, thread 0's included, to
+// have consumed the previous copy).
+template <int MODE, typename Sm>
+__device__ __forceinline__ void drain_mixed_ring(Sm &sm, const Ring &ring, int32_t *flags)
+{
+    if (MODE != kModeOpen) {
+        drain_ring<Sm::kStages>(sm.bar, ring, flags);
+        return;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Sm::kStages; ++s)
+            if ((sm.issued[s] & 1u) != ((ring.parity >> s) & 1u))
+                mbar_wait_bounded(&sm.bar[s], (ring.parity >> s) & 1u, flags);
+    }
+}
+
 // One work item of the mixed kernel; false if a bounded wait gave up.
 template <int NT, int KT, int S, int U, bool POT, bool SACC, bool PAIR, int MODE>
-__device__ __forceinline__ bool mixed_item(const EvalArgs &a,
-                                           MixedSmem<NT, KT, S, POT, SACC, PAIR> &sm, Ring &ring,
-                                           const ItemSpec &it)
+__device__ __forceinline__ bool mixed_item(
+    const EvalArgs &a, MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()> &sm, Ring &ring,
+    const ItemSpec &it)
 {
-    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR>;
+    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>;
     constexpr int BT = Sm::BT;
-    constexpr int NSTAGE = 2;
+    constexpr int NSTAGE = Sm::kStages;
+    // open boundaries: each warp releases a stage when it is done with it and
+    // the last warp to do so refills it (no block barrier per tile)
+    constexpr bool kWarpRelease = MODE == kModeOpen;
     constexpr int NC = Sm::NC;
     constexpr bool soft = MODE == kModeSoft;
     constexpr uint32_t kTileBytes = PAIR ? S * 28 : S * 2 * sizeof(float4);
@@ -1191,8 +1240,13 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
         }
     }
     block_bbox<NT>(lo, hi, sm.blo, sm.bhi);     // (its barriers also publish sm.x)
-    const float blo_r[3] = {sm.blo[0], sm.blo[1], sm.blo[2]};
-    const float bhi_r[3] = {sm.bhi[0], sm.bhi[1], sm.bhi[2]};
+    // the near/far test of a tile: with per-warp release each warp takes it
+    // against its own targets' box (lo/hi now hold it), which culls far more
+    // tiles when the targets are sparse; otherwise against the block's box
+    const float blo_r[3] = {kWarpRelease ? lo[0] : sm.blo[0], kWarpRelease ? lo[1] : sm.blo[1],
+                            kWarpRelease ? lo[2] : sm.blo[2]};
+    const float bhi_r[3] = {kWarpRelease ? hi[0] : sm.bhi[0], kWarpRelease ? hi[1] : sm.bhi[1],
+                            kWarpRelease ? hi[2] : sm.bhi[2]};
 
     // adaptive softening: the targets' 1/h_i and zeta_i, the block's largest
     // support, and the shared copy of a near tile's (1/h_j, zeta_j)
@@ -1237,6 +1291,7 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
             if (t < t_end) {
                 tma_load_1d(sm.stage[s], src + (int64_t)t * 2 * S, kTileBytes, &sm.bar[s]);
                 ring.pending |= 1u << s;
+                if (kWarpRelease) sm.issued[s] += 1u;
             }
         }
     }
@@ -1350,21 +1405,47 @@ __device__ __forceinline__ bool mixed_item(const EvalArgs &a,
             }
         }
 
-        __syncthreads();                       // all reads of stage s are done
-        if (threadIdx.x == 0) {
-            if (got) ring.pending &= ~(1u << s);
-            if (t + NSTAGE < t_end && !sm.abort_flag) {
-                tma_load_1d(sm.stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes, &sm.bar[s]);
-                ring.pending |= 1u << s;
+        if (kWarpRelease) {
+            // this warp is done reading stage s; the last warp refills it
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) {
+                __threadfence_block();
+                const int prev = atomicAdd(&sm.done[s], 1);
+                if (prev == NT / 32 - 1) {
+                    sm.done[s] = 0;
+                    __threadfence_block();
+                    if (t + NSTAGE < t_end && !*(volatile int *)&sm.abort_flag) {
+                        fence_proxy_async_smem();
+                        tma_load_1d(sm.stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes,
+                                    &sm.bar[s]);
+                        sm.issued[s] += 1u;
+                    }
+                }
             }
+            __syncwarp();
+            if (*(volatile int *)&sm.abort_flag) break;
+        } else {
+            __syncthreads();                       // all reads of stage s are done
+            if (threadIdx.x == 0) {
+                if (got) ring.pending &= ~(1u << s);
+                if (t + NSTAGE < t_end && !sm.abort_flag) {
+                    tma_load_1d(sm.stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes,
+                                &sm.bar[s]);
+                    ring.pending |= 1u << s;
+                }
+            }
+            if (sm.abort_flag) break;
         }
-        if (sm.abort_flag) break;
         g = gn;
 #pragma unroll
         for (int q = 0; q < KT; ++q)
 #pragma unroll
             for (int c = 0; c < 3; ++c) tx[q][c] = tx_next[q][c];
     }
+
+    // warps may leave the tile loop at different tiles: meet here so that
+    // every thread returns the same status
+    if (kWarpRelease) __syncthreads();
 
     // ---- results ----
 #pragma unroll
@@ -1395,11 +1476,11 @@ template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR
 __global__ void __launch_bounds__(NT, MINB)
 eval_mixed_kernel(const EvalArgs a)
 {
-    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR>;
+    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>;
     constexpr int BT = Sm::BT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
-    init_ring(sm);
+    init_mixed_ring(sm);
     Ring ring{0u, 0u};
     const int64_t n_act = active_count(a);
     const int64_t n_tb = (n_act + BT - 1) / BT;
@@ -1422,7 +1503,7 @@ eval_mixed_kernel(const EvalArgs a)
         if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }
-    drain_ring<2>(sm.bar, ring, a.flags);
+    drain_mixed_ring<MODE>(sm, ring, a.flags);
 }
 
 // Batched: items of all systems from the plan, taken through an atomic
@@ -1433,11 +1514,11 @@ template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR
 __global__ void __launch_bounds__(NT, MINB)
 eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
 {
-    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR>;
+    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>;
     constexpr int BT = Sm::BT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
-    init_ring(sm);
+    init_mixed_ring(sm);
     Ring ring{0u, 0u};
     const int64_t total = b.hdr->total_items;
     for (;;) {
@@ -1462,7 +1543,7 @@ eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
         if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }
-    drain_ring<2>(sm.bar, ring, a.flags);
+    drain_mixed_ring<MODE>(sm, ring, a.flags);
 }
 
 // ---------------------------------------------------------------------------
@@ -1505,8 +1586,13 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
         }
     }
     block_bbox<NT>(lo, hi, sm.blo, sm.bhi);
-    const float blo_r[3] = {sm.blo[0], sm.blo[1], sm.blo[2]};
-    const float bhi_r[3] = {sm.bhi[0], sm.bhi[1], sm.bhi[2]};
+    // open boundaries: each warp tests tiles against its own targets' box
+    // (lo/hi now hold it; the near and far loops synchronise nothing)
+    constexpr bool kWarpBox = MODE == kModeOpen;
+    const float blo_r[3] = {kWarpBox ? lo[0] : sm.blo[0], kWarpBox ? lo[1] : sm.blo[1],
+                            kWarpBox ? lo[2] : sm.blo[2]};
+    const float bhi_r[3] = {kWarpBox ? hi[0] : sm.bhi[0], kWarpBox ? hi[1] : sm.bhi[1],
+                            kWarpBox ? hi[2] : sm.bhi[2]};
     double hinv_i = 1.0, zeta_i = 0.0;
     float h_block = 0.0f;
     if (MODE == kModeSoft) {
@@ -1713,6 +1799,9 @@ typedef void (*batched_launch_fn)(const EvalArgs &, const BatchView &, int grid,
 typedef void (*batched_pack_fn)(const BatchView &, const double *, const double *, const double *,
                                 TileGeom *, void *, int32_t *, int max_tiles, cudaStream_t);
 
+// Upper bound on the tile configurations of one precision (host caches).
+constexpr int kMaxTileConfigs = 32;
+
 struct EvalConfig {
     int32_t precision;
     int32_t threads, kt, s, unroll, sacc;
@@ -1728,14 +1817,14 @@ struct EvalConfig {
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 void launch_mixed(const EvalArgs &a, int grid, cudaStream_t st)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>);
     eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE><<<grid, NT, bytes, st>>>(a);
 }
 
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 int occupancy_mixed(int *b)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>);
     auto k = eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
@@ -1745,14 +1834,14 @@ int occupancy_mixed(int *b)
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 void launch_mixed_batched(const EvalArgs &a, const BatchView &b, int grid, cudaStream_t st)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>);
     eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE><<<grid, NT, bytes, st>>>(a, b);
 }
 
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 int occupancy_mixed_batched(int *b)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>);
     auto k = eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;

@@ -36,6 +36,8 @@ GRAV_MIXED_CONFIG_LIST(GRAV_MIXED_EXTERN)
      launch_pack_batched<S, true, true, PAIR>, PAIR},
 
 static const EvalConfig kMixedConfigs[] = {GRAV_MIXED_CONFIG_LIST(GRAV_MIXED_CFG)};
+static_assert(sizeof(kMixedConfigs) / sizeof(kMixedConfigs[0]) <= kMaxTileConfigs,
+              "more tile configurations than the host caches hold");
 
 const EvalConfig *mixed_configs(int *count)
 {

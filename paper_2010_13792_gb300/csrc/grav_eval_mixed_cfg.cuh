@@ -27,7 +27,11 @@
     X(128, 2, 256, 4, 1, true, true)       \
     X(128, 2, 256, 4, 2, true, true)       \
     X(64, 2, 256, 8, 1, true, true)        \
-    X(256, 2, 256, 2, 1, true, true)
+    X(256, 2, 256, 2, 1, true, true)       \
+    X(384, 1, 256, 2, 4, true, true)       \
+    X(768, 1, 256, 1, 4, true, true)       \
+    X(768, 1, 256, 1, 8, true, true)       \
+    X(384, 1, 256, 2, 8, true, true)
 // (512-source tiles were measured 2% faster but their longer FP32 partial
 // sums take the jerk's worst-case error past 1e-4 on dense inputs.)
 

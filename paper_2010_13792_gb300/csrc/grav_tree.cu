@@ -60,6 +60,8 @@ struct TreeView {
     int8_t *n_child, *level;
     double *m, *com, *vcom;
     float4 *vcom32;       // mixed walk: node mean velocity in FP32
+    float4 *chi, *clo;    // node centre of mass as two FP32 parts (com = chi + clo to 2^-48);
+                          // chi.w = m in FP32, clo.w = L^2 (node side squared) in FP32
     float4 *soff;         // mixed walk, per tree position: (x_j - com of its leaf, m_j) in FP32
     float4 *svel;         // mixed walk, per tree position: v_j in FP32
     int32_t *flags;
@@ -72,7 +74,8 @@ int64_t max_nodes_for(int64_t n, int32_t leaf)
 
 struct TreeLayout {
     int64_t key_a, key_b, val_a, val_b, hist, part, frame, counters;
-    int64_t first, count, child_first, next, n_child, level, m, com, vcom, vcom32, soff, svel, total;
+    int64_t first, count, child_first, next, n_child, level, m, com, vcom, vcom32, chi, clo, soff, svel;
+    int64_t total;
     int64_t n_sort_blocks, max_nodes;
 };
 
@@ -107,6 +110,8 @@ TreeLayout tree_layout(int64_t n, int32_t leaf)
     L.com = take(mn * 24);
     L.vcom = take(mn * 24);
     L.vcom32 = take(mn * 16);
+    L.chi = take(mn * 16);
+    L.clo = take(mn * 16);
     L.soff = take(n * 16);
     L.svel = take(n * 16);
     L.total = o;
@@ -430,20 +435,33 @@ __global__ void __launch_bounds__(256) tree_next_kernel(TreeView t, int lvl)
     }
 }
 
-// FP32 data of the mixed walk: every node's mean velocity, and per tree
-// position the element's offset from its leaf's centre of mass (formed in
-// FP64, rounded once), mass and velocity.
-__global__ void __launch_bounds__(256) tree_mixed_data_kernel(TreeView t, const double *__restrict__ pos,
-                                                              const double *__restrict__ vel,
-                                                              const double *__restrict__ mass)
+// FP32 data of the walk.  Every node: its centre of mass as two FP32 parts
+// (hi = com rounded, lo = the remainder rounded), its mass and squared side
+// in FP32 (the opening decisions' FP32 bounds), its mean velocity in FP32.
+// Mixed walk only, per tree position: the element's offset from its leaf's
+// centre of mass (formed in FP64, rounded once), mass and velocity.
+__global__ void __launch_bounds__(256) tree_walk_data_kernel(TreeView t, const double *__restrict__ pos,
+                                                             const double *__restrict__ vel,
+                                                             const double *__restrict__ mass,
+                                                             bool mixed)
 {
     int64_t nn = t.counters[0];
     if (nn > t.max_nodes) nn = t.max_nodes;
+    const double ext = t.frame[3];
     for (int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x; k < nn; k += (int64_t)gridDim.x * 256) {
         const double *vc = t.vcom + 3 * k;
         t.vcom32[k] = make_float4(__double2float_rn(vc[0]), __double2float_rn(vc[1]),
                                   __double2float_rn(vc[2]), 0.0f);
-        if (t.child_first[k] >= 0) continue;
+        float hi[3], lo[3];
+        for (int c = 0; c < 3; ++c) {
+            const double x = t.com[3 * k + c];
+            hi[c] = __double2float_rn(x);
+            lo[c] = __double2float_rn(__dsub_rn(x, (double)hi[c]));
+        }
+        const double L = scalbn(ext, -(int)t.level[k]);
+        t.chi[k] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(t.m[k]));
+        t.clo[k] = make_float4(lo[0], lo[1], lo[2], __double2float_rn(__dmul_rn(L, L)));
+        if (!mixed || t.child_first[k] >= 0) continue;
         const double *c = t.com + 3 * k;
         const int32_t f = t.first[k], cnt = t.count[k];
         for (int32_t q = f; q < f + cnt; ++q) {
@@ -539,10 +557,63 @@ __device__ __forceinline__ void pair_f(float acc[kNCPot], float m, float dx, flo
     acc[PSUM] += mp;
 }
 
-// MIXED: decisions and the target-to-node offsets in FP64, every pair term
-// in FP32 (leaf elements from their FP32 offsets to the leaf's centre of mass
-// plus the target's offset to it), FP32 sums of up to 32 interactions added
-// into FP64.
+// Offset from a target to a node's centre of mass in FP32, and the geometric
+// opening criterion of Section 3 (accept iff L^2 < Theta^2 r^2) decided from
+// FP32 bounds when they are conclusive.  The offset is formed from the
+// two-part FP32 forms of both positions (x = hi + lo to 2^-48 relative):
+// TwoSum of the hi parts plus the difference of the lo parts, so it is within
+// 2^-24 |d| + 2^-46 (|com| + |x|) of the exact difference; each component is
+// widened by 2^-23 |d| + 2^-44 (|com| + |x|) into an interval that holds the
+// exact one, and r^2 is bracketed by the sums of squares of the interval
+// ends.  The FP64 decision (L^2 and Theta^2 r^2 rounded from values within
+// 2^-50 of the exact ones) then agrees with the FP32 one whenever L^2 is
+// below Theta^2 r_lo^2 (1 - 2^-18) or above Theta^2 r_hi^2 (1 + 2^-18), a
+// margin far beyond the few FP32 roundings of the bounds; the guards keep
+// every FP32 quantity normal.  Returns 1 (accept), 0 (open) or -1 (FP32
+// bounds inconclusive: the caller decides in FP64).
+__device__ __forceinline__ int open_test_f32(const float4 &hi, const float4 &lo, const float xh[3],
+                                             const float xl[3], float theta2f, float d[3])
+{
+    const float ch[3] = {hi.x, hi.y, hi.z}, cl[3] = {lo.x, lo.y, lo.z};
+    float r2lo = 0.0f, r2hi = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float a = ch[c], b = -xh[c];
+        const float sum = __fadd_rn(a, b);
+        const float bb = __fsub_rn(sum, a);
+        const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(b, bb));
+        d[c] = __fadd_rn(sum, __fadd_rn(err, __fsub_rn(cl[c], xl[c])));
+        const float ad = fabsf(d[c]);
+        const float del = __fmaf_rn(0x1p-23f, ad, 0x1p-44f * (fabsf(a) + fabsf(b)));
+        const float l = fmaxf(__fsub_rn(ad, del), 0.0f), u = __fadd_rn(ad, del);
+        r2lo = __fmaf_rn(l, l, r2lo);
+        r2hi = __fmaf_rn(u, u, r2hi);
+    }
+    const float L2 = lo.w;
+    if (L2 >= 0x1p-100f && r2hi <= 0x1p100f && theta2f <= 0x1p20f) {
+        if (L2 < __fmul_rn(__fmul_rn(theta2f, r2lo), 1.0f - 0x1p-18f)) return 1;
+        if (L2 > __fmul_rn(__fmul_rn(theta2f, r2hi), 1.0f + 0x1p-18f)) return 0;
+    }
+    return -1;
+}
+
+// The walk is warp-coherent: the 32 targets of a warp (neighbours in tree
+// order) share one traversal position and read each node once.  Every lane
+// still takes its own decisions, in the order and with the operations of a
+// walk of its own: the warp descends into a node when any active lane opens
+// it, and a lane that accepted a node (or is past its subtree) stays idle
+// until the traversal leaves that node's range of tree positions -- children
+// partition their parent's range in order, so a pre-order walk reaches the
+// next node outside it exactly at the node the lane's own walk goes to next.
+// Each lane therefore visits the same nodes, in the same order, as a walk of
+// its own, and its sums are the same bit for bit.
+//
+// Decisions are those of FP64 arithmetic (open_test_f32, else FP64; always
+// FP64 with the relative criterion).  MIXED: every pair term in FP32 (nodes
+// from the FP32 offset of open_test_f32; leaf elements from their FP32
+// offsets to the leaf's centre of mass plus that offset), FP32 sums of up to
+// 32 interactions added into FP64.  FP64 walk: offsets and pair terms in
+// FP64.
 template <bool POT, bool MIXED>
 __global__ void __launch_bounds__(kWalkNT) tree_walk_kernel(TreeView t, EvalArgs a, WalkArgs w)
 {
@@ -553,12 +624,18 @@ __global__ void __launch_bounds__(kWalkNT) tree_walk_kernel(TreeView t, EvalArgs
         if (c < n_tgt) n_tgt = c;
     }
     const int64_t s = (int64_t)blockIdx.x * kWalkNT + threadIdx.x;
-    if (s >= n_tgt) return;
-    int64_t i = w.idx ? (int64_t)w.idx[s] : (int64_t)t.order[s];
-    if (i < 0 || i >= t.n) {
-        flag_or(t.flags, GRAV_FLAG_BADINDEX);
-        return;
+    bool live = s < n_tgt;
+    int64_t i = 0;
+    if (live) {
+        i = w.idx ? (int64_t)w.idx[s] : (int64_t)t.order[s];
+        if (i < 0 || i >= t.n) {
+            flag_or(t.flags, GRAV_FLAG_BADINDEX);
+            live = false;
+            i = 0;
+        }
     }
+    // the whole warp walks together; a warp without live targets leaves
+    if (__ballot_sync(0xffffffffu, live) == 0u) return;
     const double xi[3] = {w.pos[3 * i], w.pos[3 * i + 1], w.pos[3 * i + 2]};
     const double vi[3] = {w.vel[3 * i], w.vel[3 * i + 1], w.vel[3 * i + 2]};
     const double h2 = w.h * w.h, hinv = 1.0 / w.h;
@@ -581,83 +658,115 @@ __global__ void __launch_bounds__(kWalkNT) tree_walk_kernel(TreeView t, EvalArgs
     }
     const float h2f = (float)(w.h * w.h), hinvf = (float)(1.0 / w.h);
     const float vi32[3] = {__double2float_rn(vi[0]), __double2float_rn(vi[1]), __double2float_rn(vi[2])};
+    float xh[3], xl[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        xh[c] = __double2float_rn(xi[c]);
+        xl[c] = __double2float_rn(__dsub_rn(xi[c], (double)xh[c]));
+    }
+    const float theta2f = __double2float_rn(w.theta2);
     int pending = 0;
     long long inter = 0;
-    int32_t node = 0;
+    // tree positions below skip_until belong to nodes this lane does not
+    // visit (dead lanes visit none)
+    int32_t skip_until = live ? 0 : INT32_MAX;
+    int32_t node = 0;                          // shared by the warp
     int64_t steps = 0;
     const int64_t n_nodes = t.counters[0];
     while (node >= 0) {
         if (++steps > n_nodes + 1) {            // a walk visits each node at most once
-            flag_or(t.flags, GRAV_FLAG_OVERFLOW);
+            if ((threadIdx.x & 31) == 0) flag_or(t.flags, GRAV_FLAG_OVERFLOW);
             break;
         }
-        const double dx = __dsub_rn(t.com[3 * (int64_t)node], xi[0]);
-        const double dy = __dsub_rn(t.com[3 * (int64_t)node + 1], xi[1]);
-        const double dz = __dsub_rn(t.com[3 * (int64_t)node + 2], xi[2]);
-        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        const double L = scalbn(ext, -(int)t.level[node]);
-        const double L2 = __dmul_rn(L, L);
-        const double mn = t.m[node];
-        bool accept = L2 < __dmul_rn(w.theta2, r2);
-        if (accept && rel > 0.0)
-            accept = __dmul_rn(__dmul_rn(a.G, mn), L2) <= __dmul_rn(__dmul_rn(rel, r2), r2);
-        if (MIXED && (accept || t.child_first[node] < 0)) {
-            const float dxf = __double2float_rn(dx), dyf = __double2float_rn(dy),
-                        dzf = __double2float_rn(dz);
-            if (accept) {
-                const float4 vc = t.vcom32[node];
-                pair_f(accf, __double2float_rn(mn), dxf, dyf, dzf, vc.x - vi32[0], vc.y - vi32[1],
-                       vc.z - vi32[2], h2f, hinvf, false);
-                ++inter;
-                ++pending;
-            } else {
-                const int32_t f = t.first[node], c = t.count[node];
-                for (int32_t q = f; q < f + c; ++q) {
-                    const float4 o = t.soff[q];
-                    const float4 v = t.svel[q];
-                    const bool self = t.order[q] == i;
-                    pair_f(accf, o.w, o.x + dxf, o.y + dyf, o.z + dzf, v.x - vi32[0], v.y - vi32[1],
-                           v.z - vi32[2], h2f, hinvf, self);
-                    inter += !self;
-                    ++pending;
-                }
+        const int32_t nfirst = t.first[node], ncount = t.count[node];
+        const int32_t child = t.child_first[node];
+        bool open = false;
+        if (nfirst >= skip_until) {
+            const float4 chi = t.chi[node], clo = t.clo[node];
+            float d[3];
+            int decided = open_test_f32(chi, clo, xh, xl, theta2f, d);
+            if (decided < 0 || rel > 0.0) {
+                const double dx = __dsub_rn(t.com[3 * (int64_t)node], xi[0]);
+                const double dy = __dsub_rn(t.com[3 * (int64_t)node + 1], xi[1]);
+                const double dz = __dsub_rn(t.com[3 * (int64_t)node + 2], xi[2]);
+                const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                const double L = scalbn(ext, -(int)t.level[node]);
+                const double L2 = __dmul_rn(L, L);
+                bool acc64 = L2 < __dmul_rn(w.theta2, r2);
+                if (acc64 && rel > 0.0)
+                    acc64 = __dmul_rn(__dmul_rn(a.G, t.m[node]), L2) <= __dmul_rn(__dmul_rn(rel, r2), r2);
+                decided = acc64 ? 1 : 0;
             }
-            node = t.next[node];
-        } else if (accept) {
-            pair_d(acc, mn, dx, dy, dz, t.vcom[3 * (int64_t)node] - vi[0],
-                   t.vcom[3 * (int64_t)node + 1] - vi[1], t.vcom[3 * (int64_t)node + 2] - vi[2], h2,
-                   hinv, false);
-            ++inter;
-            ++pending;
-            node = t.next[node];
-        } else if (t.child_first[node] < 0) {
-            const int32_t f = t.first[node], c = t.count[node];
-            for (int32_t q = f; q < f + c; ++q) {
-                const int32_t j = t.order[q];
-                pair_d(acc, w.mass[j], w.pos[3 * j] - xi[0], w.pos[3 * j + 1] - xi[1],
-                       w.pos[3 * j + 2] - xi[2], w.vel[3 * j] - vi[0], w.vel[3 * j + 1] - vi[1],
-                       w.vel[3 * j + 2] - vi[2], h2, hinv, j == i);
-                inter += (j != i);
-                ++pending;
-            }
-            node = t.next[node];
-        } else {
-            node = t.child_first[node];
-        }
-        if (pending >= kFlushEvery) {
-#pragma unroll
-            for (int c = 0; c < kNCPot; ++c) {
+            const bool accept = decided == 1;
+            if (accept) skip_until = nfirst + ncount;
+            if (accept || child < 0) {
+                // an accepted node is one interaction, a leaf its elements in
+                // order; both run through one loop so that the lanes of a warp
+                // that accept and those that sum the leaf share its passes
+                const int32_t cnt = accept ? 1 : ncount;
                 if (MIXED) {
-                    shi[c] += (double)accf[MIXED ? c : 0];
-                    accf[MIXED ? c : 0] = 0.0f;
+                    const float4 vc = t.vcom32[node];
+                    for (int32_t q = 0; q < cnt; ++q) {
+                        float4 o = make_float4(0.0f, 0.0f, 0.0f, chi.w), v = vc;
+                        bool self = false;
+                        if (!accept) {
+                            o = t.soff[nfirst + q];
+                            v = t.svel[nfirst + q];
+                            self = t.order[nfirst + q] == i;
+                        }
+                        pair_f(accf, o.w, o.x + d[0], o.y + d[1], o.z + d[2], v.x - vi32[0],
+                               v.y - vi32[1], v.z - vi32[2], h2f, hinvf, self);
+                        inter += !self;
+                        ++pending;
+                    }
                 } else {
-                    two_sum_acc(shi[c], slo[c], acc[c]);
-                    acc[c] = 0.0;
+                    for (int32_t q = 0; q < cnt; ++q) {
+                        double m, dx, dy, dz, ux, uy, uz;
+                        bool self = false;
+                        if (accept) {
+                            m = t.m[node];
+                            dx = __dsub_rn(t.com[3 * (int64_t)node], xi[0]);
+                            dy = __dsub_rn(t.com[3 * (int64_t)node + 1], xi[1]);
+                            dz = __dsub_rn(t.com[3 * (int64_t)node + 2], xi[2]);
+                            ux = t.vcom[3 * (int64_t)node] - vi[0];
+                            uy = t.vcom[3 * (int64_t)node + 1] - vi[1];
+                            uz = t.vcom[3 * (int64_t)node + 2] - vi[2];
+                        } else {
+                            const int32_t j = t.order[nfirst + q];
+                            m = w.mass[j];
+                            dx = w.pos[3 * j] - xi[0];
+                            dy = w.pos[3 * j + 1] - xi[1];
+                            dz = w.pos[3 * j + 2] - xi[2];
+                            ux = w.vel[3 * j] - vi[0];
+                            uy = w.vel[3 * j + 1] - vi[1];
+                            uz = w.vel[3 * j + 2] - vi[2];
+                            self = j == i;
+                        }
+                        pair_d(acc, m, dx, dy, dz, ux, uy, uz, h2, hinv, self);
+                        inter += !self;
+                        ++pending;
+                    }
                 }
+            } else {
+                open = true;
             }
-            pending = 0;
+            if (pending >= kFlushEvery) {
+#pragma unroll
+                for (int c = 0; c < kNCPot; ++c) {
+                    if (MIXED) {
+                        shi[c] += (double)accf[MIXED ? c : 0];
+                        accf[MIXED ? c : 0] = 0.0f;
+                    } else {
+                        two_sum_acc(shi[c], slo[c], acc[c]);
+                        acc[c] = 0.0;
+                    }
+                }
+                pending = 0;
+            }
         }
+        node = __any_sync(0xffffffffu, open) ? child : t.next[node];
     }
+    if (!live) return;
     double sum[kNCPot];
 #pragma unroll
     for (int c = 0; c < kNCPot; ++c) {
@@ -746,6 +855,8 @@ extern "C" int grav_eval_tree(const grav_params *p, const grav_tree_params *tp, 
     t.com = reinterpret_cast<double *>(ws + L.com);
     t.vcom = reinterpret_cast<double *>(ws + L.vcom);
     t.vcom32 = reinterpret_cast<float4 *>(ws + L.vcom32);
+    t.chi = reinterpret_cast<float4 *>(ws + L.chi);
+    t.clo = reinterpret_cast<float4 *>(ws + L.clo);
     t.soff = reinterpret_cast<float4 *>(ws + L.soff);
     t.svel = reinterpret_cast<float4 *>(ws + L.svel);
     t.flags = flags_dev;
@@ -788,7 +899,7 @@ extern "C" int grav_eval_tree(const grav_params *p, const grav_tree_params *tp, 
         tree_moment_kernel<<<g, 256, 0, st>>>(t, pos, vel, mass, lvl);
     for (int lvl = 0; lvl < kMaxLevel; ++lvl) tree_next_kernel<<<g, 256, 0, st>>>(t, lvl);
     const bool mixed = p->precision == GRAV_MIXED;
-    if (mixed) tree_mixed_data_kernel<<<g, 256, 0, st>>>(t, pos, vel, mass);
+    tree_walk_data_kernel<<<g, 256, 0, st>>>(t, pos, vel, mass, mixed);
     rc = check_launch("grav_eval_tree/build");
     if (rc) return rc;
     if (order_out) {

@@ -96,6 +96,7 @@ _SIGS = {
     "grav_version": (ctypes.c_char_p, []),
     "grav_tile_config_count": (_c_i32, [_c_i32]),
     "grav_tile_config": (ctypes.c_int, [_c_i32, _c_i32, ctypes.POINTER(TileInfo)]),
+    "grav_default_tile_config": (_c_i32, [_c_i32, _c_i32, _c_i32, ctypes.c_int64]),
     "grav_select_due": (ctypes.c_int, [_c_i64, _c_i64, _c_i32, _c_ptr, _c_ptr, _c_ptr, _c_dbl,
                                        _c_dbl, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr]),
     "grav_compact_workspace_bytes": (_c_i64, [_c_i64]),
@@ -198,17 +199,15 @@ def version() -> str:
     return lib().grav_version().decode()
 
 
-def default_tile_config(precision: int) -> int:
-    """Index of the library's default tile configuration for a precision."""
-    ti = TileInfo()
-    _err("grav_tile_config", lib().grav_tile_config(precision, -1, ctypes.byref(ti)))
-    key = (ti.threads, ti.targets_per_thread, ti.sources_per_tile, ti.unroll,
-           ti.shared_accumulators)
-    for c in tile_configs(precision):
-        if (c["threads"], c["targets_per_thread"], c["sources_per_tile"], c["unroll"],
-                c["shared_accumulators"]) == key:
-            return c["index"]
-    return -1
+def default_tile_config(precision: int, n_targets: int = 0, periodic: bool = False,
+                        soft: bool = False) -> int:
+    """Index of the tile configuration the library picks (tile_config = -1)
+    for an evaluation of n_targets targets in a precision and mode."""
+    r = int(lib().grav_default_tile_config(int(precision), int(bool(periodic)), int(bool(soft)),
+                                           int(n_targets)))
+    if r < 0:
+        _err("grav_default_tile_config", r)
+    return r
 
 
 def tile_configs(precision: int):

@@ -43,7 +43,7 @@ def test_mixed_uniform_sphere_4096(sphere4096):
     assert_mixed(e)
 
 
-@pytest.mark.parametrize("cfg", range(16))
+@pytest.mark.parametrize("cfg", range(24))
 def test_mixed_tile_configs(cfg):
     if cfg >= grav.lib().grav_tile_config_count(grav.MIXED):
         pytest.skip("no such tile configuration")
@@ -218,7 +218,7 @@ def test_cloud_2e20_f64_sampled(cloud_2e20):
     assert_f64(errors(out, ref, rows))
 
 
-@pytest.mark.parametrize("cfg", range(16))
+@pytest.mark.parametrize("cfg", range(24))
 def test_cloud_2e20_every_mixed_config(cloud_2e20, cfg):
     if cfg >= grav.lib().grav_tile_config_count(grav.MIXED):
         pytest.skip("no such tile configuration")

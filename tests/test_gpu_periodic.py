@@ -59,7 +59,7 @@ def test_small_box_tiles_reach_across(precision):
     (assert_f64 if precision == grav.F64 else assert_mixed)(errors(out, ref, idx))
 
 
-@pytest.mark.parametrize("cfg", range(16))
+@pytest.mark.parametrize("cfg", range(24))
 def test_every_mixed_config_periodic(cfg):
     if cfg >= grav.lib().grav_tile_config_count(grav.MIXED):
         pytest.skip("no such tile configuration")

@@ -108,7 +108,7 @@ def test_eval_soft_target_subset(plummer_solved, precision):
     assert np.all(np.isnan(out["acc"][rest]))
 
 
-@pytest.mark.parametrize("cfg", range(16))
+@pytest.mark.parametrize("cfg", range(24))
 def test_every_mixed_config_soft(cfg):
     if cfg >= grav.lib().grav_tile_config_count(grav.MIXED):
         pytest.skip("no such tile configuration")
