@@ -6,8 +6,10 @@
 //   mass_bar_k = -G sum_{i!=k} f (d . a_bar_i) + w_bar Phi_k,      d = x_i - x_k,
 // obtained by differentiating a_i = G sum_j m_j f(r) d (Eq. 4's acceleration)
 // with respect to x_k and m_k; T_k = d a_k / d x_k is the forward tidal tensor.
-// The paper has no adjoint.  The kernel is the forward direct sum with the
-// source attribute a_bar_i in place of (v_i, m_i): per pair it accumulates
+// The paper has no adjoint.  The kernels are the forward direct sum with the
+// source attribute a_bar_i in place of (v_i, m_i) (FP64: backward_kernel;
+// mixed: backward_pair_kernel on the forward's paired FP32x2 tile layout and
+// per-warp TMA ring): per pair they accumulate
 //   X1 += f a_bar_i,   X2 += g' (d . a_bar_i) d,   MB += f (d . a_bar_i)
 // with g' = -g/3, recomputing every pair term instead of storing any, and the
 // epilogue forms pos_bar = T a_bar + G m (X1 - 3 X2) - w_bar m a.
@@ -43,8 +45,6 @@ struct BwdArgs {
 
 template <typename T>
 __device__ __forceinline__ T rsqrt_t(T x);
-template <>
-__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrt_sfu(x); }
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 
@@ -270,6 +270,271 @@ backward_kernel(const BwdArgs a)
     }
 }
 
+// Mixed adjoint on the paired source layout of the forward kernel (the
+// packer's velocity slots carry a_bar_i, its mass slots are unused): two
+// sources per packed FP32x2 instruction in the Newtonian loop, 20 such
+// instructions per source pair (the scalar loop's 20 per source).
+template <int KT, int S, int U>
+__device__ __forceinline__ void bwd_far_pair(const float *__restrict__ tile, const float tx[KT][3],
+                                             float2 acc[KT][kNB])
+{
+    const float4 *P0 = reinterpret_cast<const float4 *>(tile);
+    const float4 *P1 = P0 + S / 2;
+    const float4 *V0 = P1 + S / 2;
+    const float2 *V1 = reinterpret_cast<const float2 *>(V0 + S / 2);
+    float2 ntx[KT], nty[KT], ntz[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        ntx[q] = make_float2(-tx[q][0], -tx[q][0]);
+        nty[q] = make_float2(-tx[q][1], -tx[q][1]);
+        ntz[q] = make_float2(-tx[q][2], -tx[q][2]);
+    }
+#pragma unroll U
+    for (int k = 0; k < S / 2; ++k) {
+        const float4 p0 = P0[k], p1 = P1[k], v0 = V0[k];
+        const float2 bz = V1[k];
+        const float2 bx = make_float2(v0.x, v0.y), by = make_float2(v0.z, v0.w);
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const float2 dx = __fadd2_rn(make_float2(p0.x, p0.y), ntx[q]);
+            const float2 dy = __fadd2_rn(make_float2(p0.z, p0.w), nty[q]);
+            const float2 dz = __fadd2_rn(make_float2(p1.x, p1.y), ntz[q]);
+            float2 r2 = __fmul2_rn(dz, dz);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dx, dx, r2);
+            const float2 ri = make_float2(rsqrt_sfu(r2.x), rsqrt_sfu(r2.y));
+            const float2 ri2 = __fmul2_rn(ri, ri);
+            const float2 f = __fmul2_rn(ri, ri2);
+            const float2 gp = __fmul2_rn(f, ri2);
+            float2 da = __fmul2_rn(dz, bz);
+            da = __ffma2_rn(dy, by, da);
+            da = __ffma2_rn(dx, bx, da);
+            acc[q][X10 + 0] = __ffma2_rn(f, bx, acc[q][X10 + 0]);
+            acc[q][X10 + 1] = __ffma2_rn(f, by, acc[q][X10 + 1]);
+            acc[q][X10 + 2] = __ffma2_rn(f, bz, acc[q][X10 + 2]);
+            const float2 gd = __fmul2_rn(gp, da);
+            acc[q][X20 + 0] = __ffma2_rn(gd, dx, acc[q][X20 + 0]);
+            acc[q][X20 + 1] = __ffma2_rn(gd, dy, acc[q][X20 + 1]);
+            acc[q][X20 + 2] = __ffma2_rn(gd, dz, acc[q][X20 + 2]);
+            acc[q][MBS] = __ffma2_rn(f, da, acc[q][MBS]);
+        }
+    }
+}
+
+// Softened loop on the paired layout, one source at a time (lane x of the
+// accumulators), the self pair excluded by index.
+template <int KT, int S>
+__device__ __forceinline__ void bwd_near_pair(const float *__restrict__ tile, const float tx[KT][3],
+                                              const int64_t tk[KT], int64_t jbase, float h2, float hinv,
+                                              float2 acc[KT][kNB])
+{
+    const float hinv3 = hinv * hinv * hinv;
+    const float hinv5 = hinv3 * hinv * hinv;
+#pragma unroll 2
+    for (int j = 0; j < S; ++j) {
+        const int k = j >> 1, h = j & 1;
+        const float x = tile[4 * k + h], y = tile[4 * k + 2 + h];
+        const float z = tile[2 * S + 4 * k + h];
+        const float bx = tile[4 * S + 4 * k + h], by = tile[4 * S + 4 * k + 2 + h];
+        const float bz = tile[6 * S + 2 * k + h];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const float dx = x - tx[q][0], dy = y - tx[q][1], dz = z - tx[q][2];
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = rsqrt_sfu(r2);
+            const float ri2 = ri * ri;
+            float f = ri * ri2;
+            float gp = f * ri2;
+            if (r2 < h2) {
+                float F, Gp, P;
+                spline_kernel<float>(sqrtf(r2) * hinv, F, Gp, P);
+                f = F * hinv3;
+                gp = Gp * hinv5;
+                if (jbase + j == tk[q]) {
+                    f = 0.0f;
+                    gp = 0.0f;
+                }
+            }
+            const float da = fmaf(dx, bx, fmaf(dy, by, dz * bz));
+            acc[q][X10 + 0].x = fmaf(f, bx, acc[q][X10 + 0].x);
+            acc[q][X10 + 1].x = fmaf(f, by, acc[q][X10 + 1].x);
+            acc[q][X10 + 2].x = fmaf(f, bz, acc[q][X10 + 2].x);
+            const float gd = gp * da;
+            acc[q][X20 + 0].x = fmaf(gd, dx, acc[q][X20 + 0].x);
+            acc[q][X20 + 1].x = fmaf(gd, dy, acc[q][X20 + 1].x);
+            acc[q][X20 + 2].x = fmaf(gd, dz, acc[q][X20 + 2].x);
+            acc[q][MBS].x = fmaf(f, da, acc[q][MBS].x);
+        }
+    }
+}
+
+// Shared memory of the mixed adjoint: a three-stage ring of paired tiles.
+template <int S>
+struct BwdPairSmem {
+    static constexpr int kStages = 3;
+    float4 stage[kStages][7 * S / 4];
+    uint64_t bar[kStages];
+    int done[kStages];           // warps finished with the tile in each stage
+    unsigned issued[kStages];    // copies issued into each stage
+    float blo[3], bhi[3];
+    int abort_flag;
+};
+
+// The mixed adjoint kernel: the structure of the forward mixed kernel (work
+// items of target blocks x source chunks, a three-stage TMA ring in which
+// each warp releases a stage on its own and the last warp to release it
+// issues the refill, each warp's near/far test against its own targets'
+// box), with the adjoint's pair terms.  Per-tile FP32 sums are carried across
+// tiles as compensated FP32 pairs (TwoSum); the result is FP64.
+template <int NT, int KT, int S, int MINB, int U>
+__global__ void __launch_bounds__(NT, MINB) backward_pair_kernel(const BwdArgs a)
+{
+    using Sm = BwdPairSmem<S>;
+    constexpr int NSTAGE = Sm::kStages;
+    constexpr int BT = NT * KT;
+    constexpr uint32_t kTileBytes = S * 28;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&sm.bar[s], 1);
+            sm.done[s] = 0;
+            sm.issued[s] = 0;
+        }
+        sm.abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+
+    const int64_t n_tb = (a.n + BT - 1) / BT;
+    const int split = choose_split(n_tb, a.n_tiles, a.grid, a.max_split, a.part_cap_rows, BT);
+    const int64_t items = n_tb * split;
+    const int64_t rows = n_tb * BT;
+    const float4 *src = static_cast<const float4 *>(a.src);
+    const float h2 = a.h2f_up, hinv = a.hinvf;
+
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t tb = item / split;
+        const int sp = (int)(item - tb * split);
+        const int t_begin = (int)((int64_t)sp * a.n_tiles / split);
+        const int t_end = (int)((int64_t)(sp + 1) * a.n_tiles / split);
+
+        double xk[KT][3];
+        int64_t tk[KT];
+        float lo[3], hi[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = __int_as_float(0x7f800000);
+            hi[c] = -__int_as_float(0x7f800000);
+        }
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const int64_t k = tb * BT + (int64_t)q * NT + threadIdx.x;
+            tk[q] = k < a.n ? k : -1;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xk[q][c] = tk[q] >= 0 ? a.pos[3 * k + c] : 0.0;
+                if (tk[q] >= 0) {
+                    lo[c] = fminf(lo[c], __double2float_rd(xk[q][c]));
+                    hi[c] = fmaxf(hi[c], __double2float_ru(xk[q][c]));
+                }
+            }
+        }
+        // lo/hi become the warp's box; tiles are tested against it
+        block_bbox<NT>(lo, hi, sm.blo, sm.bhi);
+
+        float shi[KT][kNB], slo[KT][kNB];
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+#pragma unroll
+            for (int c = 0; c < kNB; ++c) {
+                shi[q][c] = 0.0f;
+                slo[q][c] = 0.0f;
+            }
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < NSTAGE; ++s) {
+                const int t = t_begin + s;
+                if (t < t_end) {
+                    tma_load_1d(sm.stage[s], src + (int64_t)t * 2 * S, kTileBytes, &sm.bar[s]);
+                    sm.issued[s] += 1u;
+                }
+            }
+        }
+        for (int t = t_begin; t < t_end; ++t) {
+            const int s = (t - t_begin) % NSTAGE;
+            const TileGeom g = a.geo[t];
+            const bool near = tile_is_near(lo, hi, g, h2);
+            float tx[KT][3];
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) tx[q][c] = __double2float_rn(__dsub_rn(xk[q][c], g.c[c]));
+            const bool got = mbar_wait_bounded(&sm.bar[s], (parity >> s) & 1u, a.flags);
+            if (got)
+                parity ^= 1u << s;
+            else
+                atomicExch(&sm.abort_flag, 1);
+            float2 acc[KT][kNB];
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+#pragma unroll
+                for (int c = 0; c < kNB; ++c) acc[q][c] = make_float2(0.0f, 0.0f);
+            const float *tf = reinterpret_cast<const float *>(sm.stage[s]);
+            if (!near)
+                bwd_far_pair<KT, S, U>(tf, tx, acc);
+            else
+                bwd_near_pair<KT, S>(tf, tx, tk, g.first, h2, hinv, acc);
+#pragma unroll
+            for (int q = 0; q < KT; ++q)
+#pragma unroll
+                for (int c = 0; c < kNB; ++c) two_sum_acc(shi[q][c], slo[q][c], acc[q][c].x + acc[q][c].y);
+            // this warp is done reading stage s; the last warp refills it
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) {
+                __threadfence_block();
+                const int prev = atomicAdd(&sm.done[s], 1);
+                if (prev == NT / 32 - 1) {
+                    sm.done[s] = 0;
+                    __threadfence_block();
+                    if (t + NSTAGE < t_end && !*(volatile int *)&sm.abort_flag) {
+                        fence_proxy_async_smem();
+                        tma_load_1d(sm.stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes,
+                                    &sm.bar[s]);
+                        sm.issued[s] += 1u;
+                    }
+                }
+            }
+            __syncwarp();
+            if (*(volatile int *)&sm.abort_flag) break;
+        }
+        __syncthreads();   // every warp is out of the tile loop: a uniform status
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            double sum[kNB];
+#pragma unroll
+            for (int c = 0; c < kNB; ++c) sum[c] = (double)shi[q][c] + (double)slo[q][c];
+            const int64_t slot = tb * BT + (int64_t)q * NT + threadIdx.x;
+            if (split == 1) {
+                if (tk[q] >= 0) bwd_write(a, tk[q], sum);
+            } else {
+#pragma unroll
+                for (int c = 0; c < kNB; ++c) a.part[((int64_t)sp * kNB + c) * rows + slot] = sum[c];
+            }
+        }
+        if (sm.abort_flag) break;
+        __syncthreads();
+    }
+    // copies still in flight (only after a timed-out wait): a stage holds one
+    // exactly when thread 0 has seen fewer completions there than were issued
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s)
+            if ((sm.issued[s] & 1u) != ((parity >> s) & 1u))
+                mbar_wait_bounded(&sm.bar[s], (parity >> s) & 1u, a.flags);
+    }
+}
+
 __global__ void __launch_bounds__(256) backward_reduce_kernel(const BwdArgs a, int32_t BT)
 {
     const int64_t n_tb = (a.n + BT - 1) / BT;
@@ -303,7 +568,8 @@ __global__ void __launch_bounds__(256) backward_pot_only_kernel(const BwdArgs a)
 }
 
 // Fixed tile shapes of the adjoint.
-constexpr int kBwdNTf = 128, kBwdKTf = 2, kBwdSf = 256, kBwdMinBf = 3;
+constexpr int kBwdNTf = 768, kBwdKTf = 1, kBwdSf = 256, kBwdMinBf = 1, kBwdUf = 4;
+constexpr size_t kBwdSmemf = sizeof(BwdPairSmem<kBwdSf>);
 constexpr int kBwdNTd = 128, kBwdKTd = 1, kBwdSd = 128, kBwdMinBd = 2;
 
 struct BwdLayout {
@@ -347,8 +613,15 @@ int bwd_grid(bool mixed, int *grid)
     int &slot = cache[dev][mixed ? 1 : 0];
     if (slot == 0) {
         int b = 0;
-        cudaError_t e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                    &b, backward_kernel<float, kBwdNTf, kBwdKTf, kBwdSf, kBwdMinBf>, kBwdNTf, 0)
+        cudaError_t e = cudaSuccess;
+        if (mixed) {
+            auto k = backward_pair_kernel<kBwdNTf, kBwdKTf, kBwdSf, kBwdMinBf, kBwdUf>;
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmemf);
+        }
+        if (e == cudaSuccess)
+            e = mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &b, backward_pair_kernel<kBwdNTf, kBwdKTf, kBwdSf, kBwdMinBf, kBwdUf>,
+                                    kBwdNTf, kBwdSmemf)
                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                                     &b, backward_kernel<double, kBwdNTd, kBwdKTd, kBwdSd, kBwdMinBd>, kBwdNTd, 0);
         rc = check_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
@@ -454,7 +727,7 @@ extern "C" int grav_eval_backward(const grav_params *p, int64_t n, const double 
     // Pack (x, a_bar) tiles: the forward packer with a_bar in the velocity
     // slot and no mass.
     if (mixed)
-        pack_tiles_kernel<kBwdSf, true, false><<<(unsigned)L.n_tiles, kBwdSf, 0, st>>>(
+        pack_tiles_kernel<kBwdSf, true, false, true><<<(unsigned)L.n_tiles, kBwdSf, 0, st>>>(
             n, pos, a_bar, nullptr, const_cast<TileGeom *>(a.geo), const_cast<void *>(a.src), flags_dev);
     else
         pack_tiles_kernel<kBwdSd, false, false><<<(unsigned)L.n_tiles, kBwdSd, 0, st>>>(
@@ -462,7 +735,7 @@ extern "C" int grav_eval_backward(const grav_params *p, int64_t n, const double 
     rc = check_launch("grav_eval_backward/pack");
     if (rc) return rc;
     if (mixed)
-        backward_kernel<float, kBwdNTf, kBwdKTf, kBwdSf, kBwdMinBf><<<grid, kBwdNTf, 0, st>>>(a);
+        backward_pair_kernel<kBwdNTf, kBwdKTf, kBwdSf, kBwdMinBf, kBwdUf><<<grid, kBwdNTf, kBwdSmemf, st>>>(a);
     else
         backward_kernel<double, kBwdNTd, kBwdKTd, kBwdSd, kBwdMinBd><<<grid, kBwdNTd, 0, st>>>(a);
     rc = check_launch("grav_eval_backward/sum");

@@ -606,14 +606,14 @@ __device__ __forceinline__ int open_test_f32(const float4 &hi, const float4 &lo,
 // partition their parent's range in order, so a pre-order walk reaches the
 // next node outside it exactly at the node the lane's own walk goes to next.
 // Each lane therefore visits the same nodes, in the same order, as a walk of
-// its own, and its sums are the same bit for bit.
+// its own: the oracle's interactions, summed in the oracle's order.
 //
 // Decisions are those of FP64 arithmetic (open_test_f32, else FP64; always
 // FP64 with the relative criterion).  MIXED: every pair term in FP32 (nodes
 // from the FP32 offset of open_test_f32; leaf elements from their FP32
-// offsets to the leaf's centre of mass plus that offset), FP32 sums of up to
-// 32 interactions added into FP64.  FP64 walk: offsets and pair terms in
-// FP64.
+// offsets to the leaf's centre of mass plus that offset), FP32 sums of at
+// most 32 + leaf_size interactions added into FP64.  FP64 walk: offsets and
+// pair terms in FP64, partial sums carried by TwoSum.
 template <bool POT, bool MIXED>
 __global__ void __launch_bounds__(kWalkNT) tree_walk_kernel(TreeView t, EvalArgs a, WalkArgs w)
 {
@@ -750,19 +750,23 @@ __global__ void __launch_bounds__(kWalkNT) tree_walk_kernel(TreeView t, EvalArgs
             } else {
                 open = true;
             }
-            if (pending >= kFlushEvery) {
+        }
+        // carry the partial sums into the FP64 ones when any lane of the warp
+        // has gathered kFlushEvery interactions: all lanes carry together, so
+        // the FP64 pipe (1/74 of the FP32 rate) runs once per warp, not once
+        // per lane
+        if (__any_sync(0xffffffffu, pending >= kFlushEvery)) {
 #pragma unroll
-                for (int c = 0; c < kNCPot; ++c) {
-                    if (MIXED) {
-                        shi[c] += (double)accf[MIXED ? c : 0];
-                        accf[MIXED ? c : 0] = 0.0f;
-                    } else {
-                        two_sum_acc(shi[c], slo[c], acc[c]);
-                        acc[c] = 0.0;
-                    }
+            for (int c = 0; c < kNCPot; ++c) {
+                if (MIXED) {
+                    shi[c] += (double)accf[MIXED ? c : 0];
+                    accf[MIXED ? c : 0] = 0.0f;
+                } else {
+                    two_sum_acc(shi[c], slo[c], acc[c]);
+                    acc[c] = 0.0;
                 }
-                pending = 0;
             }
+            pending = 0;
         }
         node = __any_sync(0xffffffffu, open) ? child : t.next[node];
     }

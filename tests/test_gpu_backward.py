@@ -34,13 +34,17 @@ def test_backward_vs_oracle(n, precision):
     pb_o, mb_o = O.backward(pos, mass, a_bar, 1.0, ref["acc"], ref["tidal"], ref["pot"], h=h)
     pb, mb = gpu_backward(pos, mass, a_bar, 1.0, ref["acc"], ref["tidal"], ref["pot"], h, precision)
     tol = 1e-11 if precision == grav.F64 else 1e-4
-    # error relative to each element's gradient scale
+    # error relative to each element's gradient scale; the mass gradient is
+    # the sum of two terms, -G sum f (d . a_bar) and w_bar Phi, which can
+    # nearly cancel (by 600x for one element here), so its error is taken
+    # relative to the sum of their magnitudes
+    _, mb_sums = O.backward(pos, mass, a_bar, 0.0, ref["acc"], ref["tidal"], ref["pot"], h=h)
     scale_p = np.linalg.norm(pb_o, axis=1) + 1e-300
-    scale_m = np.abs(mb_o) + 1e-300
+    scale_m = np.abs(mb_sums) + np.abs(1.0 * ref["pot"]) + 1e-300
     ep = np.linalg.norm(pb - pb_o, axis=1) / scale_p
     em = np.abs(mb - mb_o) / scale_m
     assert np.max(ep) <= tol, float(np.max(ep))
-    assert np.median(em) <= tol and np.max(em) <= 10 * tol, (float(np.median(em)), float(np.max(em)))
+    assert np.max(em) <= tol, (float(np.median(em)), float(np.max(em)))
 
 
 @pytest.mark.parametrize("precision", [grav.F64, grav.MIXED])
