@@ -2,10 +2,11 @@
 //
 // Direct summation, target-blocked: a CTA owns a block of BT = NT*KT targets
 // (KT per thread) and streams source tiles of S elements through shared
-// memory with 1-D TMA bulk copies (cp.async.bulk + mbarrier, a ring of two or
-// three stages; in the open-boundary mixed kernels each warp releases a stage
-// on its own and the last warp to release it issues the refill, so no block
-// barrier separates the tiles).  Every thread evaluates each staged source
+// memory with 1-D TMA bulk copies (cp.async.bulk + mbarrier).  Mixed kernels:
+// a ring of three stages, each released by every warp on its own and refilled
+// by the last warp to release it, so no block barrier separates the tiles and
+// each warp tests tiles against its own targets' box; FP64 kernels: two
+// stages and a block barrier after every tile.  Every thread evaluates each staged source
 // against its KT targets with the SFU reciprocal square root; all lanes read
 // the same source (shared-memory broadcast).  This is CUDA-core work, not a
 // contraction: no tensor cores.
@@ -1123,7 +1124,10 @@ pack_tiles_batched_kernel(const BatchView b, const double *__restrict__ pos,
 // thread); otherwise in registers.
 // ---------------------------------------------------------------------------
 
-template <int NT, int KT, int S, bool POT, bool SACC, bool PAIR = false, int NST = 2>
+// The mixed kernels' tile loops synchronise nothing across warps, so each
+// warp releases a stage of the source ring on its own (no block barrier per
+// tile) and a third stage lets warps drift apart by up to two tiles.
+template <int NT, int KT, int S, bool POT, bool SACC, bool PAIR = false, int NST = 3>
 struct MixedSmem {
     static constexpr int BT = NT * KT;
     static constexpr int NC = POT ? kNCPot : kNC;
@@ -1139,11 +1143,6 @@ struct MixedSmem {
     long long ticket;
 };
 
-// Stages of the mixed kernels' source ring: open-boundary kernels release a
-// stage per warp (no block barrier per tile), so they keep one more stage in
-// flight to let warps drift apart by up to two tiles.
-template <int MODE>
-constexpr int mixed_stages() { return MODE == kModeOpen ? 3 : 2; }
 
 template <typename Sm>
 __device__ __forceinline__ void init_mixed_ring(Sm &sm)
@@ -1176,13 +1175,9 @@ __device__ __forceinline__ void init_ring(Sm &sm)
 // stage s exactly when thread 0 has seen fewer completions there than were
 // issued (at most one: a refill needs every warp, thread 0's included, to
 // have consumed the previous copy).
-template <int MODE, typename Sm>
+template <typename Sm>
 __device__ __forceinline__ void drain_mixed_ring(Sm &sm, const Ring &ring, int32_t *flags)
 {
-    if (MODE != kModeOpen) {
-        drain_ring<Sm::kStages>(sm.bar, ring, flags);
-        return;
-    }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int s = 0; s < Sm::kStages; ++s)
@@ -1194,15 +1189,12 @@ __device__ __forceinline__ void drain_mixed_ring(Sm &sm, const Ring &ring, int32
 // One work item of the mixed kernel; false if a bounded wait gave up.
 template <int NT, int KT, int S, int U, bool POT, bool SACC, bool PAIR, int MODE>
 __device__ __forceinline__ bool mixed_item(
-    const EvalArgs &a, MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()> &sm, Ring &ring,
+    const EvalArgs &a, MixedSmem<NT, KT, S, POT, SACC, PAIR> &sm, Ring &ring,
     const ItemSpec &it)
 {
-    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>;
+    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR>;
     constexpr int BT = Sm::BT;
     constexpr int NSTAGE = Sm::kStages;
-    // open boundaries: each warp releases a stage when it is done with it and
-    // the last warp to do so refills it (no block barrier per tile)
-    constexpr bool kWarpRelease = MODE == kModeOpen;
     constexpr int NC = Sm::NC;
     constexpr bool soft = MODE == kModeSoft;
     constexpr uint32_t kTileBytes = PAIR ? S * 28 : S * 2 * sizeof(float4);
@@ -1240,19 +1232,16 @@ __device__ __forceinline__ bool mixed_item(
         }
     }
     block_bbox<NT>(lo, hi, sm.blo, sm.bhi);     // (its barriers also publish sm.x)
-    // the near/far test of a tile: with per-warp release each warp takes it
-    // against its own targets' box (lo/hi now hold it), which culls far more
-    // tiles when the targets are sparse; otherwise against the block's box
-    const float blo_r[3] = {kWarpRelease ? lo[0] : sm.blo[0], kWarpRelease ? lo[1] : sm.blo[1],
-                            kWarpRelease ? lo[2] : sm.blo[2]};
-    const float bhi_r[3] = {kWarpRelease ? hi[0] : sm.bhi[0], kWarpRelease ? hi[1] : sm.bhi[1],
-                            kWarpRelease ? hi[2] : sm.bhi[2]};
+    // each warp takes the near/far test of a tile against its own targets'
+    // box (lo/hi now hold it): far more tiles are culled than with the
+    // block's box when the targets are sparse
+    const float blo_r[3] = {lo[0], lo[1], lo[2]};
+    const float bhi_r[3] = {hi[0], hi[1], hi[2]};
 
-    // adaptive softening: the targets' 1/h_i and zeta_i, the block's largest
-    // support, and the shared copy of a near tile's (1/h_j, zeta_j)
+    // adaptive softening: the targets' 1/h_i and zeta_i, the warp's largest
+    // support
     float thinv[soft ? KT : 1], tzeta[soft ? KT : 1];
     float h_block = 0.0f;
-    __shared__ float2 soft_hz[soft ? S : 1];
     if (soft) {
         float hb = 0.0f;
 #pragma unroll
@@ -1266,7 +1255,9 @@ __device__ __forceinline__ bool mixed_item(
                 hb = fmaxf(hb, __double2float_ru(h));
             }
         }
-        h_block = block_max<NT>(hb);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) hb = fmaxf(hb, __shfl_xor_sync(0xffffffffu, hb, o));
+        h_block = hb;
     }
 
     float rhi[SACC ? 1 : KT][SACC ? 1 : kNCPot], rlo[SACC ? 1 : KT][SACC ? 1 : kNCPot];
@@ -1290,8 +1281,7 @@ __device__ __forceinline__ bool mixed_item(
             int t = t_begin + s;
             if (t < t_end) {
                 tma_load_1d(sm.stage[s], src + (int64_t)t * 2 * S, kTileBytes, &sm.bar[s]);
-                ring.pending |= 1u << s;
-                if (kWarpRelease) sm.issued[s] += 1u;
+                sm.issued[s] += 1u;
             }
         }
     }
@@ -1323,8 +1313,9 @@ __device__ __forceinline__ bool mixed_item(
             const float hm = fmaxf(h_block, a.geo_h[t]);
             h2_tile = __fmul_ru(hm, hm);
         }
+        // (periodic: taken for the warp's targets)
         const bool near = periodic
-            ? (__syncthreads_or(periodic_special<KT>(tx, ti, g, a.h2f_up, a.box_tie_f)) != 0)
+            ? __any_sync(0xffffffffu, periodic_special<KT>(tx, ti, g, a.h2f_up, a.box_tie_f))
             : tile_is_near(blo_r, bhi_r, g, h2_tile);
         // next tile's geometry and offsets, computed ahead (FP64 latency)
         TileGeom gn = g;
@@ -1344,10 +1335,10 @@ __device__ __forceinline__ bool mixed_item(
 #pragma unroll
             for (int c = 0; c < kNCPot; ++c) acc[q][c] = 0.0f;
         if (soft && near) {
-            // the previous tile's reads of soft_hz ended at its closing barrier
-            for (int k = threadIdx.x; k < S; k += NT) soft_hz[k] = a.hz[(int64_t)t * S + k];
-            __syncthreads();
-            soft_loop_f<KT, S, POT, PAIR>(sm.stage[s], soft_hz, tx, ti, g.first, thinv, tzeta, acc);
+            // the tile's (1/h_j, zeta_j) straight from global memory (every
+            // lane reads the same source: one cached load per warp)
+            soft_loop_f<KT, S, POT, PAIR>(sm.stage[s], a.hz + (int64_t)t * S, tx, ti, g.first, thinv,
+                                          tzeta, acc);
         } else if (periodic && near) {
             periodic_loop_f<KT, S, POT, PAIR>(sm.stage[s], tx, ti, g.first, a.h2f_up, a.hinvf, a,
                                               acc);
@@ -1405,37 +1396,24 @@ __device__ __forceinline__ bool mixed_item(
             }
         }
 
-        if (kWarpRelease) {
-            // this warp is done reading stage s; the last warp refills it
-            __syncwarp();
-            if ((threadIdx.x & 31) == 0) {
+        // this warp is done reading stage s; the last warp refills it
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) {
+            __threadfence_block();
+            const int prev = atomicAdd(&sm.done[s], 1);
+            if (prev == NT / 32 - 1) {
+                sm.done[s] = 0;
                 __threadfence_block();
-                const int prev = atomicAdd(&sm.done[s], 1);
-                if (prev == NT / 32 - 1) {
-                    sm.done[s] = 0;
-                    __threadfence_block();
-                    if (t + NSTAGE < t_end && !*(volatile int *)&sm.abort_flag) {
-                        fence_proxy_async_smem();
-                        tma_load_1d(sm.stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes,
-                                    &sm.bar[s]);
-                        sm.issued[s] += 1u;
-                    }
-                }
-            }
-            __syncwarp();
-            if (*(volatile int *)&sm.abort_flag) break;
-        } else {
-            __syncthreads();                       // all reads of stage s are done
-            if (threadIdx.x == 0) {
-                if (got) ring.pending &= ~(1u << s);
-                if (t + NSTAGE < t_end && !sm.abort_flag) {
+                if (t + NSTAGE < t_end && !*(volatile int *)&sm.abort_flag) {
+                    fence_proxy_async_smem();
                     tma_load_1d(sm.stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes,
                                 &sm.bar[s]);
-                    ring.pending |= 1u << s;
+                    sm.issued[s] += 1u;
                 }
             }
-            if (sm.abort_flag) break;
         }
+        __syncwarp();
+        if (*(volatile int *)&sm.abort_flag) break;
         g = gn;
 #pragma unroll
         for (int q = 0; q < KT; ++q)
@@ -1445,7 +1423,7 @@ __device__ __forceinline__ bool mixed_item(
 
     // warps may leave the tile loop at different tiles: meet here so that
     // every thread returns the same status
-    if (kWarpRelease) __syncthreads();
+    __syncthreads();
 
     // ---- results ----
 #pragma unroll
@@ -1476,7 +1454,7 @@ template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR
 __global__ void __launch_bounds__(NT, MINB)
 eval_mixed_kernel(const EvalArgs a)
 {
-    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>;
+    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR>;
     constexpr int BT = Sm::BT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
@@ -1503,7 +1481,7 @@ eval_mixed_kernel(const EvalArgs a)
         if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }
-    drain_mixed_ring<MODE>(sm, ring, a.flags);
+    drain_mixed_ring(sm, ring, a.flags);
 }
 
 // Batched: items of all systems from the plan, taken through an atomic
@@ -1514,7 +1492,7 @@ template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR
 __global__ void __launch_bounds__(NT, MINB)
 eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
 {
-    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>;
+    using Sm = MixedSmem<NT, KT, S, POT, SACC, PAIR>;
     constexpr int BT = Sm::BT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
@@ -1543,7 +1521,7 @@ eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
         if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }
-    drain_mixed_ring<MODE>(sm, ring, a.flags);
+    drain_mixed_ring(sm, ring, a.flags);
 }
 
 // ---------------------------------------------------------------------------
@@ -1817,14 +1795,14 @@ struct EvalConfig {
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 void launch_mixed(const EvalArgs &a, int grid, cudaStream_t st)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
     eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE><<<grid, NT, bytes, st>>>(a);
 }
 
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 int occupancy_mixed(int *b)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
     auto k = eval_mixed_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
@@ -1834,14 +1812,14 @@ int occupancy_mixed(int *b)
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 void launch_mixed_batched(const EvalArgs &a, const BatchView &b, int grid, cudaStream_t st)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
     eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE><<<grid, NT, bytes, st>>>(a, b);
 }
 
 template <int NT, int KT, int S, int MINB, int U, bool POT, bool SACC, bool PAIR, int MODE>
 int occupancy_mixed_batched(int *b)
 {
-    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR, mixed_stages<MODE>()>);
+    constexpr size_t bytes = sizeof(MixedSmem<NT, KT, S, POT, SACC, PAIR>);
     auto k = eval_mixed_batched_kernel<NT, KT, S, MINB, U, POT, SACC, PAIR, MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;

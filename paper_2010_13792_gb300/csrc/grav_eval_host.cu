@@ -10,14 +10,16 @@
 namespace grav {
 namespace {
 
-// Default tile configurations: 768-thread CTAs with per-warp stage release
-// and per-warp tile culling for open-boundary evaluations of at least 8192
-// targets (measured fastest from 1% to 100% of 2^20 targets); 256-thread CTAs
-// (three per SM) for the periodic box, adaptive softening, batched launches
-// and small target sets, where more CTAs per SM keep the SMs busier.
+// Default tile configurations (measured on 2^20-element clouds and 64^3 and
+// 96^3 periodic lattices): 768-thread CTAs, one per SM, for open boundaries
+// and adaptive softening from 8192 targets and for the periodic box from
+// 2^19 targets; 256-thread CTAs (three per SM) for smaller sets and batched
+// launches, where more CTAs per SM keep the SMs busier through the last
+// round of work items.
 constexpr int kDefaultMixed = 11;
 constexpr int kDefaultMixedLarge = 17;
 constexpr int64_t kLargeTargetSet = 1 << 13;
+constexpr int64_t kLargePeriodicSet = 1 << 19;
 constexpr int kDefaultF64 = 0;
 constexpr int64_t kSplitRowsPerSM = 16;   // partial capacity, in target blocks per SM
 
@@ -51,7 +53,8 @@ int check_params(const grav_params *p, const char *who)
 int default_index(int32_t precision, int mode, int64_t n_targets)
 {
     if (precision != GRAV_MIXED) return kDefaultF64;
-    return mode == kModeOpen && n_targets >= kLargeTargetSet ? kDefaultMixedLarge : kDefaultMixed;
+    const int64_t large = mode == kModePeriodic ? kLargePeriodicSet : kLargeTargetSet;
+    return n_targets >= large ? kDefaultMixedLarge : kDefaultMixed;
 }
 
 // The configuration of an evaluation: p->tile_config, or the default for its

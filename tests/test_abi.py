@@ -144,3 +144,29 @@ def test_python_binding_rejects_cpu_tensors():
     with pytest.raises(grav.GravError):
         grav.select_due(0, 2, x, torch.zeros(4, dtype=torch.int64), torch.zeros(4, dtype=torch.float64),
                         0.5, 1.0, torch.zeros(4, dtype=torch.uint8), torch.zeros(4, dtype=torch.uint8))
+
+
+def test_default_tile_config_choice(libgrav):
+    """The configuration tile_config = -1 selects: 768-thread CTAs from 8192
+    targets (2^19 in a periodic box), 256-thread CTAs below; one FP64 default;
+    bad arguments rejected.  Host logic only."""
+    from paper_2010_13792_gb300 import grav
+    L = grav.lib()
+    big = grav.tile_configs(grav.MIXED)[grav.default_tile_config(grav.MIXED, 1 << 20)]
+    small = grav.tile_configs(grav.MIXED)[grav.default_tile_config(grav.MIXED, 100)]
+    assert big["threads"] == 768 and small["threads"] == 256
+    assert grav.default_tile_config(grav.MIXED, 8192) == grav.default_tile_config(grav.MIXED, 1 << 20)
+    assert grav.default_tile_config(grav.MIXED, 8191) == grav.default_tile_config(grav.MIXED, 100)
+    assert grav.default_tile_config(grav.MIXED, 1 << 18, periodic=True) == \
+        grav.default_tile_config(grav.MIXED, 100)
+    assert grav.default_tile_config(grav.MIXED, 1 << 19, periodic=True) == \
+        grav.default_tile_config(grav.MIXED, 1 << 20)
+    assert grav.default_tile_config(grav.MIXED, 1 << 20, soft=True) == \
+        grav.default_tile_config(grav.MIXED, 1 << 20)
+    assert grav.default_tile_config(grav.F64, 1 << 20) == grav.default_tile_config(grav.F64, 1)
+    assert L.grav_default_tile_config(7, 0, 0, 10) == grav.GRAV_EINVAL
+    assert L.grav_default_tile_config(grav.MIXED, 0, 0, -1) == grav.GRAV_EINVAL
+    # index -1 of grav_tile_config describes the small-set default
+    ti = grav.TileInfo()
+    assert L.grav_tile_config(grav.MIXED, -1, ctypes.byref(ti)) == grav.GRAV_OK
+    assert ti.threads == small["threads"]
