@@ -5,7 +5,9 @@ maximum relative error per target of a, j, T and Phi (|d|/|ref|,
 ||dT||_F/||T||_F) and of the adjoint gradients.  Workloads: the uniform
 sphere N = 4096 (all targets), the Plummer sphere N = 2^17 (all active,
 sampled targets), the turbulent cloud N = 2^20 at 1%, 10% and 100% active
-(sampled targets) and the Plummer N = 2^16 adjoint (sampled rows).
+(sampled targets), the oct-tree on the cloud against the oracle's tree
+(sampled targets), the periodic box on a 48^3 lattice (sampled targets) and
+the Plummer N = 2^16 adjoint (sampled rows).
 
     python tests/accuracy_report.py > accuracy.json
 """
@@ -60,6 +62,24 @@ def main():
         if frac == 0.01:
             out = run_eval(pos, vel, mass, idx, h=2e-3, precision=grav.F64)
             rep[f"cloud_N1048576_active{frac}_f64_384_sampled"] = stats(errors(out, ref, rows))
+
+    # oct-tree (Theta = 0.5, leaves of 8) against the oracle's tree walk
+    from test_gpu_periodic import run_periodic
+    from test_gpu_tree import gpu_tree
+    pos, vel, mass = ics.turbulent_cloud(1 << 20, seed=ics.BASE_SEED + 2)
+    rows = sample(np.arange(mass.size), 128, 4)
+    ref = O.tree_eval(pos, vel, mass, rows, h=2e-3, theta=0.5, leaf_size=8)
+    for name, prec in (("f64", grav.F64), ("mixed", grav.MIXED)):
+        out = gpu_tree(pos, vel, mass, h=2e-3, theta=0.5, leaf=8, precision=prec)
+        rep[f"tree_cloud_N1048576_{name}_128_sampled"] = stats(errors(out, ref, rows))
+
+    # periodic box (nearest image), 48^3 Zeldovich-shaped lattice, all targets
+    pos, vel, mass = ics.zeldovich_box(48, 1.0, amplitude=0.8)
+    rows = sample(np.arange(mass.size), 256, 5)
+    ref = O.eval_active(pos, vel, mass, rows, h=2e-3, box=1.0)
+    for name, prec in (("f64", grav.F64), ("mixed", grav.MIXED)):
+        out = run_periodic(pos, vel, mass, None, 2e-3, 1.0, prec)
+        rep[f"periodic_lattice_48cubed_{name}_256_sampled"] = stats(errors(out, ref, rows))
 
     from paper_2010_13792_gb300.autograd import gravity
     pos, vel, mass = ics.plummer(1 << 16, seed=ics.BASE_SEED + 3)

@@ -103,8 +103,12 @@ def test_compact_unaligned_and_empty():
     assert int(cnt_t.item()) == 0
 
 
-@pytest.mark.parametrize("n", [1, 1000, (1 << 20) + 1])
-def test_predict_bitexact(n):
+@pytest.mark.parametrize("row_offset", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 1000, (1 << 20) + 1])
+def test_predict_bitexact(n, row_offset):
+    """Both kernels: 16-byte-aligned [n][3] arrays (pairs of doubles per
+    thread, odd and even 3n) and views starting one row (24 bytes) into a
+    buffer (one double per thread)."""
     g = ics.rng(400 + n)
     active = (g.uniform(size=n) < 0.7).astype(np.uint8)
     due = ((g.uniform(size=n) < 0.3) & (active == 1)).astype(np.uint8)
@@ -114,8 +118,12 @@ def test_predict_bitexact(n):
     dt_min = 2.0**-13 * 3.0
     init = g.normal(size=(n, 3))
     want = O.predict(active, due, a_last, j_last, tf, dt_min, init)
-    out = T(init)
-    grav.predict(T(active, torch.uint8), T(due, torch.uint8), T(a_last), T(j_last),
+
+    def rows(x):      # a contiguous view row_offset rows into a larger buffer
+        buf = T(np.concatenate([np.zeros((row_offset, 3)), x]))
+        return buf[row_offset:]
+    out = rows(init)
+    grav.predict(T(active, torch.uint8), T(due, torch.uint8), rows(a_last), rows(j_last),
                  T(tf, torch.int64), dt_min, out)
     torch.cuda.synchronize()
     got = out.cpu().numpy()
