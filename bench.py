@@ -389,6 +389,7 @@ def extras(args, path, dev, sms, peak32, flush):
     out["adaptive_softening_N1048576"] = soft_extra(path, dev, flush)
     out["tree_N1048576"] = tree_extra(path, dev, flush)
     out["adjoint"] = backward_extra(path, dev, flush)
+    out["other_workloads_mixed_all_active"] = workloads_extra(dev, flush, sms, peak32)
     out["batched_256_systems"] = batched_extra(dev, flush)
     out["adaptive_plummer_131072"] = adaptive_extra(dev)
     try:
@@ -554,6 +555,42 @@ def tree_extra(path, dev, flush):
         res[name] = {"ms": 1e3 * t, "interactions_per_s": inter / t,
                      "acc_rel_error_vs_direct": {"median": float(q[0]), "p99": float(q[1]),
                                                  "max": float(e.max())}}
+    return res
+
+
+def workloads_extra(dev, flush, sms, peak32):
+    """The mixed force evaluation, every element a target, on the other
+    synthetic inputs shaped like the paper's tests: the Plummer sphere of
+    2^17 (h = 1e-3, centrally concentrated: many softened tiles near the
+    centre) and a uniform sphere of 2^20 (h = 0.01)."""
+    import torch
+
+    from paper_2010_13792_gb300 import grav, ics
+    res = {}
+    for name, (pos, vel, mass), h in (
+            ("plummer_N131072_h1e-3", ics.plummer(1 << 17, seed=ics.BASE_SEED + 1), 1e-3),
+            ("uniform_sphere_N1048576_h1e-2", ics.uniform_sphere(1 << 20, seed=ics.BASE_SEED), 1e-2)):
+        n = mass.size
+        f64 = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
+        P, V, M = f64(pos), f64(vel), f64(mass)
+        acc = torch.empty(n, 3, dtype=torch.float64, device=dev)
+        jerk, tid = torch.empty_like(acc), torch.empty(n, 6, dtype=torch.float64, device=dev)
+        p = grav.params(h=h, precision=grav.MIXED)
+        ws = grav.Workspace()
+        grav.eval_active(p, P, V, M, None, None, n, acc, jerk, tid, workspace=ws)
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            grav.eval_active(p, P, V, M, None, None, n, acc, jerk, tid, workspace=ws)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) * 1e-3)
+        t = statistics.median(ts)
+        ips = n * n / t
+        res[name] = {"ms": 1e3 * t, "interactions_per_s": ips,
+                     "frac_of_fp32_peak": FLOPS_PER_INTERACTION * ips / 1e12 / peak32}
     return res
 
 
