@@ -1733,35 +1733,52 @@ eval_f64_batched_kernel(const EvalArgs a, const BatchView b)
 // K9: deterministic reduction of the chunk partials (fixed chunk order)
 // ---------------------------------------------------------------------------
 
+// Threads of the split reduction: one per (target, accumulated component),
+// so that a small target set (the usual case of a split) still spreads its
+// FP64 work -- `split` TwoSums per component, at 1/74 of the FP32 rate on
+// GB300 -- over many warps instead of queueing it on a few.
+constexpr int kReduceThreads = 256;
+template <bool POT>
+constexpr int reduce_targets_per_block() { return kReduceThreads / (POT ? kNCPot : kNC); }
+
 template <bool POT, bool ETRACE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kReduceThreads)
 reduce_partials_kernel(const EvalArgs a, int32_t BT)
 {
     constexpr int NC = POT ? kNCPot : kNC;
+    constexpr int TPB = reduce_targets_per_block<POT>();
+    __shared__ double red[NC][TPB];
     const int64_t n_act = active_count(a);
     const int64_t n_tb = (n_act + BT - 1) / BT;
     const int split = choose_split(n_tb, a.n_tiles, a.grid, a.max_split, a.part_cap_rows, BT);
     if (split <= 1) return;
     const int64_t rows = n_tb * BT;
-    const int64_t slot = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (slot >= n_act) return;
-    int64_t i = a.idx ? (int64_t)a.idx[slot] : slot;
-    if (i < 0 || i >= a.n_src) return;
-    double hi[kNCPot], lo[kNCPot];
+    const int k = threadIdx.x % TPB, c = threadIdx.x / TPB;
+    // a bounded grid strides over groups of TPB targets (the count is known
+    // on the device only, so the host sizes the grid for the upper bound)
+    for (int64_t slot0 = (int64_t)blockIdx.x * TPB; slot0 < n_act;
+         slot0 += (int64_t)gridDim.x * TPB) {
+        const int64_t slot = slot0 + k;
+        if (c < NC && slot < n_act) {
+            // the chunk partials of component c of this target, in split order
+            double hi = 0.0, lo = 0.0;
+            for (int sp = 0; sp < split; ++sp)
+                two_sum_acc(hi, lo, a.part[((int64_t)sp * NC + c) * rows + slot]);
+            red[c][k] = __dadd_rn(hi, lo);
+        }
+        __syncthreads();
+        if (threadIdx.x < TPB && slot0 + threadIdx.x < n_act) {
+            const int64_t sl = slot0 + threadIdx.x;
+            const int64_t i = a.idx ? (int64_t)a.idx[sl] : sl;
+            if (i >= 0 && i < a.n_src) {
+                double sum[kNCPot];
 #pragma unroll
-    for (int c = 0; c < kNCPot; ++c) {
-        hi[c] = 0.0;
-        lo[c] = 0.0;
+                for (int q = 0; q < kNCPot; ++q) sum[q] = q < NC ? red[q][threadIdx.x] : 0.0;
+                write_target<POT, ETRACE>(a, i, sum);
+            }
+        }
+        __syncthreads();                             // red is reused by the next group
     }
-    for (int sp = 0; sp < split; ++sp) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-            two_sum_acc(hi[c], lo[c], a.part[((int64_t)sp * NC + c) * rows + slot]);
-    }
-    double sum[kNCPot];
-#pragma unroll
-    for (int c = 0; c < kNCPot; ++c) sum[c] = __dadd_rn(hi[c], lo[c]);
-    write_target<POT, ETRACE>(a, i, sum);
 }
 
 // ---------------------------------------------------------------------------
@@ -1867,6 +1884,7 @@ void launch_pack(int64_t n_src, const double *pos, const double *vel, const doub
 // Defined in the per-precision translation units.
 const EvalConfig *mixed_configs(int *count);
 const EvalConfig *f64_configs(int *count);
-void launch_reduce(const EvalArgs &a, int32_t BT, bool pot, bool etrace, int blocks, cudaStream_t st);
+void launch_reduce(const EvalArgs &a, int32_t BT, bool pot, bool etrace, int64_t n_targets,
+                   cudaStream_t st);
 
 }  // namespace grav

@@ -29,16 +29,22 @@ const EvalConfig *f64_configs(int *count)
     return kF64Configs;
 }
 
-void launch_reduce(const EvalArgs &a, int32_t BT, bool pot, bool etrace, int blocks, cudaStream_t st)
+void launch_reduce(const EvalArgs &a, int32_t BT, bool pot, bool etrace, int64_t n_targets,
+                   cudaStream_t st)
 {
+    const int tpb = pot ? reduce_targets_per_block<true>() : reduce_targets_per_block<false>();
+    int sms = 0;
+    if (device_sm_count(&sms) != GRAV_OK || sms <= 0) sms = 1;
+    const unsigned blocks =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_targets + tpb - 1) / tpb, 8LL * sms));
     if (pot && etrace)
-        reduce_partials_kernel<true, true><<<blocks, 256, 0, st>>>(a, BT);
+        reduce_partials_kernel<true, true><<<blocks, kReduceThreads, 0, st>>>(a, BT);
     else if (pot)
-        reduce_partials_kernel<true, false><<<blocks, 256, 0, st>>>(a, BT);
+        reduce_partials_kernel<true, false><<<blocks, kReduceThreads, 0, st>>>(a, BT);
     else if (etrace)
-        reduce_partials_kernel<false, true><<<blocks, 256, 0, st>>>(a, BT);
+        reduce_partials_kernel<false, true><<<blocks, kReduceThreads, 0, st>>>(a, BT);
     else
-        reduce_partials_kernel<false, false><<<blocks, 256, 0, st>>>(a, BT);
+        reduce_partials_kernel<false, false><<<blocks, kReduceThreads, 0, st>>>(a, BT);
 }
 
 }  // namespace grav

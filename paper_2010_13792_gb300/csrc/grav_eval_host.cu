@@ -336,8 +336,7 @@ int eval_single(const char *who, const grav_params *p, bool soft, int64_t n_src,
         need_reduce = choose_split(n_tb, a.n_tiles, grid, a.max_split, a.part_cap_rows, BT) > 1;
     }
     if (need_reduce) {
-        int blocks = (int)((n_idx_max + 255) / 256);
-        launch_reduce(a, BT, want_pot, c->precision == GRAV_MIXED, blocks, st);
+        launch_reduce(a, BT, want_pot, c->precision == GRAV_MIXED, n_idx_max, st);
         rc = check_launch("grav_eval/reduce");
         if (rc) return rc;
     }
