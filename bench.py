@@ -389,7 +389,7 @@ def extras(args, path, dev, sms, peak32, flush):
     out["adaptive_softening_N1048576"] = soft_extra(path, dev, flush)
     out["tree_N1048576"] = tree_extra(path, dev, flush)
     out["adjoint"] = backward_extra(path, dev, flush)
-    out["other_workloads_mixed_all_active"] = workloads_extra(dev, flush, sms, peak32)
+    out["other_workloads_mixed_all_active"] = workloads_extra(dev, flush, peak32)
     out["batched_256_systems"] = batched_extra(dev, flush)
     out["adaptive_plummer_131072"] = adaptive_extra(dev)
     try:
@@ -558,7 +558,7 @@ def tree_extra(path, dev, flush):
     return res
 
 
-def workloads_extra(dev, flush, sms, peak32):
+def workloads_extra(dev, flush, peak32):
     """The mixed force evaluation, every element a target, on the other
     synthetic inputs shaped like the paper's tests: the Plummer sphere of
     2^17 (h = 1e-3, centrally concentrated: many softened tiles near the

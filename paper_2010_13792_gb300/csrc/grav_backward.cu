@@ -54,8 +54,6 @@ __device__ __forceinline__ T sqrt_t(T x) { return sqrt(x); }
 template <typename T>
 struct Src;
 template <>
-struct Src<float> { using type = float4; };
-template <>
 struct Src<double> { using type = D4; };
 
 template <typename T, int KT, int S, bool NEAR>
@@ -126,6 +124,8 @@ __device__ __forceinline__ void bwd_write(const BwdArgs &a, int64_t k, const dou
     a.mass_bar[k] = pm;
 }
 
+// The direct-sum adjoint on scalar (x, a_bar) tiles; instantiated for FP64
+// (the mixed adjoint is backward_pair_kernel below).
 template <typename T, int NT, int KT, int S, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 backward_kernel(const BwdArgs a)
