@@ -63,6 +63,9 @@ class AdaptiveIntegrator:
         self.idx = torch.zeros(n, dtype=torch.int32, device=device)
         self.count = torch.zeros(1, dtype=torch.int32, device=device)
         self.a_kick = torch.zeros(n, 3, dtype=torch.float64, device=device)
+        # half of the step of each bin (exact powers of two), for the kicks
+        self.half_step = torch.tensor([0.5 * self.dt_min * 2.0 ** (k_max - k) for k in range(k_max + 1)],
+                                      dtype=torch.float64, device=device)
         self.zero_j = torch.zeros_like(self.acc)
         # history of the polynomial predictor
         self.elapsed = torch.zeros(n, dtype=torch.int64, device=device)
@@ -84,9 +87,6 @@ class AdaptiveIntegrator:
         self.graph_ticks = 0
 
     # -- pieces ---------------------------------------------------------------
-    def _steps(self):
-        return self.dt_min * torch.pow(2.0, (self.k_max - self.bins.to(torch.int32)).to(torch.float64))
-
     def _gravity(self, tick: int):
         g = grav
         poly = self.predictor == "poly"
@@ -113,9 +113,11 @@ class AdaptiveIntegrator:
         self.n_due_total += self.count.to(torch.int64)
         self.n_active_total += self.active.sum(dtype=torch.int64)
 
-    def _kick(self, steps):
-        w = (0.5 * steps * self.active.to(torch.float64)).unsqueeze(1)
-        self.vel.addcmul_(self.a_kick, w)
+    def _kick(self):
+        # half a step of the element's bin for active elements, 0 for the rest
+        # (one gather and one product: these launches run every tick)
+        w = self.half_step[self.bins.long()] * self.active
+        self.vel.addcmul_(self.a_kick, w.unsqueeze(1))
 
     def substep(self, tick: int):
         """One tick: drift, gravity for the elements at a step boundary, kicks."""
@@ -123,10 +125,10 @@ class AdaptiveIntegrator:
             self.pos.add_(self.vel, alpha=self.dt_min)
         self._gravity(tick)
         if tick > 0:
-            self._kick(self._steps())              # closes the step that ends now
+            self._kick()                           # closes the step that ends now
         grav.assign_bins(tick, self.k_max, self.dt_max, self.active, self.dt_grav, self.dt_hydro,
                          self.bins)
-        self._kick(self._steps())                  # opens the next step
+        self._kick()                               # opens the next step
 
     # -- driving --------------------------------------------------------------
     def start(self):
