@@ -124,7 +124,7 @@ __host__ __device__ inline int choose_split(int64_t n_tb, int32_t n_tiles, int32
     for (int64_t s = 1; s <= s_max; ++s) {
         int64_t items = n_tb * s;
         int64_t slots = ((items + grid - 1) / grid) * grid;
-        if (items >= grid && 10 * items >= 9 * slots) return (int)s;
+        if (items >= grid && 20 * items >= 19 * slots) return (int)s;
         if (items * best_slots > best_items * slots) {
             best = s;
             best_items = items;
