@@ -312,14 +312,18 @@ def run_ours(args, rank, local, ws):
         "eval_ms_mean": 1e3 * eval_s,
     }
 
-    if rank == 0 and not args.no_extras:
+    if not args.no_extras:
+        # end to end on every rank (units of all ranks over the slowest rank)
+        result["e2e"] = e2e(args, path, dev, flush, ws)
+    if rank == 0 and ws == 1 and not args.no_extras:
+        # the other workloads and the oracle baseline at one GPU only (with
+        # more ranks they would hold every GPU for minutes)
         result["extras"] = extras(args, path, dev, sms, peak32, flush)
         result["extras"]["fp64_path"]["mixed_over_fp64"] = \
             value / result["extras"]["fp64_path"]["interactions_per_s"]
         tree = result["extras"]["tree_N1048576"]
         if args.n == tree["n"] and args.fraction == 1.0:
             tree["speedup_over_mixed_direct"] = 1e3 * eval_s / tree["mixed"]["ms"]
-        result["e2e"] = e2e(args, path, dev, flush)
         result["cpu_baseline"] = cpu_baseline(path, args.cpu_seconds)
     return result
 
@@ -753,7 +757,7 @@ def adaptive_extra(dev):
     return res
 
 
-def e2e(args, path, dev, flush):
+def e2e(args, path, dev, flush, ws=1):
     """The same step through the C ABI with inputs in pinned HOST memory:
     host->device copies of the step's inputs and device->host copies of its
     results are inside the timed region."""
@@ -794,8 +798,9 @@ def e2e(args, path, dev, flush):
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(b) * 1e-3)
         tick += 2
-    t = statistics.mean(ts)
-    return {"value": path.n_due_expected * path.n / t, "unit": "interactions/s",
+    t = max_over_ranks(statistics.mean(ts), ws, dev)
+    units = sum_over_ranks(float(path.n_due_expected) * path.n, ws, dev)
+    return {"value": units / t, "unit": "interactions/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
 
 
