@@ -351,7 +351,7 @@ __device__ __forceinline__ void pack_tile(int t, int64_t first, int64_t end,
         D4 pm, pv;
         if (ok) {
             pm = D4{x[0], x[1], x[2], m};
-            pv = D4{v[0], v[1], v[2], 0.0};
+            pv = D4{v[0] - (double)cvf[0], v[1] - (double)cvf[1], v[2] - (double)cvf[2], 0.0};
         } else {
             pm = D4{1.0e150, 0.0, 0.0, 0.0};
             pv = D4{0.0, 0.0, 0.0, 0.0};
@@ -885,9 +885,12 @@ __device__ __forceinline__ void accumulate_d(double acc[kNCPot], double dx, doub
     if (POT) acc[PSUM] += mp;
 }
 
+// FP64 pair loop.  Source velocities are stored relative to the tile's
+// velocity centre and the target's enters per tile (f64_item): the sums take
+// the source velocity v_j' alone, J1 = sum m f v_j' and J2 = sum m g' (d.v_j') d.
 template <int S, bool POT, bool NEAR, bool PERIODIC = false>
 __device__ __forceinline__ void loop_d(const D4 *__restrict__ sp, const D4 *__restrict__ sv,
-                                       const double xi[3], const double vi[3], int64_t ti,
+                                       const double xi[3], int64_t ti,
                                        int64_t jbase, double h2, double hinv,
                                        double acc[kNCPot], double box = 0.0, double box_inv = 0.0,
                                        double tie = 0.0)
@@ -926,8 +929,25 @@ __device__ __forceinline__ void loop_d(const D4 *__restrict__ sp, const D4 *__re
                 mp = 0.0;
             }
         }
-        accumulate_d<POT>(acc, dx, dy, dz, v.x - vi[0], v.y - vi[1], v.z - vi[2], mf, mg, mp);
+        accumulate_d<POT>(acc, dx, dy, dz, v.x, v.y, v.z, mf, mg, mp);
     }
+}
+
+// The target's velocity in the sums of one tile (v_i' relative to the tile's
+// velocity centre): J1 -= F v_i', J2 -= Tp v_i' (with v = v_j' - v_i' the
+// pair sums J1 = sum m f v and J2 = sum m g' (d.v) d split exactly so).
+__device__ __forceinline__ void target_velocity_d(double acc[kNCPot], const double u[3])
+{
+    const double f = acc[FSUM];
+    const double t0 = fma(acc[TXX], u[0], fma(acc[TXY], u[1], acc[TXZ] * u[2]));
+    const double t1 = fma(acc[TXY], u[0], fma(acc[TYY], u[1], acc[TYZ] * u[2]));
+    const double t2 = fma(acc[TXZ], u[0], fma(acc[TYZ], u[1], acc[TZZ] * u[2]));
+    acc[J10 + 0] = fma(-u[0], f, acc[J10 + 0]);
+    acc[J10 + 1] = fma(-u[1], f, acc[J10 + 1]);
+    acc[J10 + 2] = fma(-u[2], f, acc[J10 + 2]);
+    acc[J20 + 0] -= t0;
+    acc[J20 + 1] -= t1;
+    acc[J20 + 2] -= t2;
 }
 
 
@@ -1627,20 +1647,25 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
         double acc[kNCPot];
 #pragma unroll
         for (int c = 0; c < kNCPot; ++c) acc[c] = 0.0;
+        // the target's velocity relative to the tile's velocity centre (the
+        // tile stores its sources' velocities relative to it)
+        const double vr[3] = {vi[0] - (double)g.cv[0], vi[1] - (double)g.cv[1],
+                              vi[2] - (double)g.cv[2]};
         if (soft && near) {
-            soft_loop_d<S, POT>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, hinv_i, zeta_i, a,
+            soft_loop_d<S, POT>(sm.stage[s], sm.stage[s] + S, xi, vr, i, g.first, hinv_i, zeta_i, a,
                                 acc);
-        } else if (periodic) {
-            if (!near)
-                loop_d<S, POT, false, true>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, h2, hinv,
-                                            acc, a.box, a.box_inv, a.box_tie);
-            else
-                loop_d<S, POT, true, true>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, h2, hinv,
-                                           acc, a.box, a.box_inv, a.box_tie);
-        } else if (!near) {
-            loop_d<S, POT, false>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, h2, hinv, acc);
         } else {
-            loop_d<S, POT, true>(sm.stage[s], sm.stage[s] + S, xi, vi, i, g.first, h2, hinv, acc);
+            if (periodic && !near)
+                loop_d<S, POT, false, true>(sm.stage[s], sm.stage[s] + S, xi, i, g.first, h2, hinv,
+                                            acc, a.box, a.box_inv, a.box_tie);
+            else if (periodic)
+                loop_d<S, POT, true, true>(sm.stage[s], sm.stage[s] + S, xi, i, g.first, h2, hinv,
+                                           acc, a.box, a.box_inv, a.box_tie);
+            else if (!near)
+                loop_d<S, POT, false>(sm.stage[s], sm.stage[s] + S, xi, i, g.first, h2, hinv, acc);
+            else
+                loop_d<S, POT, true>(sm.stage[s], sm.stage[s] + S, xi, i, g.first, h2, hinv, acc);
+            target_velocity_d(acc, vr);
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) two_sum_acc(shi[c], slo[c], acc[c]);

@@ -14,8 +14,8 @@ namespace grav {
 
 #define GRAV_F64_CFG(NT, S)                                                                       \
     {GRAV_F64, NT, 1, S, 4, 0, GRAV_F64_FN3(launch_f64, NT, S), GRAV_F64_FN3(occupancy_f64, NT, S), \
-     launch_pack<S, false, false, false>, GRAV_F64_FN2(launch_f64_batched, NT, S),                 \
-     GRAV_F64_FN2(occupancy_f64_batched, NT, S), launch_pack_batched<S, false, false, false>, false}
+     launch_pack<S, false, true, false>, GRAV_F64_FN2(launch_f64_batched, NT, S),                  \
+     GRAV_F64_FN2(occupancy_f64_batched, NT, S), launch_pack_batched<S, false, true, false>, false}
 
 static const EvalConfig kF64Configs[] = {
     GRAV_F64_CFG(128, 128),
