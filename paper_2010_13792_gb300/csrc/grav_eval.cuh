@@ -31,12 +31,13 @@
 //     the pair loop.
 // Per-tile sums are FP32; they are carried across tiles as compensated FP32
 // pairs (TwoSum), in registers or in shared memory, and the final per-target
-// result is FP64.  The FP64 path (K4) accumulates the plain sums in FP64.
+// result is FP64.  The FP64 path (K4) accumulates the sums in FP64, with the
+// second identity (tile-relative velocities) but F summed directly.
 //
-// Tiles whose bounding box lies at least h from the target block's bounding
-// box take the Newtonian loop (exact there: the cubic spline has compact
-// support); the others take the softened loop, which also excludes the self
-// pair by index.
+// Tiles whose bounding box lies at least h from the bounding box of the
+// targets of a warp (of the block in the FP64 adaptive-softening kernel) take
+// the Newtonian loop (exact there: the cubic spline has compact support); the
+// others take the softened loop, which also excludes the self pair by index.
 //
 // Work items are (target block, source chunk).  A fixed grid of CTAs takes
 // items round-robin; when the target set is small the sources are split into
