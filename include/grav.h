@@ -108,8 +108,8 @@ GRAV_API int grav_tile_config(int32_t precision, int32_t index, grav_tile_info *
 /* The configuration that tile_config = -1 selects for an evaluation of
  * n_targets targets (the n_idx_max of the call): open boundaries
  * (periodic = soft = 0), a periodic box (periodic != 0) or adaptive softening
- * (soft != 0).  768-thread CTAs from 8192 targets (2^19 in a periodic box),
- * 256-thread CTAs below.  Returns
+ * (soft != 0).  768-thread CTAs from 8192 targets, 256-thread CTAs below
+ * (the same in every mode).  Returns
  * the index (>= 0), or GRAV_EINVAL for a bad precision or n_targets < 0.  A
  * property of the library's kernels; the paper has no counterpart. */
 GRAV_API int32_t grav_default_tile_config(int32_t precision, int32_t periodic, int32_t soft,

@@ -10,16 +10,14 @@
 namespace grav {
 namespace {
 
-// Default tile configurations (measured on 2^20-element clouds and 64^3 and
-// 96^3 periodic lattices): 768-thread CTAs, one per SM, for open boundaries
-// and adaptive softening from 8192 targets and for the periodic box from
-// 2^19 targets; 256-thread CTAs (three per SM) for smaller sets and batched
-// launches, where more CTAs per SM keep the SMs busier through the last
-// round of work items.
+// Default tile configurations (measured on 2^20-element clouds, a 2^17
+// Plummer sphere and 64^3 and 96^3 periodic lattices): 768-thread CTAs, one
+// per SM, from 8192 targets; 256-thread CTAs (three per SM) for smaller sets
+// and batched launches, where more CTAs per SM keep the SMs busier through the
+// last round of work items.
 constexpr int kDefaultMixed = 11;
 constexpr int kDefaultMixedLarge = 17;
 constexpr int64_t kLargeTargetSet = 1 << 13;
-constexpr int64_t kLargePeriodicSet = 1 << 19;
 constexpr int kDefaultF64 = 0;
 constexpr int64_t kSplitRowsPerSM = 16;   // partial capacity, in target blocks per SM
 
@@ -53,8 +51,8 @@ int check_params(const grav_params *p, const char *who)
 int default_index(int32_t precision, int mode, int64_t n_targets)
 {
     if (precision != GRAV_MIXED) return kDefaultF64;
-    const int64_t large = mode == kModePeriodic ? kLargePeriodicSet : kLargeTargetSet;
-    return n_targets >= large ? kDefaultMixedLarge : kDefaultMixed;
+    (void)mode;   // the same choice in every mode
+    return n_targets >= kLargeTargetSet ? kDefaultMixedLarge : kDefaultMixed;
 }
 
 // The configuration of an evaluation: p->tile_config, or the default for its

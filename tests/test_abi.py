@@ -148,8 +148,8 @@ def test_python_binding_rejects_cpu_tensors():
 
 def test_default_tile_config_choice(libgrav):
     """The configuration tile_config = -1 selects: 768-thread CTAs from 8192
-    targets (2^19 in a periodic box), 256-thread CTAs below; one FP64 default;
-    bad arguments rejected.  Host logic only."""
+    targets in every mode, 256-thread CTAs below; one FP64 default; bad
+    arguments rejected.  Host logic only."""
     from paper_2010_13792_gb300 import grav
     L = grav.lib()
     big = grav.tile_configs(grav.MIXED)[grav.default_tile_config(grav.MIXED, 1 << 20)]
@@ -157,9 +157,9 @@ def test_default_tile_config_choice(libgrav):
     assert big["threads"] == 768 and small["threads"] == 256
     assert grav.default_tile_config(grav.MIXED, 8192) == grav.default_tile_config(grav.MIXED, 1 << 20)
     assert grav.default_tile_config(grav.MIXED, 8191) == grav.default_tile_config(grav.MIXED, 100)
-    assert grav.default_tile_config(grav.MIXED, 1 << 18, periodic=True) == \
+    assert grav.default_tile_config(grav.MIXED, 8191, periodic=True) == \
         grav.default_tile_config(grav.MIXED, 100)
-    assert grav.default_tile_config(grav.MIXED, 1 << 19, periodic=True) == \
+    assert grav.default_tile_config(grav.MIXED, 1 << 18, periodic=True) == \
         grav.default_tile_config(grav.MIXED, 1 << 20)
     assert grav.default_tile_config(grav.MIXED, 1 << 20, soft=True) == \
         grav.default_tile_config(grav.MIXED, 1 << 20)
