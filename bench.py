@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="headline steps only (no sweeps, FP64 path, e2e, CPU baseline)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--predict-only", action="store_true",
+                    help="time only the predictor (grav_predict) on --n elements, all active, "
+                         "none due, and print its bandwidth")
     return ap.parse_args()
 
 
@@ -409,10 +412,10 @@ def extras(args, path, dev, sms, peak32, flush):
     return out
 
 
-def predict_bandwidth(dev, n):
+def predict_bandwidth(dev, n, reps=5, warmup=1):
     """The predictor (HBM-bound) on n elements, all active, none due:
     82 B per element (flags 2, T_f 8, a_last 24, j_last 24 read; a_out 24
-    written); inputs larger than L2, median of 5 event-timed launches."""
+    written); inputs larger than L2, median of `reps` event-timed launches."""
     import torch
 
     from paper_2010_13792_gb300 import grav
@@ -423,9 +426,10 @@ def predict_bandwidth(dev, n):
     j_last = torch.randn(n, 3, dtype=torch.float64, device=dev, generator=g)
     tf = torch.randint(0, 64, (n,), dtype=torch.int64, device=dev, generator=g)
     a_out = torch.empty_like(a_last)
-    grav.predict(ones, zeros, a_last, j_last, tf, 2.0**-10, a_out)
+    for _ in range(max(warmup, 1)):
+        grav.predict(ones, zeros, a_last, j_last, tf, 2.0**-10, a_out)
     ts = []
-    for _ in range(5):
+    for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         grav.predict(ones, zeros, a_last, j_last, tf, 2.0**-10, a_out)
@@ -434,6 +438,15 @@ def predict_bandwidth(dev, n):
         ts.append(a.elapsed_time(b) * 1e-3)
     t = statistics.median(ts)
     return {"n": n, "bytes": 82 * n, "us": 1e6 * t, "GB_per_s": 82 * n / t / 1e9}
+
+
+def measured_hbm_peak():
+    """The machine's measured copy bandwidth (GB/s), if the machine provides it."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def periodic_extra(dev, flush):
@@ -872,6 +885,15 @@ def run_reference(args, rank, ws):
 def main():
     args = parse()
     rank, local, ws = dist_setup()
+    if args.predict_only:
+        import torch
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        res = predict_bandwidth(dev, args.n, reps=max(args.steps, 1), warmup=max(args.warmup, 0))
+        res["peak_GB_per_s"] = measured_hbm_peak()
+        if rank == 0:
+            print(json.dumps({"predict": res}), flush=True)
+        return
     if args.impl == "reference":
         res = run_reference(args, rank, ws)
     else:

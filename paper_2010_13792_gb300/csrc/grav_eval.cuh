@@ -91,6 +91,7 @@ struct EvalArgs {
     int64_t part_cap_rows;     // partial rows available (each row NC doubles)
     const double *pos;
     const double *vel;
+    const double *mass;           // FP64 masses (the periodic close field reads them)
     double G, h, sqrt_eta;
     float hf, h2f_up, hinvf, pad1;
     double *acc, *jerk, *tidal, *pot, *dt_grav;
@@ -643,20 +644,23 @@ __device__ __forceinline__ double nearest_image_d(double xj, double xi, double b
     return fabs(w) > tie ? nearest_image_exact(xj, xi, box) : w;
 }
 
-// Per target and tile: does the tile need the general loop (softened pairs,
-// or sources that might not lie within `tie` (a little under half a box) of
-// the target's image of the tile centre)?  t is the target's wrapped offset
-// from the tile centre.  Outside the general loop every pair separation is
-// then shorter than half a box by more than the FP32 rounding of the
-// offsets, so its nearest image is unambiguous.
+// Per target and tile of the periodic box: bit 0 when the tile needs the
+// general loop (softened pairs, or sources that might not lie within `tie`,
+// a little under half a box, of the target's image of the tile centre), bit
+// 1 when the tile comes within the target's close radius (rc2, squared; see
+// close_radii).  t is the target's wrapped offset from the tile centre.
+// Outside the general loop every pair separation is shorter than half a box
+// by more than the FP32 rounding of the offsets, so its nearest image is
+// unambiguous.  Distances are rounded down (any doubt means "near").
 template <int KT>
-__device__ __forceinline__ bool periodic_special(const float t[KT][3], const int64_t ti[KT],
-                                                 const TileGeom &g, float h2_up, float tie)
+__device__ __forceinline__ int periodic_class(const float t[KT][3], const int64_t ti[KT],
+                                              const TileGeom &g, float h2_up, float tie,
+                                              const float rc2[KT])
 {
     float e[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) e[c] = __fmul_ru(0.5f, __fsub_ru(g.hi[c], g.lo[c]));
-    bool special = false;
+    int cls = 0;
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
         if (ti[q] < 0) continue;
@@ -664,13 +668,87 @@ __device__ __forceinline__ bool periodic_special(const float t[KT][3], const int
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const float at = fabsf(t[q][c]);
-            if (__fadd_ru(at, e[c]) >= tie) special = true;
+            if (__fadd_ru(at, e[c]) >= tie) cls |= 1;
             const float gap = fmaxf(0.0f, __fsub_rd(at, e[c]));
             d2 = __fmaf_rd(gap, gap, d2);
         }
-        if (d2 < h2_up) special = true;
+        if (d2 < h2_up) cls |= 1;
+        if (d2 < rc2[q]) cls |= 2;
     }
-    return special;
+    return cls;
+}
+
+// ---------------------------------------------------------------------------
+// Periodic box: the close field of a target.  On a lattice the tidal tensor
+// and the jerk of an element are near-cancellations of the pair terms of its
+// nearest neighbours (sum_j ||T_ij|| / ||T_i|| reaches 10^3 - 10^4 on the
+// pancake lattices), so the FP32 rounding of those few terms, and of long FP32
+// running sums of positive terms such as sum m dx^2 / r^5, is amplified that
+// much.  Two radii around each target scale with the distance r_own from it
+// to the nearest other source of its own tile:
+//   - pairs closer than R_p = 2.4 r_own are left out of the FP32 sums, listed,
+//     and evaluated in FP64 from the FP64 positions, velocities and masses once
+//     the item's tiles are done (at most kCloseList per target; past that a
+//     pair stays in the FP32 sums);
+//   - tiles whose box comes within R_c = 4.5 r_own of a target of the warp take
+//     a close loop, whose FP32 sums run over kCloseRun sources before they
+//     enter the compensated carry.
+// Everything else keeps the FP32 loops.  The FP64 kernels use R_c only (their
+// pair terms are FP64 already; their close tiles are summed in runs too).  A
+// target alone in its tile, or with a coincident source there, has no close
+// field.
+// ---------------------------------------------------------------------------
+constexpr int kCloseRun = 32;
+constexpr int kCloseList = 64;
+constexpr float kCloseRp = 2.4f;
+constexpr float kCloseRc = 4.5f;
+
+// One pair of the close field in FP64 (target i at FP64 position xi, source
+// j != i): the pair's contributions to the accumulated sums, in the slots of
+// the mixed path (A, J1, J2 with the pair's own relative velocity, E = m f -
+// m g' r^2, Tp, and P), nearest image decided as the FP64 kernels decide it.
+template <bool POT>
+__device__ __forceinline__ void close_pair_d(const EvalArgs &a, int64_t i, int64_t j,
+                                             const double xi[3], double out[kNCPot])
+{
+    double d[3], v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        d[c] = nearest_image_d(a.pos[3 * j + c], xi[c], a.box, a.box_inv, a.box_tie);
+        v[c] = a.vel[3 * j + c] - a.vel[3 * i + c];
+    }
+    const double m = a.mass[j];
+    const double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
+    double mp, mf, mg;
+    if (r2 < a.h * a.h) {
+        const double hinv = 1.0 / a.h;
+        double F, Gp, P;
+        spline_kernel<double>(sqrt(r2) * hinv, F, Gp, P);
+        mf = m * F * (hinv * hinv * hinv);
+        mg = m * Gp * (hinv * hinv * hinv * hinv * hinv);
+        mp = m * P * hinv;
+    } else {
+        const double ri = rsqrt(r2);
+        const double ri2 = ri * ri;
+        mp = m * ri;
+        mf = mp * ri2;
+        mg = mf * ri2;
+    }
+    const double dv = fma(d[0], v[0], fma(d[1], v[1], d[2] * v[2]));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        out[A0 + c] = mf * d[c];
+        out[J10 + c] = mf * v[c];
+        out[J20 + c] = mg * dv * d[c];
+    }
+    out[ESUM] = fma(-mg, r2, mf);
+    out[TXX] = mg * d[0] * d[0];
+    out[TYY] = mg * d[1] * d[1];
+    out[TZZ] = mg * d[2] * d[2];
+    out[TXY] = mg * d[0] * d[1];
+    out[TXZ] = mg * d[0] * d[2];
+    out[TYZ] = mg * d[1] * d[2];
+    out[PSUM] = POT ? mp : 0.0;
 }
 
 // General loop of the periodic box: every pair taken to its nearest image
@@ -747,6 +825,193 @@ __device__ __forceinline__ void periodic_loop_f(const float4 *__restrict__ stage
             }
             accumulate_f<KT, POT>(acc, q, dx, dy, dz, vx, vy, vz, mf, mg, mp);
         }
+    }
+}
+
+// 1/sqrt(x) refined by one Newton-Raphson step on f(y) = y^-2 - x from the
+// SFU estimate y0: y1 = y0 + (y0 / 2) (1 - x y0^2), which roughly halves the
+// relative error of y0 (the close loops only: their pair terms feed the
+// cancellations described above).
+__device__ __forceinline__ float rsqrt_refined(float x)
+{
+    const float y = rsqrt_sfu(x);
+    const float e = fmaf(-(x * y), y, 1.0f);
+    return fmaf(0.5f * y, e, y);
+}
+
+__device__ __forceinline__ float2 rsqrt_refined2(float2 x)
+{
+    const float2 y = make_float2(rsqrt_sfu(x.x), rsqrt_sfu(x.y));
+    const float2 xy = __fmul2_rn(x, y);
+    const float2 e = __ffma2_rn(make_float2(-xy.x, -xy.y), y, make_float2(1.0f, 1.0f));
+    return __ffma2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), y), e, y);
+}
+
+// Close tiles of the periodic box (see close_radii) that may need wrapping or
+// hold softened or self pairs: the general loop's pair arithmetic (nearest
+// image in FP32, FP64 re-formation near half a box, the cubic spline inside
+// h, the self pair excluded) over runs of kCloseRun sources, each run's FP32
+// sums handed to carry(acc) (the per-tile target-velocity correction and the
+// compensated carry).  A pair closer than R_p (squared: rp2) is offered to
+// record(q, j), which lists it for the FP64 close field and returns true, or
+// returns false when the list is full and the pair stays in the FP32 sums.
+template <int KT, int S, bool POT, bool PAIR, typename Carry, typename Record>
+__device__ __forceinline__ void close_loop_f(const float4 *__restrict__ stage,
+                                             const float tx[KT][3], const int64_t ti[KT],
+                                             int64_t jbase, float h2, float hinv,
+                                             const float rp2[KT], const EvalArgs &a, Carry &carry,
+                                             Record &record)
+{
+    const float box = a.box_f, box_inv = a.box_inv_f, tie = a.box_tie_f;
+    const float hinv3 = hinv * hinv * hinv;
+    const float hinv5 = hinv3 * hinv * hinv;
+    const float *tile = reinterpret_cast<const float *>(stage);
+#pragma unroll 1
+    for (int j0 = 0; j0 < S; j0 += kCloseRun) {
+        float acc[KT][kNCPot];
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+#pragma unroll
+            for (int c = 0; c < kNCPot; ++c) acc[q][c] = 0.0f;
+#pragma unroll 2
+        for (int j = j0; j < j0 + kCloseRun; ++j) {
+            float x, y, z, m, vx, vy, vz;
+            if (PAIR) {
+                const int k = j >> 1, h = j & 1;
+                x = tile[4 * k + h];
+                y = tile[4 * k + 2 + h];
+                z = tile[2 * S + 4 * k + h];
+                m = tile[2 * S + 4 * k + 2 + h];
+                vx = tile[4 * S + 4 * k + h];
+                vy = tile[4 * S + 4 * k + 2 + h];
+                vz = tile[6 * S + 2 * k + h];
+            } else {
+                const float4 p = stage[j], v = stage[S + j];
+                x = p.x;
+                y = p.y;
+                z = p.z;
+                m = p.w;
+                vx = v.x;
+                vy = v.y;
+                vz = v.z;
+            }
+            const int64_t jg = jbase + j;
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                float dx = x - tx[q][0], dy = y - tx[q][1], dz = z - tx[q][2];
+                dx = fmaf(-box, rintf(dx * box_inv), dx);
+                dy = fmaf(-box, rintf(dy * box_inv), dy);
+                dz = fmaf(-box, rintf(dz * box_inv), dz);
+                if (fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) > tie && m != 0.0f && ti[q] >= 0) {
+                    const double *pi = a.pos + 3 * ti[q], *pj = a.pos + 3 * jg;
+                    dx = __double2float_rn(nearest_image_d(pj[0], pi[0], a.box, a.box_inv, a.box_tie));
+                    dy = __double2float_rn(nearest_image_d(pj[1], pi[1], a.box, a.box_inv, a.box_tie));
+                    dz = __double2float_rn(nearest_image_d(pj[2], pi[2], a.box, a.box_inv, a.box_tie));
+                }
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (r2 < rp2[q] && jg != ti[q] && m != 0.0f && record(q, jg)) continue;
+                const float ri = rsqrt_refined(r2);
+                const float ri2 = ri * ri;
+                float mp = m * ri;
+                float mf = mp * ri2;
+                float mg = mf * ri2;
+                if (r2 < h2) {
+                    float F, Gp, P;
+                    spline_kernel<float>(sqrtf(r2) * hinv, F, Gp, P);
+                    mf = m * F * hinv3;
+                    mg = m * Gp * hinv5;
+                    mp = m * P * hinv;
+                    if (jg == ti[q]) {
+                        mf = 0.0f;
+                        mg = 0.0f;
+                        mp = 0.0f;
+                    }
+                    acc[q][ESUM] += fmaf(-mg, r2, mf);
+                }
+                accumulate_f<KT, POT>(acc, q, dx, dy, dz, vx, vy, vz, mf, mg, mp);
+            }
+        }
+        carry(acc);
+    }
+}
+
+// Close tiles that need no wrapping and hold no softened or self pair (no
+// target of the warp flags the tile in bit 0 of periodic_class): the paired
+// Newtonian loop of far_loop_pair, with pairs closer than R_p offered to
+// record(q, j) (and left out of the sums when it takes them) and the sums
+// carried every kCloseRun sources.
+template <int KT, int S, bool POT, typename Carry, typename Record>
+__device__ __forceinline__ void close_loop_pair(const float *__restrict__ tile, const float tx[KT][3],
+                                                int64_t jbase, const float rp2[KT], Carry &carry,
+                                                Record &record)
+{
+    const float4 *P0 = reinterpret_cast<const float4 *>(tile);
+    const float4 *P1 = P0 + S / 2;
+    const float4 *V0 = P1 + S / 2;
+    const float2 *V1 = reinterpret_cast<const float2 *>(V0 + S / 2);
+    float2 ntx[KT], nty[KT], ntz[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        ntx[q] = make_float2(-tx[q][0], -tx[q][0]);
+        nty[q] = make_float2(-tx[q][1], -tx[q][1]);
+        ntz[q] = make_float2(-tx[q][2], -tx[q][2]);
+    }
+#pragma unroll 1
+    for (int k0 = 0; k0 < S / 2; k0 += kCloseRun / 2) {
+        float2 acc2[KT][kNCPot];
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+#pragma unroll
+            for (int c = 0; c < kNCPot; ++c) acc2[q][c] = make_float2(0.0f, 0.0f);
+#pragma unroll 2
+        for (int k = k0; k < k0 + kCloseRun / 2; ++k) {
+            const float4 p0 = P0[k], p1 = P1[k], v0 = V0[k];
+            const float2 vz = V1[k];
+            const float2 vx = make_float2(v0.x, v0.y), vy = make_float2(v0.z, v0.w);
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                const float2 dx = __fadd2_rn(make_float2(p0.x, p0.y), ntx[q]);
+                const float2 dy = __fadd2_rn(make_float2(p0.z, p0.w), nty[q]);
+                const float2 dz = __fadd2_rn(make_float2(p1.x, p1.y), ntz[q]);
+                float2 r2 = __fmul2_rn(dz, dz);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dx, dx, r2);
+                float2 m = make_float2(p1.z, p1.w);
+                if (r2.x < rp2[q] && m.x != 0.0f && record(q, jbase + 2 * k)) m.x = 0.0f;
+                if (r2.y < rp2[q] && m.y != 0.0f && record(q, jbase + 2 * k + 1)) m.y = 0.0f;
+                const float2 ri = rsqrt_refined2(r2);
+                const float2 ri2 = __fmul2_rn(ri, ri);
+                const float2 mp = __fmul2_rn(m, ri);
+                const float2 mf = __fmul2_rn(mp, ri2);
+                const float2 mg = __fmul2_rn(mf, ri2);
+                acc2[q][A0 + 0] = __ffma2_rn(mf, dx, acc2[q][A0 + 0]);
+                acc2[q][A0 + 1] = __ffma2_rn(mf, dy, acc2[q][A0 + 1]);
+                acc2[q][A0 + 2] = __ffma2_rn(mf, dz, acc2[q][A0 + 2]);
+                acc2[q][J10 + 0] = __ffma2_rn(mf, vx, acc2[q][J10 + 0]);
+                acc2[q][J10 + 1] = __ffma2_rn(mf, vy, acc2[q][J10 + 1]);
+                acc2[q][J10 + 2] = __ffma2_rn(mf, vz, acc2[q][J10 + 2]);
+                float2 dv = __fmul2_rn(dz, vz);
+                dv = __ffma2_rn(dy, vy, dv);
+                dv = __ffma2_rn(dx, vx, dv);
+                const float2 gx = __fmul2_rn(mg, dx), gy = __fmul2_rn(mg, dy), gz = __fmul2_rn(mg, dz);
+                acc2[q][TXX] = __ffma2_rn(gx, dx, acc2[q][TXX]);
+                acc2[q][TYY] = __ffma2_rn(gy, dy, acc2[q][TYY]);
+                acc2[q][TZZ] = __ffma2_rn(gz, dz, acc2[q][TZZ]);
+                acc2[q][TXY] = __ffma2_rn(gx, dy, acc2[q][TXY]);
+                acc2[q][TXZ] = __ffma2_rn(gx, dz, acc2[q][TXZ]);
+                acc2[q][TYZ] = __ffma2_rn(gy, dz, acc2[q][TYZ]);
+                acc2[q][J20 + 0] = __ffma2_rn(gx, dv, acc2[q][J20 + 0]);
+                acc2[q][J20 + 1] = __ffma2_rn(gy, dv, acc2[q][J20 + 1]);
+                acc2[q][J20 + 2] = __ffma2_rn(gz, dv, acc2[q][J20 + 2]);
+                if (POT) acc2[q][PSUM] = __fadd2_rn(acc2[q][PSUM], mp);
+            }
+        }
+        float acc[KT][kNCPot];
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+#pragma unroll
+            for (int c = 0; c < kNCPot; ++c) acc[q][c] = acc2[q][c].x + acc2[q][c].y;
+        carry(acc);
     }
 }
 
@@ -1047,10 +1312,12 @@ __device__ __forceinline__ void write_partial(const EvalArgs &a, int sp, int64_t
 struct ItemSpec {
     const int32_t *idx;
     int64_t slot0, slot_end;
-    int64_t elem_lo, elem_hi;
+    int64_t elem_lo, elem_hi;   // the targets' system: elements [elem_lo, elem_hi)
     int32_t t_begin, t_end;
     int32_t sp, split;
     int64_t rows;
+    int32_t tile0;              // the system's first tile (holds element elem_lo)
+    int32_t pad;
 };
 
 // TMA ring state of a CTA, carried from item to item.
@@ -1068,6 +1335,73 @@ __device__ __forceinline__ int64_t item_target(const ItemSpec &it, int64_t slot,
         return -1;
     }
     return i;
+}
+
+// Squared radii R_p^2 and R_c^2 of target i (element of the item's system, at
+// FP64 position xi) from r_own^2, found over the packed sources of its own
+// tile: mixed tiles (FP32 offsets from the tile centre, paired or float4
+// layout) in FP32, FP64 tiles in FP64; separations wrapped to the nearest
+// image.  -1 (no close field) when the tile holds no other source or a
+// coincident one.
+template <int S, bool MIXED, bool PAIR>
+__device__ __forceinline__ void close_radii(const EvalArgs &a, const ItemSpec &it, int64_t i,
+                                            const double xi[3], float &rp2, float &rc2)
+{
+    const int64_t k = (i - it.elem_lo) / S;
+    const int32_t t = it.tile0 + (int32_t)k;
+    const int self = (int)(i - (it.elem_lo + k * S));
+    float r2min = __int_as_float(0x7f800000);
+    if (MIXED) {
+        const TileGeom &g = a.geo[t];
+        float to[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) to[c] = __double2float_rn(__dsub_rn(xi[c], g.c[c]));
+        const float *tile = static_cast<const float *>(a.src) + (int64_t)t * 8 * S;
+        const float4 *t4 = static_cast<const float4 *>(a.src) + (int64_t)t * 2 * S;
+#pragma unroll 4
+        for (int j = 0; j < S; ++j) {
+            float x, y, z, m;
+            if (PAIR) {
+                const int kk = j >> 1, h = j & 1;
+                x = tile[4 * kk + h];
+                y = tile[4 * kk + 2 + h];
+                z = tile[2 * S + 4 * kk + h];
+                m = tile[2 * S + 4 * kk + 2 + h];
+            } else {
+                const float4 p = t4[j];
+                x = p.x;
+                y = p.y;
+                z = p.z;
+                m = p.w;
+            }
+            float dx = x - to[0], dy = y - to[1], dz = z - to[2];
+            dx = fmaf(-a.box_f, rintf(dx * a.box_inv_f), dx);
+            dy = fmaf(-a.box_f, rintf(dy * a.box_inv_f), dy);
+            dz = fmaf(-a.box_f, rintf(dz * a.box_inv_f), dz);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (j != self && m != 0.0f) r2min = fminf(r2min, r2);
+        }
+    } else {
+        const D4 *tile = static_cast<const D4 *>(a.src) + (int64_t)t * 2 * S;
+        double m2 = __longlong_as_double(0x7ff0000000000000LL);
+#pragma unroll 4
+        for (int j = 0; j < S; ++j) {
+            const D4 p = tile[j];
+            const double dx = wrap_d(p.x - xi[0], a.box, a.box_inv);
+            const double dy = wrap_d(p.y - xi[1], a.box, a.box_inv);
+            const double dz = wrap_d(p.z - xi[2], a.box, a.box_inv);
+            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            if (j != self && p.w != 0.0) m2 = fmin(m2, r2);
+        }
+        r2min = __double2float_rn(m2);
+    }
+    if (!(r2min > 0.0f) || isinf(r2min)) {
+        rp2 = -1.0f;
+        rc2 = -1.0f;
+        return;
+    }
+    rp2 = (kCloseRp * kCloseRp) * r2min;
+    rc2 = (kCloseRc * kCloseRc) * r2min;
 }
 
 // Never leave a copy in flight into shared memory (only after a timeout).
@@ -1307,9 +1641,78 @@ __device__ __forceinline__ bool mixed_item(
         }
     }
 
+    // periodic box: the close-field radii of each target (close_radii)
+    constexpr bool periodic = MODE == kModePeriodic;
+    float rp2[KT], rc2[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        rp2[q] = -1.0f;
+        rc2[q] = -1.0f;
+        if (periodic && ti[q] >= 0) {
+            double x3[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                x3[c] = SACC ? sm.x[c * BT + q * NT + threadIdx.x] : xr[SACC ? 0 : q][c];
+            close_radii<S, true, PAIR>(a, it, ti[q], x3, rp2[q], rc2[q]);
+        }
+    }
+
+    // the target velocity in one tile's (or run's) FP32 sums: J1 -= v_i' F,
+    // J2 -= Tp v_i' (v_i' relative to the tile's velocity centre); then the
+    // compensated carry
+    TileGeom g = a.geo[t_begin];
+    auto carry_tile = [&](float (&acc)[KT][kNCPot]) {
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const float ux = tvf[q][0] - g.cv[0], uy = tvf[q][1] - g.cv[1], uz = tvf[q][2] - g.cv[2];
+            const float Ft = acc[q][ESUM] + (acc[q][TXX] + acc[q][TYY] + acc[q][TZZ]);
+            acc[q][J10 + 0] = fmaf(-ux, Ft, acc[q][J10 + 0]);
+            acc[q][J10 + 1] = fmaf(-uy, Ft, acc[q][J10 + 1]);
+            acc[q][J10 + 2] = fmaf(-uz, Ft, acc[q][J10 + 2]);
+            acc[q][J20 + 0] -= fmaf(acc[q][TXX], ux, fmaf(acc[q][TXY], uy, acc[q][TXZ] * uz));
+            acc[q][J20 + 1] -= fmaf(acc[q][TXY], ux, fmaf(acc[q][TYY], uy, acc[q][TYZ] * uz));
+            acc[q][J20 + 2] -= fmaf(acc[q][TXZ], ux, fmaf(acc[q][TYZ], uy, acc[q][TZZ] * uz));
+            if (SACC) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    float *ph = &sm.acc[(2 * c) * BT + q * NT + threadIdx.x];
+                    float *pl = &sm.acc[(2 * c + 1) * BT + q * NT + threadIdx.x];
+                    float h = *ph, l = *pl;
+                    two_sum_acc(h, l, acc[q][c]);
+                    *ph = h;
+                    *pl = l;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    two_sum_acc(rhi[SACC ? 0 : q][SACC ? 0 : c], rlo[SACC ? 0 : q][SACC ? 0 : c],
+                                acc[q][c]);
+            }
+        }
+    };
+    // periodic: the pairs of each target's FP64 close field, listed by the
+    // close loops and evaluated once the item's tiles are done
+    int32_t nlist[KT][periodic ? kCloseList : 1];
+    int ncnt[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) ncnt[q] = 0;
+    auto record = [&](int q, int64_t j) -> bool {
+        if (ncnt[q] >= kCloseList) return false;
+        nlist[q][ncnt[q]++] = (int32_t)j;
+        return true;
+    };
+    // periodic: the FP64 close field of each target, summed in FP64 and added
+    // to its final sums
+    double nsum[periodic ? KT : 1][periodic ? kNCPot : 1];
+    if constexpr (periodic) {
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+#pragma unroll
+            for (int c = 0; c < kNCPot; ++c) nsum[q][c] = 0.0;
+    }
+
     // offsets of the targets to a tile's centre (FP64, rounded once); in a
     // periodic box, to the image of the centre nearest to the target
-    constexpr bool periodic = MODE == kModePeriodic;
     auto offsets = [&](const TileGeom &g, float out[KT][3]) {
 #pragma unroll
         for (int q = 0; q < KT; ++q)
@@ -1322,7 +1725,6 @@ __device__ __forceinline__ bool mixed_item(
             }
     };
     float tx[KT][3], tx_next[KT][3];
-    TileGeom g = a.geo[t_begin];
     offsets(g, tx);
 
     for (int t = t_begin; t < t_end; ++t) {
@@ -1334,10 +1736,16 @@ __device__ __forceinline__ bool mixed_item(
             const float hm = fmaxf(h_block, a.geo_h[t]);
             h2_tile = __fmul_ru(hm, hm);
         }
-        // (periodic: taken for the warp's targets)
-        const bool near = periodic
-            ? __any_sync(0xffffffffu, periodic_special<KT>(tx, ti, g, a.h2f_up, a.box_tie_f))
-            : tile_is_near(blo_r, bhi_r, g, h2_tile);
+        // (periodic: taken for the warp's targets; "close" tiles come within
+        // a target's close radius and take the close loop)
+        bool near, close = false;
+        if (periodic) {
+            const int cls = periodic_class<KT>(tx, ti, g, a.h2f_up, a.box_tie_f, rc2);
+            close = __any_sync(0xffffffffu, (cls & 2) != 0);
+            near = __any_sync(0xffffffffu, (cls & 1) != 0);
+        } else {
+            near = tile_is_near(blo_r, bhi_r, g, h2_tile);
+        }
         // next tile's geometry and offsets, computed ahead (FP64 latency)
         TileGeom gn = g;
         if (t + 1 < t_end) {
@@ -1355,7 +1763,15 @@ __device__ __forceinline__ bool mixed_item(
         for (int q = 0; q < KT; ++q)
 #pragma unroll
             for (int c = 0; c < kNCPot; ++c) acc[q][c] = 0.0f;
-        if (soft && near) {
+        if (periodic && close) {
+            // runs of the close loops carry their own sums; acc stays zero
+            if (PAIR && !near)
+                close_loop_pair<KT, S, POT>(reinterpret_cast<const float *>(sm.stage[s]), tx, g.first,
+                                            rp2, carry_tile, record);
+            else
+                close_loop_f<KT, S, POT, PAIR>(sm.stage[s], tx, ti, g.first, a.h2f_up, a.hinvf, rp2,
+                                               a, carry_tile, record);
+        } else if (soft && near) {
             // the tile's (1/h_j, zeta_j) straight from global memory (every
             // lane reads the same source: one cached load per warp)
             soft_loop_f<KT, S, POT, PAIR>(sm.stage[s], a.hz + (int64_t)t * S, tx, ti, g.first, thinv,
@@ -1389,33 +1805,7 @@ __device__ __forceinline__ bool mixed_item(
         }
 
         // per-tile corrections for the target velocity, then the carry
-#pragma unroll
-        for (int q = 0; q < KT; ++q) {
-            const float ux = tvf[q][0] - g.cv[0], uy = tvf[q][1] - g.cv[1], uz = tvf[q][2] - g.cv[2];
-            const float Ft = acc[q][ESUM] + (acc[q][TXX] + acc[q][TYY] + acc[q][TZZ]);
-            acc[q][J10 + 0] = fmaf(-ux, Ft, acc[q][J10 + 0]);
-            acc[q][J10 + 1] = fmaf(-uy, Ft, acc[q][J10 + 1]);
-            acc[q][J10 + 2] = fmaf(-uz, Ft, acc[q][J10 + 2]);
-            acc[q][J20 + 0] -= fmaf(acc[q][TXX], ux, fmaf(acc[q][TXY], uy, acc[q][TXZ] * uz));
-            acc[q][J20 + 1] -= fmaf(acc[q][TXY], ux, fmaf(acc[q][TYY], uy, acc[q][TYZ] * uz));
-            acc[q][J20 + 2] -= fmaf(acc[q][TXZ], ux, fmaf(acc[q][TYZ], uy, acc[q][TZZ] * uz));
-            if (SACC) {
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    float *ph = &sm.acc[(2 * c) * BT + q * NT + threadIdx.x];
-                    float *pl = &sm.acc[(2 * c + 1) * BT + q * NT + threadIdx.x];
-                    float h = *ph, l = *pl;
-                    two_sum_acc(h, l, acc[q][c]);
-                    *ph = h;
-                    *pl = l;
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    two_sum_acc(rhi[SACC ? 0 : q][SACC ? 0 : c], rlo[SACC ? 0 : q][SACC ? 0 : c],
-                                acc[q][c]);
-            }
-        }
+        if (!(periodic && close)) carry_tile(acc);
 
         // this warp is done reading stage s; the last warp refills it
         __syncwarp();
@@ -1442,6 +1832,23 @@ __device__ __forceinline__ bool mixed_item(
             for (int c = 0; c < 3; ++c) tx[q][c] = tx_next[q][c];
     }
 
+    // periodic: the FP64 close field (each lane its own list)
+    if constexpr (periodic) {
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            double xi[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                xi[c] = SACC ? sm.x[c * BT + q * NT + threadIdx.x] : xr[SACC ? 0 : q][c];
+            for (int k = 0; k < ncnt[q]; ++k) {
+                double v[kNCPot];
+                close_pair_d<POT>(a, ti[q], nlist[q][k], xi, v);
+#pragma unroll
+                for (int c = 0; c < kNCPot; ++c) nsum[q][c] += v[c];
+            }
+        }
+    }
+
     // warps may leave the tile loop at different tiles: meet here so that
     // every thread returns the same status
     __syncthreads();
@@ -1460,6 +1867,9 @@ __device__ __forceinline__ bool mixed_item(
             } else {
                 sum[c] = __dadd_rn((double)rhi[SACC ? 0 : q][SACC ? 0 : c],
                                    (double)rlo[SACC ? 0 : q][SACC ? 0 : c]);
+            }
+            if constexpr (periodic) {
+                if (c < NC) sum[c] = __dadd_rn(sum[c], nsum[q][c]);
             }
         }
         if (it.split == 1) {
@@ -1499,6 +1909,8 @@ eval_mixed_kernel(const EvalArgs a)
         it.sp = sp;
         it.split = split;
         it.rows = n_tb * BT;
+        it.tile0 = 0;
+        it.pad = 0;
         if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }
@@ -1539,6 +1951,8 @@ eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
         it.sp = 0;
         it.split = 1;
         it.rows = 0;
+        it.tile0 = b.tile_off[s];
+        it.pad = 0;
         if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }
@@ -1592,6 +2006,13 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
                             kWarpBox ? lo[2] : sm.blo[2]};
     const float bhi_r[3] = {kWarpBox ? hi[0] : sm.bhi[0], kWarpBox ? hi[1] : sm.bhi[1],
                             kWarpBox ? hi[2] : sm.bhi[2]};
+    // periodic box: the target's close radius (close_radii; the FP64 pair
+    // terms need no FP64 close field, only the runs)
+    float rc2[1] = {-1.0f};
+    if (MODE == kModePeriodic && i >= 0) {
+        float rp2;
+        close_radii<S, false, false>(a, it, i, xi, rp2, rc2[0]);
+    }
     double hinv_i = 1.0, zeta_i = 0.0;
     float h_block = 0.0f;
     if (MODE == kModeSoft) {
@@ -1625,15 +2046,18 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
     for (int t = t_begin; t < t_end; ++t) {
         const int s = (t - t_begin) % NSTAGE;
         const TileGeom g = a.geo[t];
-        bool near;
+        bool near, close = false;
         if (periodic) {
             float tw[1][3];
             const int64_t ti1[1] = {i};
 #pragma unroll
             for (int c = 0; c < 3; ++c)
                 tw[0][c] = __double2float_rn(wrap_d(__dsub_rn(xi[c], g.c[c]), a.box, a.box_inv));
-            // every FP64 periodic pair is wrapped; this only decides softening
-            near = __syncthreads_or(periodic_special<1>(tw, ti1, g, a.h2f_up, a.box_tie_f)) != 0;
+            // every FP64 periodic pair is wrapped; this decides softening and
+            // the close tiles (summed in runs)
+            const int cls = periodic_class<1>(tw, ti1, g, a.h2f_up, a.box_tie_f, rc2);
+            close = __syncthreads_or((cls & 2) != 0) != 0;
+            near = close || __syncthreads_or((cls & 1) != 0) != 0;
         } else if (soft) {
             const float hm = fmaxf(h_block, a.geo_h[t]);
             near = tile_is_near(blo_r, bhi_r, g, __fmul_ru(hm, hm));
@@ -1655,6 +2079,20 @@ __device__ __forceinline__ bool f64_item(const EvalArgs &a, F64Smem<S> &sm, Ring
         if (soft && near) {
             soft_loop_d<S, POT>(sm.stage[s], sm.stage[s] + S, xi, vr, i, g.first, hinv_i, zeta_i, a,
                                 acc);
+        } else if (periodic && close) {
+            // close tiles: runs of kCloseRun sources, each carried on its own
+            // (acc stays zero)
+            for (int j0 = 0; j0 < S; j0 += kCloseRun) {
+                double racc[kNCPot];
+#pragma unroll
+                for (int c = 0; c < kNCPot; ++c) racc[c] = 0.0;
+                loop_d<kCloseRun, POT, true, true>(sm.stage[s] + j0, sm.stage[s] + S + j0, xi, i,
+                                                   g.first + j0, h2, hinv, racc, a.box, a.box_inv,
+                                                   a.box_tie);
+                target_velocity_d(racc, vr);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) two_sum_acc(shi[c], slo[c], racc[c]);
+            }
         } else {
             if (periodic && !near)
                 loop_d<S, POT, false, true>(sm.stage[s], sm.stage[s] + S, xi, i, g.first, h2, hinv,
@@ -1716,6 +2154,8 @@ eval_f64_kernel(const EvalArgs a)
         it.sp = sp;
         it.split = split;
         it.rows = n_tb * NT;
+        it.tile0 = 0;
+        it.pad = 0;
         if (!f64_item<NT, S, POT, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }
@@ -1749,6 +2189,8 @@ eval_f64_batched_kernel(const EvalArgs a, const BatchView b)
         it.sp = 0;
         it.split = 1;
         it.rows = 0;
+        it.tile0 = b.tile_off[s];
+        it.pad = 0;
         if (!f64_item<NT, S, POT, MODE>(a, sm, ring, it)) break;
         __syncthreads();
     }

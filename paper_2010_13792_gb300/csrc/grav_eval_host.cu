@@ -288,6 +288,7 @@ int eval_single(const char *who, const grav_params *p, bool soft, int64_t n_src,
     a.part_cap_rows = L.part_cap_rows;
     a.pos = pos;
     a.vel = vel;
+    a.mass = mass;
     a.G = p->G;
     a.h = p->h;
     a.sqrt_eta = std::sqrt(p->eta);
@@ -622,6 +623,7 @@ extern "C" int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav
     a.part_cap_rows = 0;
     a.pos = pos;
     a.vel = vel;
+    a.mass = mass;
     a.G = p->G;
     a.h = p->h;
     a.sqrt_eta = std::sqrt(p->eta);

@@ -123,7 +123,9 @@ def test_exact_half_box_ties(n_side, L, precision):
     a rounding of) half a box along some axis, where the two images are
     equally near and rint's ties-to-even decides.  Both sides must pick the
     same image for every such pair: the force would otherwise differ by the
-    difference of the two images' contributions."""
+    difference of the two images' contributions.  The lattice's cubic
+    symmetry cancels most of each tidal sum (sum_j ||T_ij|| / ||T_i|| is about
+    500 on the 8^3 lattice), and the stated bounds hold all the same."""
     pos, vel, mass = ics.zeldovich_box(n_side, L, amplitude=0.0, jitter=0.0)
     ref = O.eval_active(pos, vel, mass, h=0.02, box=L)
     out = run_periodic(pos, vel, mass, None, 0.02, L, precision)
@@ -131,13 +133,11 @@ def test_exact_half_box_ties(n_side, L, precision):
     if precision == grav.F64:
         assert_f64(e)
         return
-    # The lattice's cubic symmetry cancels most of each tidal sum (its
-    # condition number is about 500), so the FP32 tidal error is bounded
-    # against the sum's own scale, sum_j |T_ij|_F = sum_j sqrt(6) m_j / r_ij^3
-    # (no pair is softened here).  A pair taken to the other image flips the
-    # sign of some off-diagonal terms: about 1e-3 of that scale.
-    assert e["acc"][0] <= MIXED_A_MEDIAN and e["acc"][1] <= MIXED_MAX, e["acc"]
-    assert e["jerk"][1] <= MIXED_MAX, e["jerk"]
+    assert_mixed(e)
+    # diagnostic: the error against the sum's own scale, sum_j ||T_ij||_F =
+    # sum_j sqrt(6) m_j / r_ij^3 (no pair is softened here); a pair taken to
+    # the other image would flip the sign of some off-diagonal terms, about
+    # 1e-3 of that scale
     d = pos[None, :, :] - pos[:, None, :]
     d -= L * np.rint(d / L)
     r = np.linalg.norm(d, axis=2)
@@ -146,7 +146,28 @@ def test_exact_half_box_ties(n_side, L, precision):
     scale = (np.sqrt(6.0) * mass[None, :] / r**3).sum(axis=1)
     dt = out["tidal"] - ref["tidal"]
     frob = np.sqrt((dt[:, :3] ** 2).sum(1) + 2.0 * (dt[:, 3:] ** 2).sum(1))
-    assert (frob / scale).max() <= 1e-5, (frob / scale).max()
+    assert (frob / scale).max() <= 1e-7, (frob / scale).max()
+
+
+@pytest.fixture(scope="module")
+def pancake48():
+    """The pancake-shaped 48^3 lattice (one sinusoidal mode of amplitude 0.8,
+    jitter 1% of the spacing) and the oracle at every element."""
+    pos, vel, mass = ics.zeldovich_box(48, 1.0, amplitude=0.8)
+    return pos, vel, mass, O.eval_active(pos, vel, mass, h=2e-3, box=1.0)
+
+
+@pytest.mark.parametrize("precision", [grav.F64, grav.MIXED])
+def test_pancake_lattice_48cubed_every_target(pancake48, precision):
+    """Every one of the 110592 targets of the 48^3 pancake lattice.  Where the
+    lattice is locally undistorted its tidal tensor and jerk nearly cancel:
+    sum_j ||T_ij|| / ||T_i|| reaches about 8000 here, and the mixed kernels'
+    close field (FP64 nearest pairs, FP32 sums in short runs near the
+    target) keeps T, j and a inside the stated bounds at those targets too."""
+    pos, vel, mass, ref = pancake48
+    out = run_periodic(pos, vel, mass, None, 2e-3, 1.0, precision)
+    e = errors(out, ref, np.arange(mass.size))
+    (assert_f64 if precision == grav.F64 else assert_mixed)(e)
 
 
 def test_box_narrower_than_two_softenings_is_rejected():
