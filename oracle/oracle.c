@@ -289,11 +289,36 @@ void oracle_kernel_w(double r, double h, double *w, double *w_r, double *w_h, do
     *psi_h = -dup / (h * h);
 }
 
-/* Per element, at the given supports h_i:
- *   rho[i]   = sum_j m_j W(r_ij, h_i)              (j = i included)
- *   rho_h[i] = sum_j m_j dW(r_ij, h_i)/dh          (j = i included)
- *   psi_h[i] = sum_{j != i} m_j dpsi(r_ij, h_i)/dh
- */
+/* The sums of element i at support h:
+ *   rho   = sum_j m_j W(r_ij, h)               (j = i included)
+ *   rho_h = sum_j m_j dW(r_ij, h)/dh           (j = i included)
+ *   psi_h = sum_{j != i} m_j dpsi(r_ij, h)/dh
+ * (the density of the support constraint, its derivative in h, and the sum
+ * that gives the correction coefficient zeta). */
+static void soft_sums_at(int64_t n, const double *pos, const double *mass, int64_t i, double h,
+                         double *rho, double *rho_h, double *psi_h)
+{
+    nsum sr, srh, sp;
+    memset(&sr, 0, sizeof sr);
+    memset(&srh, 0, sizeof srh);
+    memset(&sp, 0, sizeof sp);
+    for (int64_t j = 0; j < n; ++j) {
+        double d[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1],
+                       pos[3 * j + 2] - pos[3 * i + 2]};
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (r >= h) continue;
+        double w, wr, wh, ph;
+        oracle_kernel_w(r, h, &w, &wr, &wh, &ph);
+        nadd(&sr, mass[j] * w);
+        nadd(&srh, mass[j] * wh);
+        if (j != i) nadd(&sp, mass[j] * ph);
+    }
+    *rho = nval(&sr);
+    *rho_h = nval(&srh);
+    *psi_h = nval(&sp);
+}
+
+/* Per element, the sums of soft_sums_at at the given supports h_i. */
 int oracle_soft_sums(int64_t n, const double *pos, const double *mass, const double *hs,
                      double *rho, double *rho_h, double *psi_h, int nthreads)
 {
@@ -304,24 +329,7 @@ int oracle_soft_sums(int64_t n, const double *pos, const double *mass, const dou
     for (int64_t i = 0; i < n; ++i) {
         double h = hs[i];
         if (!(h > 0.0)) { bad = 1; continue; }
-        nsum sr, srh, sp;
-        memset(&sr, 0, sizeof sr);
-        memset(&srh, 0, sizeof srh);
-        memset(&sp, 0, sizeof sp);
-        for (int64_t j = 0; j < n; ++j) {
-            double d[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1],
-                           pos[3 * j + 2] - pos[3 * i + 2]};
-            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            if (r >= h) continue;
-            double w, wr, wh, ph;
-            oracle_kernel_w(r, h, &w, &wr, &wh, &ph);
-            nadd(&sr, mass[j] * w);
-            nadd(&srh, mass[j] * wh);
-            if (j != i) nadd(&sp, mass[j] * ph);
-        }
-        rho[i] = nval(&sr);
-        rho_h[i] = nval(&srh);
-        psi_h[i] = nval(&sp);
+        soft_sums_at(n, pos, mass, i, h, &rho[i], &rho_h[i], &psi_h[i]);
     }
     return bad ? -1 : 0;
 }
@@ -355,24 +363,7 @@ int oracle_soft_solve(int64_t n, const double *pos, const double *mass, double n
         int done = 0;
         double rho = 0.0, rho_h = 0.0, psi_h = 0.0;
         for (; it < max_iter; ++it) {
-            nsum sr, srh, sp;
-            memset(&sr, 0, sizeof sr);
-            memset(&srh, 0, sizeof srh);
-            memset(&sp, 0, sizeof sp);
-            for (int64_t j = 0; j < n; ++j) {
-                double d[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1],
-                               pos[3 * j + 2] - pos[3 * i + 2]};
-                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-                if (r >= h) continue;
-                double w, wr, wh, ph;
-                oracle_kernel_w(r, h, &w, &wr, &wh, &ph);
-                nadd(&sr, mass[j] * w);
-                nadd(&srh, mass[j] * wh);
-                if (j != i) nadd(&sp, mass[j] * ph);
-            }
-            rho = nval(&sr);
-            rho_h = nval(&srh);
-            psi_h = nval(&sp);
+            soft_sums_at(n, pos, mass, i, h, &rho, &rho_h, &psi_h);
             double vol = 4.0 * ORACLE_PI / 3.0 * h * h * h;
             double F = vol * rho - target;
             if (fabs(F) <= tol * target) { done = 1; break; }

@@ -608,6 +608,43 @@ def pin_soft_solve(lib):
         assert abs(sol["zeta"][i] - float(zeta)) <= 1e-11 * abs(float(zeta)), i
 
 
+def pin_soft_sums(lib):
+    """The per-element sums at given (unsolved) supports: rho = sum_j m_j W
+    and rho_h = sum_j m_j dW/dh with the self term, psi_h = sum_{j != i} m_j
+    dpsi/dh, against a 30-digit brute force over the CAS kernels; rho_h
+    against a central difference of rho in h; and an isolated element, whose
+    sums are its self term alone: rho = m 8/(pi h^3), rho_h = -3 rho / h,
+    psi_h = 0."""
+    import mpmath as mp
+    mp.mp.dps = 30
+    pos, vel, mass = _soft_system(53, 50)
+    pos[49] = [40.0, -40.0, 40.0]                    # far from every other element
+    h = ics.rng(54).uniform(0.3, 0.9, 50)
+    rho, rho_h, psi_h = O.soft_sums(pos, mass, h, lib=lib)
+    for i in (0, 11, 25, 48):
+        r_ = rh_ = ph_ = mp.mpf(0)
+        for j in range(50):
+            r = mp.sqrt(sum((mp.mpf(pos[j, c]) - mp.mpf(pos[i, c])) ** 2 for c in range(3)))
+            w, _, wh, ph = kernel_h_mp(r, h[i])
+            r_ += mass[j] * w
+            rh_ += mass[j] * wh
+            if j != i:
+                ph_ += mass[j] * ph
+        assert abs(rho[i] - float(r_)) <= 1e-13 * float(r_), ("rho", i)
+        assert abs(rho_h[i] - float(rh_)) <= 1e-12 * abs(float(rh_)), ("rho_h", i)
+        assert abs(psi_h[i] - float(ph_)) <= 1e-12 * abs(float(ph_)), ("psi_h", i)
+    eps = 1e-6
+    up = O.soft_sums(pos, mass, h * (1 + eps), lib=lib)[0]
+    dn = O.soft_sums(pos, mass, h * (1 - eps), lib=lib)[0]
+    fd = (up - dn) / (2 * eps * h)
+    sel = np.arange(49)
+    assert np.allclose(rho_h[sel], fd[sel], rtol=1e-6, atol=1e-8 * np.abs(rho_h).max()), "rho_h vs FD"
+    w0 = 8.0 / (np.pi * h[49] ** 3)
+    assert abs(rho[49] - mass[49] * w0) <= 1e-15 * mass[49] * w0
+    assert abs(rho_h[49] + 3.0 * mass[49] * w0 / h[49]) <= 1e-14 * 3.0 * mass[49] * w0 / h[49]
+    assert psi_h[49] == 0.0
+
+
 def pin_soft_energy_gradient(lib):
     """With the correction the acceleration is -grad_i U / m_i, U the potential
     energy with every support re-solved from the constraint (central
@@ -1054,7 +1091,7 @@ ALL_PINS = [
     pin_momentum_balance, pin_trace_density, pin_cube_symmetry, pin_scaling, pin_jerk_fd,
     pin_tidal_fd, pin_tidal_dt, pin_periodic_translation, pin_periodic_two_body,
     pin_periodic_half_box_tie, pin_periodic_open_limit, pin_periodic_derivatives,
-    pin_soft_kernel_vs_cas, pin_soft_constant_h, pin_soft_two_body, pin_soft_solve,
+    pin_soft_kernel_vs_cas, pin_soft_constant_h, pin_soft_two_body, pin_soft_solve, pin_soft_sums,
     pin_soft_energy_gradient, pin_soft_momentum, pin_soft_derivatives,
     pin_tree_theta_zero, pin_tree_order, pin_tree_error_bounds, pin_tree_far_cluster,
     pin_tree_derivatives, pin_tree_relative_criterion,

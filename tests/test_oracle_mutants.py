@@ -65,10 +65,13 @@ MUTANTS = {
     "soft_omega_one": ("double om = 1.0 + h * rho_h / (3.0 * rho);", "double om = 1.0;"),
     "soft_dh_drho": ("if (zeta) zeta[i] = -h * psi_h / (3.0 * rho * om);",
                      "if (zeta) zeta[i] = -h * psi_h / (2.0 * rho * om);"),
-    "soft_rho_no_self": ("                nadd(&sr, mass[j] * w);",
-                         "                if (j != i) nadd(&sr, mass[j] * w);"),
-    "soft_psi_with_self": ("                if (j != i) nadd(&sp, mass[j] * ph);",
-                           "                nadd(&sp, mass[j] * ph);"),
+    "soft_rho_no_self": ("        nadd(&sr, mass[j] * w);",
+                         "        if (j != i) nadd(&sr, mass[j] * w);"),
+    "soft_psi_with_self": ("        if (j != i) nadd(&sp, mass[j] * ph);",
+                           "        nadd(&sp, mass[j] * ph);"),
+    "soft_sums_rho_h_sign": ("        nadd(&srh, mass[j] * wh);", "        nadd(&srh, -mass[j] * wh);"),
+    "soft_sums_psi_h_kernel": ("        if (j != i) nadd(&sp, mass[j] * ph);",
+                               "        if (j != i) nadd(&sp, mass[j] * wh);"),
     "soft_force_own_h": ("f = 0.5 * (fi + fj);", "f = fi;"),
     "soft_g_own_h": ("g = 0.5 * (gi + gj);", "g = gi;"),
     "soft_pot_own_h": ("phi = 0.5 * (pi_ + pj);", "phi = pi_;"),
