@@ -237,6 +237,58 @@ int oracle_eval(int64_t n_src, const double *pos, const double *vel, const doubl
                      tidal, pot, dt_grav, nthreads);
 }
 
+/*
+ * Conditioning of the sums of oracle_eval, the scale against which their
+ * rounding errors grow (the error metric's kappa_i = sum_j |a_ij| / |a_i|):
+ * at the same targets and over the same pairs (j != i, nearest image when
+ * box > 0), per target slot t
+ *   cond[3t]     = G sum_j m_j |f(r)| r                    (sum_j |a_ij|)
+ *   cond[3t + 1] = G sum_j m_j |f v_ji + g (d . v_ji) d|   (sum_j |j_ij|)
+ *   cond[3t + 2] = G sum_j m_j ||f I + g d d^T||_F          (sum_j ||T_ij||_F)
+ * with ||f I + g d d^T||_F^2 = 2 f^2 + (f + g r^2)^2 (eigenvalues f, f and
+ * f + g r^2).  Sums of non-negative terms, added in order.
+ */
+int oracle_conditioning(int64_t n_src, const double *pos, const double *vel, const double *mass,
+                        int64_t n_tgt, const int32_t *idx, double G, double h, double box,
+                        double *cond, int nthreads)
+{
+    if (n_src < 0 || n_tgt < 0 || !(h > 0.0) || box < 0.0) return -1;
+    if (n_tgt > 0 && (!pos || !vel || !mass || !cond)) return -1;
+    set_threads(nthreads);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(|: bad)
+    for (int64_t t = 0; t < n_tgt; ++t) {
+        int64_t i = idx ? (int64_t)idx[t] : t;
+        if (i < 0 || i >= n_src) { bad = 1; continue; }
+        double sa = 0.0, sj = 0.0, st = 0.0;
+        for (int64_t j = 0; j < n_src; ++j) {
+            if (j == i) continue;
+            double d[3], v[3];
+            for (int c = 0; c < 3; ++c) {
+                d[c] = pos[3 * j + c] - pos[3 * i + c];
+                if (box > 0.0) d[c] -= box * nearbyint(d[c] / box);
+                v[c] = vel[3 * j + c] - vel[3 * i + c];
+            }
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double r = sqrt(r2);
+            double f, g, phi;
+            oracle_kernel(r, h, &f, &g, &phi);
+            double m = mass[j];
+            double dv = d[0] * v[0] + d[1] * v[1] + d[2] * v[2];
+            double jv[3];
+            for (int c = 0; c < 3; ++c) jv[c] = f * v[c] + g * dv * d[c];
+            double e3 = f + g * r2;
+            sa += m * fabs(f) * r;
+            sj += m * sqrt(jv[0] * jv[0] + jv[1] * jv[1] + jv[2] * jv[2]);
+            st += m * sqrt(2.0 * f * f + e3 * e3);
+        }
+        cond[3 * t] = G * sa;
+        cond[3 * t + 1] = G * sj;
+        cond[3 * t + 2] = G * st;
+    }
+    return bad ? -1 : 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Adaptive softening (Section 3: fully adaptive softening with the extra     */
 /* force terms of Price & Monaghan 2007 that keep energy conserved).          */

@@ -86,6 +86,10 @@ def load(path: str | None = None):
                                         _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                         _i32p, _dp, _dp, ctypes.c_int]
         lib.oracle_backward.restype = ctypes.c_int
+        lib.oracle_conditioning.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_int64, _i32p,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             _dp, ctypes.c_int]
+        lib.oracle_conditioning.restype = ctypes.c_int
         lib.oracle_kernel_w.argtypes = [ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp]
         lib.oracle_kernel_w.restype = None
         lib.oracle_soft_sums.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
@@ -165,6 +169,29 @@ def eval_active(pos, vel, mass, idx=None, *, G=1.0, h, eta=0.01, want_pot=True,
     if rc != 0:
         raise ValueError("oracle_eval: bad arguments")
     return out
+
+
+def conditioning(pos, vel, mass, idx=None, *, G=1.0, h, box=0.0, nthreads: int = 0, lib=None):
+    """Per target the sums of pair magnitudes sum_j |a_ij|, sum_j |j_ij| and
+    sum_j ||T_ij||_F over the pairs of eval_active; returns an [n_tgt, 3]
+    array.  kappa_i = (that sum) / |a_i| (resp. |j_i|, ||T_i||_F) is the
+    conditioning of target i's sum."""
+    pos = _c(pos, np.float64, (-1, 3))
+    vel = _c(vel, np.float64, (-1, 3))
+    mass = _c(mass, np.float64)
+    n = mass.shape[0]
+    if idx is None:
+        it, n_t = None, n
+    else:
+        it = _c(idx, np.int32)
+        n_t = it.shape[0]
+    cond = np.zeros((n_t, 3))
+    rc = (lib or load()).oracle_conditioning(n, _p(pos, _dp), _p(vel, _dp), _p(mass, _dp), n_t,
+                                             _p(it, _i32p), float(G), float(h), float(box),
+                                             _p(cond, _dp), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_conditioning: bad arguments")
+    return cond
 
 
 def kernel_w(r: float, h: float, lib=None):

@@ -227,6 +227,57 @@ def pin_brute_force(lib):
         _close(o2["acc"], acc[sub], 1e-13, "acc subset")
 
 
+def pin_conditioning(lib):
+    """Sums of pair magnitudes (the conditioning of the error metric): against
+    a 40-digit brute force over the CAS kernels, with ||T_ij||_F formed from
+    the 3x3 matrix entry by entry; on two bodies (one pair) they equal |a|,
+    |j| and ||T||_F of the evaluation; and they bound the evaluation's
+    magnitudes from above (triangle inequality) on a larger system."""
+    import mpmath as mp
+    mp.mp.dps = 40
+    G, h = 1.3, 0.45
+    for seed, n, coinc in ((14, 7, False), (15, 6, True)):
+        pos, vel, mass = _tiny_system(seed, n, 0.6, coincident=coinc)
+        cond = O.conditioning(pos, vel, mass, G=G, h=h, lib=lib)
+        for i in range(n):
+            sa = sj = st = mp.mpf(0)
+            for j in range(n):
+                if j == i:
+                    continue
+                d = [mp.mpf(float(pos[j, c])) - mp.mpf(float(pos[i, c])) for c in range(3)]
+                v = [mp.mpf(float(vel[j, c])) - mp.mpf(float(vel[i, c])) for c in range(3)]
+                r = mp.sqrt(sum(x * x for x in d))
+                f, g, _ = kernel_mp(r, h)
+                m = mp.mpf(float(mass[j]))
+                dv = sum(d[c] * v[c] for c in range(3))
+                sa += m * abs(f) * r
+                sj += m * mp.sqrt(sum((f * v[c] + g * dv * d[c]) ** 2 for c in range(3)))
+                st += m * mp.sqrt(sum((f * (a == b) + g * d[a] * d[b]) ** 2
+                                      for a in range(3) for b in range(3)))
+            ref = [float(G * x) for x in (sa, sj, st)]
+            for k in range(3):
+                assert abs(cond[i, k] - ref[k]) <= 1e-13 * ref[k], (seed, i, k, cond[i, k], ref[k])
+    x = np.array([[0.1, -0.2, 0.3], [0.4, 0.1, 0.2]])
+    v = np.array([[0.2, 0.0, -0.1], [-0.3, 0.5, 0.1]])
+    mass = np.array([0.7, 1.2])
+    for hh in (0.1, 0.9):                       # beyond and inside the support
+        o = O.eval_active(x, v, mass, G=G, h=hh, lib=lib)
+        cond = O.conditioning(x, v, mass, G=G, h=hh, lib=lib)
+        t = o["tidal"]
+        tn = np.sqrt((t[:, :3] ** 2).sum(1) + 2 * (t[:, 3:] ** 2).sum(1))
+        assert np.allclose(cond[:, 0], np.linalg.norm(o["acc"], axis=1), rtol=1e-14)
+        assert np.allclose(cond[:, 1], np.linalg.norm(o["jerk"], axis=1), rtol=1e-14)
+        assert np.allclose(cond[:, 2], tn, rtol=1e-14)
+    pos, vel, mass = ics.plummer(300, seed=16)
+    o = O.eval_active(pos, vel, mass, h=0.05, lib=lib)
+    cond = O.conditioning(pos, vel, mass, h=0.05, lib=lib)
+    t = o["tidal"]
+    tn = np.sqrt((t[:, :3] ** 2).sum(1) + 2 * (t[:, 3:] ** 2).sum(1))
+    assert np.all(cond[:, 0] >= np.linalg.norm(o["acc"], axis=1) * (1 - 1e-13))
+    assert np.all(cond[:, 1] >= np.linalg.norm(o["jerk"], axis=1) * (1 - 1e-13))
+    assert np.all(cond[:, 2] >= tn * (1 - 1e-13))
+
+
 def pin_two_body(lib):
     """Two point masses beyond the softening: Newton's law and its derivatives."""
     G, h = 2.0, 0.1
@@ -1087,7 +1138,8 @@ def pin_adjoint_fd(lib):
 
 
 ALL_PINS = [
-    pin_kernel_vs_cas, pin_kernel_limits, pin_kernel_identity_g, pin_brute_force, pin_two_body,
+    pin_kernel_vs_cas, pin_kernel_limits, pin_kernel_identity_g, pin_brute_force, pin_conditioning,
+    pin_two_body,
     pin_momentum_balance, pin_trace_density, pin_cube_symmetry, pin_scaling, pin_jerk_fd,
     pin_tidal_fd, pin_tidal_dt, pin_periodic_translation, pin_periodic_two_body,
     pin_periodic_half_box_tie, pin_periodic_open_limit, pin_periodic_derivatives,

@@ -88,6 +88,11 @@ MUTANTS = {
                       "kv[i].key = (spread21(q[2]) << 2) | (spread21(q[1]) << 1) | spread21(q[0]);"),
     "tree_rel_power": ("if (accept && rel > 0.0) accept = (G * nd->m) * L2 <= (rel * r2) * r2;",
                        "if (accept && rel > 0.0) accept = (G * nd->m) * L2 <= rel * r2;"),
+    "cond_tidal_cross": ("st += m * sqrt(2.0 * f * f + e3 * e3);", "st += m * sqrt(3.0 * f * f + e3 * e3);"),
+    "cond_jerk_sign": ("for (int c = 0; c < 3; ++c) jv[c] = f * v[c] + g * dv * d[c];",
+                       "for (int c = 0; c < 3; ++c) jv[c] = f * v[c] - g * dv * d[c];"),
+    "cond_self_kept": ("            if (j == i) continue;\n            double d[3], v[3];",
+                       "            double d[3], v[3];"),
     "adj_mass_sign": ("nadd(&mb, -f * da);", "nadd(&mb, f * da);"),
     "adj_g_term": ("nadd(&xb[c], f * ab[c] + g * d[c] * da);", "nadd(&xb[c], f * ab[c]);"),
     "adj_tidal_transposed": ("ta[0] = t6[0] * ak[0] + t6[3] * ak[1] + t6[4] * ak[2];",
