@@ -121,6 +121,28 @@ __device__ __forceinline__ void tma_load_1d(void *dst_smem, const void *src_gmem
         : "memory");
 }
 
+// One elected thread: arm `bar` for both copies' bytes and start two 1-D
+// bulk copies global -> shared that complete on it.
+__device__ __forceinline__ void tma_load_1d_two(void *dst1, const void *src1, uint32_t bytes1,
+                                                void *dst2, const void *src2, uint32_t bytes2,
+                                                uint64_t *bar)
+{
+    uint32_t b = smem_addr(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                 "r"(bytes1 + bytes2)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst1)),
+        "l"(src1), "r"(bytes1), "r"(b)
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst2)),
+        "l"(src2), "r"(bytes2), "r"(b)
+        : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;

@@ -100,7 +100,11 @@ struct EvalArgs {
     double box_tie;               // FP64 path: |d_c| above it re-decides the image by division
     float box_f, box_inv_f;
     float box_tie_f;              // mixed path: |d_c| above it may be an ambiguous image
-    float pad2;
+    float box_lo_f;               // box - box_f, rounded (the low part of the side)
+    // mixed path: the low parts of the packed sources' position and velocity
+    // offsets, per tile kLoPlanes planes of S (offset = high + low to 2^-48)
+    const float *src_lo;
+
     // adaptive softening (kModeSoft): per-element supports h and correction
     // coefficients zeta (zeta nullable: no correction), FP64 by element; the
     // mixed kernels read them per source as (1/h, zeta) in FP32 from hz and
@@ -257,6 +261,9 @@ __device__ __forceinline__ void block_minmax_d(double lo[3], double hi[3], doubl
     __syncthreads();
 }
 
+// Planes of low parts per packed mixed tile: x, y, z.
+constexpr int kLoPlanes = 3;
+
 // One CTA of S threads packs one tile holding the sources [first, end).
 // MIXED: tile = [S x float4 (offset, m)][S x float4 (v', 0)] (v' = v - cv
 // when VOFF, else v); F64: tile = [S x D4 (x, m)][S x D4 (v, 0)].  Padding
@@ -268,7 +275,7 @@ __device__ __forceinline__ void pack_tile(int t, int64_t first, int64_t end,
                                           const double *__restrict__ vel,
                                           const double *__restrict__ mass,
                                           TileGeom *__restrict__ geo, void *__restrict__ src,
-                                          int32_t *flags)
+                                          int32_t *flags, float *__restrict__ src_lo = nullptr)
 {
     __shared__ double slo[3], shi[3], svlo[3], svhi[3];
     const int j = threadIdx.x;
@@ -307,6 +314,20 @@ __device__ __forceinline__ void pack_tile(int t, int64_t first, int64_t end,
     double cc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) cc[c] = __dmul_rn(0.5, __dadd_rn(slo[c], shi[c]));
+    if (MIXED && src_lo) {
+        // low parts of the FP32 position offsets (zero for padding), planes
+        // [x y z] of S each
+        float *lo_t = src_lo + (int64_t)t * kLoPlanes * S;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float lx = 0.0f;
+            if (ok) {
+                const double d = __dsub_rn(x[c], cc[c]);
+                lx = __double2float_rn(__dsub_rn(d, (double)__double2float_rn(d)));
+            }
+            lo_t[c * S + j] = lx;
+        }
+    }
     if (MIXED && PAIR) {
         // paired layout: for source j = 2k + h, floats
         //   [4k + h] x, [4k + 2 + h] y          (S/2 float4: x0 x1 y0 y1)
@@ -380,11 +401,12 @@ template <int S, bool MIXED, bool VOFF, bool PAIR = false>
 __global__ void __launch_bounds__(S)
 pack_tiles_kernel(int64_t n_src, const double *__restrict__ pos, const double *__restrict__ vel,
                   const double *__restrict__ mass, TileGeom *__restrict__ geo, void *__restrict__ src,
-                  int32_t *flags)
+                  int32_t *flags, float *__restrict__ src_lo = nullptr)
 {
     const int64_t first = (int64_t)blockIdx.x * S;
     const int64_t end = first + S < n_src ? first + S : n_src;
-    pack_tile<S, MIXED, VOFF, PAIR>(blockIdx.x, first, end, pos, vel, mass, geo, src, flags);
+    pack_tile<S, MIXED, VOFF, PAIR>(blockIdx.x, first, end, pos, vel, mass, geo, src, flags,
+                                    src_lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -467,48 +489,6 @@ __device__ __forceinline__ void far_loop_f(const float4 *__restrict__ sp,
     }
 }
 
-// Softened loop: cubic-spline kernel inside h, self pair excluded by index,
-// E collects m f - m g' r^2 of the softened pairs.
-template <int KT, int S, bool POT>
-__device__ __forceinline__ void near_loop_f(const float4 *__restrict__ sp,
-                                            const float4 *__restrict__ sv, const float tx[KT][3],
-                                            const int64_t ti[KT], int64_t jbase, float h2,
-                                            float hinv, float acc[KT][kNCPot])
-{
-    const float hinv3 = hinv * hinv * hinv;
-    const float hinv5 = hinv3 * hinv * hinv;
-#pragma unroll 2
-    for (int j = 0; j < S; ++j) {
-        const float4 p = sp[j];
-        const float4 v = sv[j];
-        const int64_t jg = jbase + j;
-#pragma unroll
-        for (int q = 0; q < KT; ++q) {
-            float dx = p.x - tx[q][0], dy = p.y - tx[q][1], dz = p.z - tx[q][2];
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            float ri = rsqrt_sfu(r2);
-            float ri2 = ri * ri;
-            float mp = p.w * ri;
-            float mf = mp * ri2;
-            float mg = mf * ri2;
-            if (r2 < h2) {
-                float F, Gp, P;
-                spline_kernel<float>(sqrtf(r2) * hinv, F, Gp, P);
-                mf = p.w * F * hinv3;
-                mg = p.w * Gp * hinv5;
-                mp = p.w * P * hinv;
-                if (jg == ti[q]) {
-                    mf = 0.0f;
-                    mg = 0.0f;
-                    mp = 0.0f;
-                }
-                acc[q][ESUM] += fmaf(-mg, r2, mf);
-            }
-            accumulate_f<KT, POT>(acc, q, dx, dy, dz, v.x, v.y, v.z, mf, mg, mp);
-        }
-    }
-}
-
 // Paired layout, Newtonian loop: two sources per packed FP32x2 instruction
 // (fma/add/mul .f32x2), so one issue slot does the work of two pairs; the
 // SFU rsqrt runs per source.  Lane 0 sums the even sources, lane 1 the odd.
@@ -570,48 +550,6 @@ __device__ __forceinline__ void far_loop_pair(const float *__restrict__ tile, co
     }
 }
 
-// Paired layout, softened loop: one source at a time (scalar).
-template <int KT, int S, bool POT>
-__device__ __forceinline__ void near_loop_pair(const float *__restrict__ tile, const float tx[KT][3],
-                                               const int64_t ti[KT], int64_t jbase, float h2,
-                                               float hinv, float acc[KT][kNCPot])
-{
-    const float hinv3 = hinv * hinv * hinv;
-    const float hinv5 = hinv3 * hinv * hinv;
-#pragma unroll 2
-    for (int j = 0; j < S; ++j) {
-        const int k = j >> 1, h = j & 1;
-        const float x = tile[4 * k + h], y = tile[4 * k + 2 + h];
-        const float z = tile[2 * S + 4 * k + h], m = tile[2 * S + 4 * k + 2 + h];
-        const float vx = tile[4 * S + 4 * k + h], vy = tile[4 * S + 4 * k + 2 + h];
-        const float vz = tile[6 * S + 2 * k + h];
-#pragma unroll
-        for (int q = 0; q < KT; ++q) {
-            float dx = x - tx[q][0], dy = y - tx[q][1], dz = z - tx[q][2];
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            float ri = rsqrt_sfu(r2);
-            float ri2 = ri * ri;
-            float mp = m * ri;
-            float mf = mp * ri2;
-            float mg = mf * ri2;
-            if (r2 < h2) {
-                float F, Gp, P;
-                spline_kernel<float>(sqrtf(r2) * hinv, F, Gp, P);
-                mf = m * F * hinv3;
-                mg = m * Gp * hinv5;
-                mp = m * P * hinv;
-                if (jbase + j == ti[q]) {
-                    mf = 0.0f;
-                    mg = 0.0f;
-                    mp = 0.0f;
-                }
-                acc[q][ESUM] += fmaf(-mg, r2, mf);
-            }
-            accumulate_f<KT, POT>(acc, q, dx, dy, dz, vx, vy, vz, mf, mg, mp);
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Periodic box (nearest periodic image)
 // ---------------------------------------------------------------------------
@@ -644,6 +582,16 @@ __device__ __forceinline__ double nearest_image_d(double xj, double xi, double b
     return fabs(w) > tie ? nearest_image_exact(xj, xi, box) : w;
 }
 
+// Tiles whose FP32 position offsets (from the tile centre, rounded to half
+// an ulp) could make a separation wrong by more than about 8e-6 of itself:
+// a target within C (|t| + |e|) of the tile's box, t its offset from the
+// tile centre and e the box's half-diagonal, C = 2^-24 / 8e-6 ~ 1/128 --
+// over a warp, a box gap below C / (1 - C) (diagonal of the warp's box +
+// diagonal of the tile's).  Compact tiles meet it only next to the targets; a tile
+// that spans a jump of the element order (a core and a distant outskirt in
+// one Morton range) meets it wherever its members are.
+constexpr float kLooseC = 1.0f / 128.0f;
+
 // Per target and tile of the periodic box: bit 0 when the tile needs the
 // general loop (softened pairs, or sources that might not lie within `tie`,
 // a little under half a box, of the target's image of the tile centre), bit
@@ -660,6 +608,7 @@ __device__ __forceinline__ int periodic_class(const float t[KT][3], const int64_
     float e[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) e[c] = __fmul_ru(0.5f, __fsub_ru(g.hi[c], g.lo[c]));
+    const float e2 = fmaf(e[0], e[0], fmaf(e[1], e[1], e[2] * e[2]));
     int cls = 0;
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
@@ -673,9 +622,84 @@ __device__ __forceinline__ int periodic_class(const float t[KT][3], const int64_
             d2 = __fmaf_rd(gap, gap, d2);
         }
         if (d2 < h2_up) cls |= 1;
-        if (d2 < rc2[q]) cls |= 2;
+        // the close radius, or the FP32 offsets' reach (kLooseC): with
+        // (|t| + |e|)^2 <= 2 (t.t + e.e)
+        const float t2 = fmaf(t[q][0], t[q][0], fmaf(t[q][1], t[q][1], t[q][2] * t[q][2]));
+        const float loose2 = (2.0f * kLooseC * kLooseC) * (t2 + e2);
+        if (d2 < fmaxf(rc2[q], loose2)) cls |= 2;
     }
     return cls;
+}
+
+// Squared gap between two outward-rounded boxes (rounded down: any doubt
+// means "nearer").
+__device__ __forceinline__ float box_gap2(const float blo[3], const float bhi[3], const TileGeom &g)
+{
+    float d2 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(g.lo[c], bhi[c]), __fsub_rd(blo[c], g.hi[c])));
+        d2 = __fmaf_rd(gap, gap, d2);
+    }
+    return d2;
+}
+
+// Squared diagonal of a box.
+__device__ __forceinline__ float box_diag2(const float lo[3], const float hi[3])
+{
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float e = hi[c] - lo[c];
+        s = fmaf(e, e, s);
+    }
+    return s;
+}
+
+// Which loop a tile takes for one warp's targets; the force kernels and the
+// close-tile kernel decide alike (warp-uniform results).  near: some pair
+// may lie inside the softening (in a periodic box: or reach half a box);
+// close: the tile is summed by the close loops -- in a periodic box when it
+// comes within a target's close radius or the FP32 offsets' reach
+// (periodic_class), with open boundaries when it lies inside h of the warp's
+// box or within the offsets' reach over it, gap < C/(1-C) (diag_w + diag_t),
+// squared with (a+b)^2 <= 2 (a^2 + b^2) (diag2_w: the warp box's squared
+// diagonal).
+template <int KT, int MODE>
+__device__ __forceinline__ void classify_tile(const EvalArgs &a, const TileGeom &g,
+                                              const float tx[KT][3], const int64_t ti[KT],
+                                              const float blo[3], const float bhi[3],
+                                              float diag2_w, const float rc2[KT], float h2_tile,
+                                              bool &near, bool &close)
+{
+    close = false;
+    if (MODE == kModePeriodic) {
+        const int cls = periodic_class<KT>(tx, ti, g, a.h2f_up, a.box_tie_f, rc2);
+        close = __any_sync(0xffffffffu, (cls & 2) != 0);
+        near = __any_sync(0xffffffffu, (cls & 1) != 0);
+    } else if (MODE == kModeSoft) {
+        near = tile_is_near(blo, bhi, g, h2_tile);
+    } else {
+        const float g2 = box_gap2(blo, bhi, g);
+        near = !(g2 >= a.h2f_up);
+        constexpr float kL = kLooseC / (1.0f - kLooseC);
+        close = near || g2 < (2.0f * kL * kL) * (diag2_w + box_diag2(g.lo, g.hi));
+    }
+}
+
+// The low parts of a target's position offset to a tile's centre (tx the
+// high parts, formed the same way: FP64 difference, wrapped in a periodic
+// box, rounded once).
+__device__ __forceinline__ void target_low_parts(const EvalArgs &a, const TileGeom &g,
+                                                 const double x[3], const float tx[3],
+                                                 bool periodic, float tl[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double d = __dsub_rn(x[c], g.c[c]);
+        if (periodic) d = wrap_d(d, a.box, a.box_inv);
+        tl[c] = __double2float_rn(__dsub_rn(d, (double)tx[c]));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -703,18 +727,20 @@ constexpr int kCloseList = 64;
 constexpr float kCloseRp = 2.4f;
 constexpr float kCloseRc = 4.5f;
 
-// One pair of the close field in FP64 (target i at FP64 position xi, source
-// j != i): the pair's contributions to the accumulated sums, in the slots of
-// the mixed path (A, J1, J2 with the pair's own relative velocity, E = m f -
-// m g' r^2, Tp, and P), nearest image decided as the FP64 kernels decide it.
-template <bool POT>
+// One listed pair in FP64 (target i at FP64 position xi, source j != i): the
+// pair's contributions to the accumulated sums, in the slots of the mixed
+// path (A, J1, J2 with the pair's own relative velocity, E = m f - m g' r^2,
+// Tp, and P); in a periodic box the nearest image decided as the FP64
+// kernels decide it.
+template <bool POT, bool PERIODIC>
 __device__ __forceinline__ void close_pair_d(const EvalArgs &a, int64_t i, int64_t j,
                                              const double xi[3], double out[kNCPot])
 {
     double d[3], v[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        d[c] = nearest_image_d(a.pos[3 * j + c], xi[c], a.box, a.box_inv, a.box_tie);
+        d[c] = PERIODIC ? nearest_image_d(a.pos[3 * j + c], xi[c], a.box, a.box_inv, a.box_tie)
+                        : a.pos[3 * j + c] - xi[c];
         v[c] = a.vel[3 * j + c] - a.vel[3 * i + c];
     }
     const double m = a.mass[j];
@@ -828,6 +854,84 @@ __device__ __forceinline__ void periodic_loop_f(const float4 *__restrict__ stage
     }
 }
 
+// Near tiles with open boundaries (inside h of the warp's box, or within the
+// FP32 offsets' reach: classify_tile): the softened scalar loop (the cubic
+// spline inside h, the self pair excluded) with separations from both
+// offsets' low parts, d = (s - t) + (s_lo - t_lo) (lo: the tile's planes of
+// low parts; tl: the targets'), good to a few units in the last place of d
+// however far the tile centre lies.  Velocities enter relative to the tile's
+// velocity centre (the per-tile correction applies), good to about 2^-24 of
+// those, which is not enough for a close pair moving with its target (w ~ u,
+// |w - u| << |w| + |u|) whose jerk term outweighs the rest of the target's
+// sum.  So every pair within 2h of its target (where a single pair can
+// dominate: inside the spline's support and just past it) is offered to
+// record(q, j) and, when taken, left out of the FP32 sums: it is summed in
+// FP64 after the item's tiles, its relative velocity formed from the FP64
+// velocities.
+template <int KT, int S, bool POT, bool PAIR, typename Record>
+__device__ __forceinline__ void near_loop_rec(const float4 *__restrict__ stage,
+                                              const float *__restrict__ lo, const float tx[KT][3],
+                                              const float tl[KT][3], const int64_t ti[KT],
+                                              int64_t jbase, float h2, float hinv,
+                                              float acc[KT][kNCPot], Record &record)
+{
+    const float hinv3 = hinv * hinv * hinv;
+    const float hinv5 = hinv3 * hinv * hinv;
+    const float *tile = reinterpret_cast<const float *>(stage);
+#pragma unroll 2
+    for (int j = 0; j < S; ++j) {
+        float x, y, z, m, wx, wy, wz;
+        if (PAIR) {
+            const int k = j >> 1, h = j & 1;
+            x = tile[4 * k + h];
+            y = tile[4 * k + 2 + h];
+            z = tile[2 * S + 4 * k + h];
+            m = tile[2 * S + 4 * k + 2 + h];
+            wx = tile[4 * S + 4 * k + h];
+            wy = tile[4 * S + 4 * k + 2 + h];
+            wz = tile[6 * S + 2 * k + h];
+        } else {
+            const float4 p = stage[j], v = stage[S + j];
+            x = p.x;
+            y = p.y;
+            z = p.z;
+            m = p.w;
+            wx = v.x;
+            wy = v.y;
+            wz = v.z;
+        }
+        const float xl = lo[j], yl = lo[S + j], zl = lo[2 * S + j];
+        const int64_t jg = jbase + j;
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const float dx = (x - tx[q][0]) + (xl - tl[q][0]);
+            const float dy = (y - tx[q][1]) + (yl - tl[q][1]);
+            const float dz = (z - tx[q][2]) + (zl - tl[q][2]);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 < 4.0f * h2 && m != 0.0f && ti[q] >= 0 && jg != ti[q] && record(q, jg)) continue;
+            const float ri = rsqrt_sfu(r2);
+            const float ri2 = ri * ri;
+            float mp = m * ri;
+            float mf = mp * ri2;
+            float mg = mf * ri2;
+            if (r2 < h2) {
+                float F, Gp, P;
+                spline_kernel<float>(sqrtf(r2) * hinv, F, Gp, P);
+                mf = m * F * hinv3;
+                mg = m * Gp * hinv5;
+                mp = m * P * hinv;
+                if (jg == ti[q]) {
+                    mf = 0.0f;
+                    mg = 0.0f;
+                    mp = 0.0f;
+                }
+                acc[q][ESUM] += fmaf(-mg, r2, mf);
+            }
+            accumulate_f<KT, POT>(acc, q, dx, dy, dz, wx, wy, wz, mf, mg, mp);
+        }
+    }
+}
+
 // 1/sqrt(x) refined by one Newton-Raphson step on f(y) = y^-2 - x from the
 // SFU estimate y0: y1 = y0 + (y0 / 2) (1 - x y0^2), which roughly halves the
 // relative error of y0 (the close loops only: their pair terms feed the
@@ -847,17 +951,24 @@ __device__ __forceinline__ float2 rsqrt_refined2(float2 x)
     return __ffma2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), y), e, y);
 }
 
-// Close tiles of the periodic box (see close_radii) that may need wrapping or
-// hold softened or self pairs: the general loop's pair arithmetic (nearest
-// image in FP32, FP64 re-formation near half a box, the cubic spline inside
-// h, the self pair excluded) over runs of kCloseRun sources, each run's FP32
-// sums handed to carry(acc) (the per-tile target-velocity correction and the
-// compensated carry).  A pair closer than R_p (squared: rp2) is offered to
+// Close tiles (see close_radii and the close-tile kernel) that may hold
+// softened or self pairs or, in a periodic box, need wrapping: the general
+// loop's pair arithmetic (in a periodic box the nearest image in FP32 and the
+// FP64 re-formation near half a box; the cubic spline inside h; the self
+// pair excluded) over runs of RUN sources, each run's FP32 sums handed to
+// carry(acc) (the per-tile target-velocity correction and the compensated
+// carry).  Separations take the low parts of both offsets, d = (s - t) +
+// (s_lo - t_lo) (lo: the tile's planes of low parts; tl: the targets'),
+// good to a few units in the last place of d however far the tile centre
+// lies.  A pair
+// closer than R_p (squared: rp2; periodic box only) is offered to
 // record(q, j), which lists it for the FP64 close field and returns true, or
 // returns false when the list is full and the pair stays in the FP32 sums.
-template <int KT, int S, bool POT, bool PAIR, typename Carry, typename Record>
+template <int KT, int S, int RUN, bool POT, bool PAIR, bool PERIODIC, typename Carry,
+          typename Record>
 __device__ __forceinline__ void close_loop_f(const float4 *__restrict__ stage,
-                                             const float tx[KT][3], const int64_t ti[KT],
+                                             const float *__restrict__ lo, const float tx[KT][3],
+                                             const float tl[KT][3], const int64_t ti[KT],
                                              int64_t jbase, float h2, float hinv,
                                              const float rp2[KT], const EvalArgs &a, Carry &carry,
                                              Record &record)
@@ -867,49 +978,62 @@ __device__ __forceinline__ void close_loop_f(const float4 *__restrict__ stage,
     const float hinv5 = hinv3 * hinv * hinv;
     const float *tile = reinterpret_cast<const float *>(stage);
 #pragma unroll 1
-    for (int j0 = 0; j0 < S; j0 += kCloseRun) {
+    for (int j0 = 0; j0 < S; j0 += RUN) {
         float acc[KT][kNCPot];
 #pragma unroll
         for (int q = 0; q < KT; ++q)
 #pragma unroll
             for (int c = 0; c < kNCPot; ++c) acc[q][c] = 0.0f;
 #pragma unroll 2
-        for (int j = j0; j < j0 + kCloseRun; ++j) {
-            float x, y, z, m, vx, vy, vz;
+        for (int j = j0; j < j0 + RUN; ++j) {
+            float x, y, z, m, wx, wy, wz;
             if (PAIR) {
                 const int k = j >> 1, h = j & 1;
                 x = tile[4 * k + h];
                 y = tile[4 * k + 2 + h];
                 z = tile[2 * S + 4 * k + h];
                 m = tile[2 * S + 4 * k + 2 + h];
-                vx = tile[4 * S + 4 * k + h];
-                vy = tile[4 * S + 4 * k + 2 + h];
-                vz = tile[6 * S + 2 * k + h];
+                wx = tile[4 * S + 4 * k + h];
+                wy = tile[4 * S + 4 * k + 2 + h];
+                wz = tile[6 * S + 2 * k + h];
             } else {
                 const float4 p = stage[j], v = stage[S + j];
                 x = p.x;
                 y = p.y;
                 z = p.z;
                 m = p.w;
-                vx = v.x;
-                vy = v.y;
-                vz = v.z;
+                wx = v.x;
+                wy = v.y;
+                wz = v.z;
             }
             const int64_t jg = jbase + j;
+            const float xl = lo[j], yl = lo[S + j], zl = lo[2 * S + j];
 #pragma unroll
             for (int q = 0; q < KT; ++q) {
                 float dx = x - tx[q][0], dy = y - tx[q][1], dz = z - tx[q][2];
-                dx = fmaf(-box, rintf(dx * box_inv), dx);
-                dy = fmaf(-box, rintf(dy * box_inv), dy);
-                dz = fmaf(-box, rintf(dz * box_inv), dz);
-                if (fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) > tie && m != 0.0f && ti[q] >= 0) {
+                float lx = xl - tl[q][0], ly = yl - tl[q][1], lz = zl - tl[q][2];
+                if (PERIODIC) {
+                    const float kx = rintf(dx * box_inv), ky = rintf(dy * box_inv),
+                                kz = rintf(dz * box_inv);
+                    dx = fmaf(-box, kx, dx);
+                    dy = fmaf(-box, ky, dy);
+                    dz = fmaf(-box, kz, dz);
+                    lx = fmaf(-a.box_lo_f, kx, lx);
+                    ly = fmaf(-a.box_lo_f, ky, ly);
+                    lz = fmaf(-a.box_lo_f, kz, lz);
+                }
+                dx += lx;
+                dy += ly;
+                dz += lz;
+                if (PERIODIC && fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) > tie && m != 0.0f &&
+                    ti[q] >= 0) {
                     const double *pi = a.pos + 3 * ti[q], *pj = a.pos + 3 * jg;
                     dx = __double2float_rn(nearest_image_d(pj[0], pi[0], a.box, a.box_inv, a.box_tie));
                     dy = __double2float_rn(nearest_image_d(pj[1], pi[1], a.box, a.box_inv, a.box_tie));
                     dz = __double2float_rn(nearest_image_d(pj[2], pi[2], a.box, a.box_inv, a.box_tie));
                 }
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (r2 < rp2[q] && jg != ti[q] && m != 0.0f && record(q, jg)) continue;
+                if (PERIODIC && r2 < rp2[q] && jg != ti[q] && m != 0.0f && record(q, jg)) continue;
                 const float ri = rsqrt_refined(r2);
                 const float ri2 = ri * ri;
                 float mp = m * ri;
@@ -928,51 +1052,80 @@ __device__ __forceinline__ void close_loop_f(const float4 *__restrict__ stage,
                     }
                     acc[q][ESUM] += fmaf(-mg, r2, mf);
                 }
-                accumulate_f<KT, POT>(acc, q, dx, dy, dz, vx, vy, vz, mf, mg, mp);
+                accumulate_f<KT, POT>(acc, q, dx, dy, dz, wx, wy, wz, mf, mg, mp);
             }
         }
         carry(acc);
     }
 }
 
-// Close tiles that need no wrapping and hold no softened or self pair (no
-// target of the warp flags the tile in bit 0 of periodic_class): the paired
-// Newtonian loop of far_loop_pair, with pairs closer than R_p offered to
-// record(q, j) (and left out of the sums when it takes them) and the sums
-// carried every kCloseRun sources.
-template <int KT, int S, bool POT, typename Carry, typename Record>
-__device__ __forceinline__ void close_loop_pair(const float *__restrict__ tile, const float tx[KT][3],
-                                                int64_t jbase, const float rp2[KT], Carry &carry,
-                                                Record &record)
+// Sums of one pair of sources (FP32x2 lanes) for one target: A, J1', J2',
+// Tp (and P), as in far_loop_pair.
+template <bool POT>
+__device__ __forceinline__ void accumulate_pair(float2 acc[kNCPot], float2 dx, float2 dy, float2 dz,
+                                                float2 vx, float2 vy, float2 vz, float2 mf,
+                                                float2 mg, float2 mp)
+{
+    acc[A0 + 0] = __ffma2_rn(mf, dx, acc[A0 + 0]);
+    acc[A0 + 1] = __ffma2_rn(mf, dy, acc[A0 + 1]);
+    acc[A0 + 2] = __ffma2_rn(mf, dz, acc[A0 + 2]);
+    acc[J10 + 0] = __ffma2_rn(mf, vx, acc[J10 + 0]);
+    acc[J10 + 1] = __ffma2_rn(mf, vy, acc[J10 + 1]);
+    acc[J10 + 2] = __ffma2_rn(mf, vz, acc[J10 + 2]);
+    float2 dv = __fmul2_rn(dz, vz);
+    dv = __ffma2_rn(dy, vy, dv);
+    dv = __ffma2_rn(dx, vx, dv);
+    const float2 gx = __fmul2_rn(mg, dx), gy = __fmul2_rn(mg, dy), gz = __fmul2_rn(mg, dz);
+    acc[TXX] = __ffma2_rn(gx, dx, acc[TXX]);
+    acc[TYY] = __ffma2_rn(gy, dy, acc[TYY]);
+    acc[TZZ] = __ffma2_rn(gz, dz, acc[TZZ]);
+    acc[TXY] = __ffma2_rn(gx, dy, acc[TXY]);
+    acc[TXZ] = __ffma2_rn(gx, dz, acc[TXZ]);
+    acc[TYZ] = __ffma2_rn(gy, dz, acc[TYZ]);
+    acc[J20 + 0] = __ffma2_rn(gx, dv, acc[J20 + 0]);
+    acc[J20 + 1] = __ffma2_rn(gy, dv, acc[J20 + 1]);
+    acc[J20 + 2] = __ffma2_rn(gz, dv, acc[J20 + 2]);
+    if (POT) acc[PSUM] = __fadd2_rn(acc[PSUM], mp);
+}
+
+// Close tiles of the periodic box that need no wrapping and hold no softened
+// or self pair (no target of the warp flags the tile in bit 0 of
+// periodic_class): the paired loop of far_loop_pair with separations from
+// both offsets' low parts (as in close_loop_f), pairs closer than R_p offered
+// to record(q, j) and left out of the sums when it takes them, and the sums
+// carried every RUN sources.
+template <int KT, int S, int RUN, bool POT, typename Carry, typename Record>
+__device__ __forceinline__ void close_loop_pair(const float *__restrict__ tile,
+                                                const float *__restrict__ lo, const float tx[KT][3],
+                                                const float tl[KT][3], int64_t jbase,
+                                                const float rp2[KT], Carry &carry, Record &record)
 {
     const float4 *P0 = reinterpret_cast<const float4 *>(tile);
     const float4 *P1 = P0 + S / 2;
     const float4 *V0 = P1 + S / 2;
     const float2 *V1 = reinterpret_cast<const float2 *>(V0 + S / 2);
-    float2 ntx[KT], nty[KT], ntz[KT];
-#pragma unroll
-    for (int q = 0; q < KT; ++q) {
-        ntx[q] = make_float2(-tx[q][0], -tx[q][0]);
-        nty[q] = make_float2(-tx[q][1], -tx[q][1]);
-        ntz[q] = make_float2(-tx[q][2], -tx[q][2]);
-    }
+    const float2 *L2 = reinterpret_cast<const float2 *>(lo);      // 3 planes of S/2 pairs
 #pragma unroll 1
-    for (int k0 = 0; k0 < S / 2; k0 += kCloseRun / 2) {
+    for (int k0 = 0; k0 < S / 2; k0 += RUN / 2) {
         float2 acc2[KT][kNCPot];
 #pragma unroll
         for (int q = 0; q < KT; ++q)
 #pragma unroll
             for (int c = 0; c < kNCPot; ++c) acc2[q][c] = make_float2(0.0f, 0.0f);
 #pragma unroll 2
-        for (int k = k0; k < k0 + kCloseRun / 2; ++k) {
+        for (int k = k0; k < k0 + RUN / 2; ++k) {
             const float4 p0 = P0[k], p1 = P1[k], v0 = V0[k];
             const float2 vz = V1[k];
             const float2 vx = make_float2(v0.x, v0.y), vy = make_float2(v0.z, v0.w);
+            const float2 lx = L2[k], ly = L2[S / 2 + k], lz = L2[S + k];
 #pragma unroll
             for (int q = 0; q < KT; ++q) {
-                const float2 dx = __fadd2_rn(make_float2(p0.x, p0.y), ntx[q]);
-                const float2 dy = __fadd2_rn(make_float2(p0.z, p0.w), nty[q]);
-                const float2 dz = __fadd2_rn(make_float2(p1.x, p1.y), ntz[q]);
+                const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(p0.x, p0.y), make_float2(-tx[q][0], -tx[q][0])),
+                                             __fadd2_rn(lx, make_float2(-tl[q][0], -tl[q][0])));
+                const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(p0.z, p0.w), make_float2(-tx[q][1], -tx[q][1])),
+                                             __fadd2_rn(ly, make_float2(-tl[q][1], -tl[q][1])));
+                const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(p1.x, p1.y), make_float2(-tx[q][2], -tx[q][2])),
+                                             __fadd2_rn(lz, make_float2(-tl[q][2], -tl[q][2])));
                 float2 r2 = __fmul2_rn(dz, dz);
                 r2 = __ffma2_rn(dy, dy, r2);
                 r2 = __ffma2_rn(dx, dx, r2);
@@ -984,26 +1137,7 @@ __device__ __forceinline__ void close_loop_pair(const float *__restrict__ tile, 
                 const float2 mp = __fmul2_rn(m, ri);
                 const float2 mf = __fmul2_rn(mp, ri2);
                 const float2 mg = __fmul2_rn(mf, ri2);
-                acc2[q][A0 + 0] = __ffma2_rn(mf, dx, acc2[q][A0 + 0]);
-                acc2[q][A0 + 1] = __ffma2_rn(mf, dy, acc2[q][A0 + 1]);
-                acc2[q][A0 + 2] = __ffma2_rn(mf, dz, acc2[q][A0 + 2]);
-                acc2[q][J10 + 0] = __ffma2_rn(mf, vx, acc2[q][J10 + 0]);
-                acc2[q][J10 + 1] = __ffma2_rn(mf, vy, acc2[q][J10 + 1]);
-                acc2[q][J10 + 2] = __ffma2_rn(mf, vz, acc2[q][J10 + 2]);
-                float2 dv = __fmul2_rn(dz, vz);
-                dv = __ffma2_rn(dy, vy, dv);
-                dv = __ffma2_rn(dx, vx, dv);
-                const float2 gx = __fmul2_rn(mg, dx), gy = __fmul2_rn(mg, dy), gz = __fmul2_rn(mg, dz);
-                acc2[q][TXX] = __ffma2_rn(gx, dx, acc2[q][TXX]);
-                acc2[q][TYY] = __ffma2_rn(gy, dy, acc2[q][TYY]);
-                acc2[q][TZZ] = __ffma2_rn(gz, dz, acc2[q][TZZ]);
-                acc2[q][TXY] = __ffma2_rn(gx, dy, acc2[q][TXY]);
-                acc2[q][TXZ] = __ffma2_rn(gx, dz, acc2[q][TXZ]);
-                acc2[q][TYZ] = __ffma2_rn(gy, dz, acc2[q][TYZ]);
-                acc2[q][J20 + 0] = __ffma2_rn(gx, dv, acc2[q][J20 + 0]);
-                acc2[q][J20 + 1] = __ffma2_rn(gy, dv, acc2[q][J20 + 1]);
-                acc2[q][J20 + 2] = __ffma2_rn(gz, dv, acc2[q][J20 + 2]);
-                if (POT) acc2[q][PSUM] = __fadd2_rn(acc2[q][PSUM], mp);
+                accumulate_pair<POT>(acc2[q], dx, dy, dz, vx, vy, vz, mf, mg, mp);
             }
         }
         float acc[KT][kNCPot];
@@ -1455,7 +1589,8 @@ template <int S, bool MIXED, bool VOFF, bool PAIR>
 __global__ void __launch_bounds__(S)
 pack_tiles_batched_kernel(const BatchView b, const double *__restrict__ pos,
                           const double *__restrict__ vel, const double *__restrict__ mass,
-                          TileGeom *__restrict__ geo, void *__restrict__ src, int32_t *flags)
+                          TileGeom *__restrict__ geo, void *__restrict__ src, int32_t *flags,
+                          float *__restrict__ src_lo)
 {
     const int t = blockIdx.x;
     if (t >= b.hdr->total_tiles) return;
@@ -1470,7 +1605,7 @@ pack_tiles_batched_kernel(const BatchView b, const double *__restrict__ pos,
     const int64_t first = b.sys[lo].offset + (int64_t)(t - b.tile_off[lo]) * S;
     const int64_t sys_end = b.sys[lo].offset + b.sys[lo].n;
     const int64_t end = first + S < sys_end ? first + S : sys_end;
-    pack_tile<S, MIXED, VOFF, PAIR>(t, first, end, pos, vel, mass, geo, src, flags);
+    pack_tile<S, MIXED, VOFF, PAIR>(t, first, end, pos, vel, mass, geo, src, flags, src_lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -1487,7 +1622,11 @@ struct MixedSmem {
     static constexpr int BT = NT * KT;
     static constexpr int NC = POT ? kNCPot : kNC;
     static constexpr int kStages = NST;
-    float4 stage[NST][PAIR ? 7 * S / 4 : 2 * S];   // 28 or 32 bytes per source
+    // a stage: the packed tile (28 or 32 bytes per source), then the low
+    // parts of its position offsets (12 bytes per source)
+    static constexpr int kTileF4 = PAIR ? 7 * S / 4 : 2 * S;
+    static constexpr int kLoF4 = kLoPlanes * S / 4;
+    float4 stage[NST][kTileF4 + kLoF4];
     float acc[SACC ? NC * 2 * BT : 1];     // [c][hi, lo][BT]
     double x[SACC ? 3 * BT : 1];           // [c][BT]
     uint64_t bar[NST];
@@ -1592,6 +1731,8 @@ __device__ __forceinline__ bool mixed_item(
     // block's box when the targets are sparse
     const float blo_r[3] = {lo[0], lo[1], lo[2]};
     const float bhi_r[3] = {hi[0], hi[1], hi[2]};
+    // the warp's squared box diagonal (open boundaries: the close-tile test)
+    const float diag2_w = (MODE == kModeOpen) ? box_diag2(blo_r, bhi_r) : 0.0f;
 
     // adaptive softening: the targets' 1/h_i and zeta_i, the warp's largest
     // support
@@ -1631,11 +1772,20 @@ __device__ __forceinline__ bool mixed_item(
             }
     }
 
+    // a tile and, when packed, the low parts of its offsets, into stage s
+    auto load_stage = [&](int s, int t) {
+        if (a.src_lo)
+            tma_load_1d_two(sm.stage[s], src + (int64_t)t * 2 * S, kTileBytes,
+                            sm.stage[s] + Sm::kTileF4, a.src_lo + (int64_t)t * kLoPlanes * S,
+                            4u * kLoPlanes * S, &sm.bar[s]);
+        else
+            tma_load_1d(sm.stage[s], src + (int64_t)t * 2 * S, kTileBytes, &sm.bar[s]);
+    };
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
             int t = t_begin + s;
             if (t < t_end) {
-                tma_load_1d(sm.stage[s], src + (int64_t)t * 2 * S, kTileBytes, &sm.bar[s]);
+                load_stage(s, t);
                 sm.issued[s] += 1u;
             }
         }
@@ -1657,21 +1807,24 @@ __device__ __forceinline__ bool mixed_item(
         }
     }
 
-    // the target velocity in one tile's (or run's) FP32 sums: J1 -= v_i' F,
-    // J2 -= Tp v_i' (v_i' relative to the tile's velocity centre); then the
+    // the target velocity in one tile's FP32 sums: J1 -= v_i' F, J2 -= Tp v_i'
+    // (v_i' relative to the tile's velocity centre; not for the close loops,
+    // whose sums take each pair's own relative velocity); then the
     // compensated carry
     TileGeom g = a.geo[t_begin];
-    auto carry_tile = [&](float (&acc)[KT][kNCPot]) {
+    auto carry_any = [&](float (&acc)[KT][kNCPot], bool correct) {
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
-            const float ux = tvf[q][0] - g.cv[0], uy = tvf[q][1] - g.cv[1], uz = tvf[q][2] - g.cv[2];
-            const float Ft = acc[q][ESUM] + (acc[q][TXX] + acc[q][TYY] + acc[q][TZZ]);
-            acc[q][J10 + 0] = fmaf(-ux, Ft, acc[q][J10 + 0]);
-            acc[q][J10 + 1] = fmaf(-uy, Ft, acc[q][J10 + 1]);
-            acc[q][J10 + 2] = fmaf(-uz, Ft, acc[q][J10 + 2]);
-            acc[q][J20 + 0] -= fmaf(acc[q][TXX], ux, fmaf(acc[q][TXY], uy, acc[q][TXZ] * uz));
-            acc[q][J20 + 1] -= fmaf(acc[q][TXY], ux, fmaf(acc[q][TYY], uy, acc[q][TYZ] * uz));
-            acc[q][J20 + 2] -= fmaf(acc[q][TXZ], ux, fmaf(acc[q][TYZ], uy, acc[q][TZZ] * uz));
+            if (correct) {
+                const float ux = tvf[q][0] - g.cv[0], uy = tvf[q][1] - g.cv[1], uz = tvf[q][2] - g.cv[2];
+                const float Ft = acc[q][ESUM] + (acc[q][TXX] + acc[q][TYY] + acc[q][TZZ]);
+                acc[q][J10 + 0] = fmaf(-ux, Ft, acc[q][J10 + 0]);
+                acc[q][J10 + 1] = fmaf(-uy, Ft, acc[q][J10 + 1]);
+                acc[q][J10 + 2] = fmaf(-uz, Ft, acc[q][J10 + 2]);
+                acc[q][J20 + 0] -= fmaf(acc[q][TXX], ux, fmaf(acc[q][TXY], uy, acc[q][TXZ] * uz));
+                acc[q][J20 + 1] -= fmaf(acc[q][TXY], ux, fmaf(acc[q][TYY], uy, acc[q][TYZ] * uz));
+                acc[q][J20 + 2] -= fmaf(acc[q][TXZ], ux, fmaf(acc[q][TYZ], uy, acc[q][TZZ] * uz));
+            }
             if (SACC) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
@@ -1690,9 +1843,12 @@ __device__ __forceinline__ bool mixed_item(
             }
         }
     };
-    // periodic: the pairs of each target's FP64 close field, listed by the
-    // close loops and evaluated once the item's tiles are done
-    int32_t nlist[KT][periodic ? kCloseList : 1];
+    auto carry_tile = [&](float (&acc)[KT][kNCPot]) { carry_any(acc, true); };
+    // the pairs listed for FP64 (periodic: each target's close field; open
+    // boundaries: the pairs within 2h), evaluated once the item's tiles are
+    // done
+    constexpr bool listed = !soft;
+    int32_t nlist[KT][listed ? kCloseList : 1];
     int ncnt[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) ncnt[q] = 0;
@@ -1703,8 +1859,8 @@ __device__ __forceinline__ bool mixed_item(
     };
     // periodic: the FP64 close field of each target, summed in FP64 and added
     // to its final sums
-    double nsum[periodic ? KT : 1][periodic ? kNCPot : 1];
-    if constexpr (periodic) {
+    double nsum[listed ? KT : 1][listed ? kNCPot : 1];
+    if constexpr (listed) {
 #pragma unroll
         for (int q = 0; q < KT; ++q)
 #pragma unroll
@@ -1736,16 +1892,8 @@ __device__ __forceinline__ bool mixed_item(
             const float hm = fmaxf(h_block, a.geo_h[t]);
             h2_tile = __fmul_ru(hm, hm);
         }
-        // (periodic: taken for the warp's targets; "close" tiles come within
-        // a target's close radius and take the close loop)
-        bool near, close = false;
-        if (periodic) {
-            const int cls = periodic_class<KT>(tx, ti, g, a.h2f_up, a.box_tie_f, rc2);
-            close = __any_sync(0xffffffffu, (cls & 2) != 0);
-            near = __any_sync(0xffffffffu, (cls & 1) != 0);
-        } else {
-            near = tile_is_near(blo_r, bhi_r, g, h2_tile);
-        }
+        bool near, close;
+        classify_tile<KT, MODE>(a, g, tx, ti, blo_r, bhi_r, diag2_w, rc2, h2_tile, near, close);
         // next tile's geometry and offsets, computed ahead (FP64 latency)
         TileGeom gn = g;
         if (t + 1 < t_end) {
@@ -1763,14 +1911,42 @@ __device__ __forceinline__ bool mixed_item(
         for (int q = 0; q < KT; ++q)
 #pragma unroll
             for (int c = 0; c < kNCPot; ++c) acc[q][c] = 0.0f;
-        if (periodic && close) {
-            // runs of the close loops carry their own sums; acc stays zero
+        if (close && periodic) {
+            // the targets' low parts for this tile; runs of the close loops
+            // carry their own sums (acc stays zero)
+            float tl[KT][3];
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                double x[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    x[c] = SACC ? sm.x[c * BT + q * NT + threadIdx.x] : xr[SACC ? 0 : q][c];
+                target_low_parts(a, g, x, tx[q], true, tl[q]);
+            }
+            const float *lo = reinterpret_cast<const float *>(sm.stage[s] + Sm::kTileF4);
+            // (tiles that may need wrapping take the scalar loop)
             if (PAIR && !near)
-                close_loop_pair<KT, S, POT>(reinterpret_cast<const float *>(sm.stage[s]), tx, g.first,
-                                            rp2, carry_tile, record);
+                close_loop_pair<KT, S, kCloseRun, POT>(reinterpret_cast<const float *>(sm.stage[s]), lo,
+                                                       tx, tl, g.first, rp2, carry_tile, record);
             else
-                close_loop_f<KT, S, POT, PAIR>(sm.stage[s], tx, ti, g.first, a.h2f_up, a.hinvf, rp2,
-                                               a, carry_tile, record);
+                close_loop_f<KT, S, kCloseRun, POT, PAIR, true>(sm.stage[s], lo, tx, tl, ti, g.first,
+                                                                a.h2f_up, a.hinvf, rp2, a, carry_tile,
+                                                                record);
+        } else if (close) {
+            // open boundaries: near tiles, separations from the low parts
+            // too, pairs within 2h listed for FP64
+            float tl[KT][3];
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                double x[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    x[c] = SACC ? sm.x[c * BT + q * NT + threadIdx.x] : xr[SACC ? 0 : q][c];
+                target_low_parts(a, g, x, tx[q], false, tl[q]);
+            }
+            near_loop_rec<KT, S, POT, PAIR>(sm.stage[s],
+                                            reinterpret_cast<const float *>(sm.stage[s] + Sm::kTileF4),
+                                            tx, tl, ti, g.first, a.h2f_up, a.hinvf, acc, record);
         } else if (soft && near) {
             // the tile's (1/h_j, zeta_j) straight from global memory (every
             // lane reads the same source: one cached load per warp)
@@ -1780,32 +1956,22 @@ __device__ __forceinline__ bool mixed_item(
             periodic_loop_f<KT, S, POT, PAIR>(sm.stage[s], tx, ti, g.first, a.h2f_up, a.hinvf, a,
                                               acc);
         } else if (PAIR) {
-            const float *tf = reinterpret_cast<const float *>(sm.stage[s]);
-            if (!near) {
-                float2 acc2[KT][kNCPot];
+            float2 acc2[KT][kNCPot];
 #pragma unroll
-                for (int q = 0; q < KT; ++q)
+            for (int q = 0; q < KT; ++q)
 #pragma unroll
-                    for (int c = 0; c < kNCPot; ++c) acc2[q][c] = make_float2(0.0f, 0.0f);
-                far_loop_pair<KT, S, U, POT>(tf, tx, acc2);
+                for (int c = 0; c < kNCPot; ++c) acc2[q][c] = make_float2(0.0f, 0.0f);
+            far_loop_pair<KT, S, U, POT>(reinterpret_cast<const float *>(sm.stage[s]), tx, acc2);
 #pragma unroll
-                for (int q = 0; q < KT; ++q)
+            for (int q = 0; q < KT; ++q)
 #pragma unroll
-                    for (int c = 0; c < kNCPot; ++c) acc[q][c] = acc2[q][c].x + acc2[q][c].y;
-            } else {
-                near_loop_pair<KT, S, POT>(tf, tx, ti, g.first, a.h2f_up, a.hinvf, acc);
-            }
+                for (int c = 0; c < kNCPot; ++c) acc[q][c] = acc2[q][c].x + acc2[q][c].y;
         } else {
-            const float4 *sp_ = sm.stage[s];
-            const float4 *sv_ = sm.stage[s] + S;
-            if (!near)
-                far_loop_f<KT, S, U, POT>(sp_, sv_, tx, acc);
-            else
-                near_loop_f<KT, S, POT>(sp_, sv_, tx, ti, g.first, a.h2f_up, a.hinvf, acc);
+            far_loop_f<KT, S, U, POT>(sm.stage[s], sm.stage[s] + S, tx, acc);
         }
 
         // per-tile corrections for the target velocity, then the carry
-        if (!(periodic && close)) carry_tile(acc);
+        if (!(close && periodic)) carry_tile(acc);
 
         // this warp is done reading stage s; the last warp refills it
         __syncwarp();
@@ -1817,8 +1983,7 @@ __device__ __forceinline__ bool mixed_item(
                 __threadfence_block();
                 if (t + NSTAGE < t_end && !*(volatile int *)&sm.abort_flag) {
                     fence_proxy_async_smem();
-                    tma_load_1d(sm.stage[s], src + (int64_t)(t + NSTAGE) * 2 * S, kTileBytes,
-                                &sm.bar[s]);
+                    load_stage(s, t + NSTAGE);
                     sm.issued[s] += 1u;
                 }
             }
@@ -1832,17 +1997,18 @@ __device__ __forceinline__ bool mixed_item(
             for (int c = 0; c < 3; ++c) tx[q][c] = tx_next[q][c];
     }
 
-    // periodic: the FP64 close field (each lane its own list)
-    if constexpr (periodic) {
+    // the listed pairs in FP64 (each lane its own list; only targets list)
+    if constexpr (listed) {
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
+            if (ti[q] < 0) continue;
             double xi[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
                 xi[c] = SACC ? sm.x[c * BT + q * NT + threadIdx.x] : xr[SACC ? 0 : q][c];
             for (int k = 0; k < ncnt[q]; ++k) {
                 double v[kNCPot];
-                close_pair_d<POT>(a, ti[q], nlist[q][k], xi, v);
+                close_pair_d<POT, periodic>(a, ti[q], nlist[q][k], xi, v);
 #pragma unroll
                 for (int c = 0; c < kNCPot; ++c) nsum[q][c] += v[c];
             }
@@ -1868,7 +2034,7 @@ __device__ __forceinline__ bool mixed_item(
                 sum[c] = __dadd_rn((double)rhi[SACC ? 0 : q][SACC ? 0 : c],
                                    (double)rlo[SACC ? 0 : q][SACC ? 0 : c]);
             }
-            if constexpr (periodic) {
+            if constexpr (listed) {
                 if (c < NC) sum[c] = __dadd_rn(sum[c], nsum[q][c]);
             }
         }
@@ -2256,11 +2422,13 @@ reduce_partials_kernel(const EvalArgs a, int32_t BT)
 typedef void (*eval_launch_fn)(const EvalArgs &, int grid, cudaStream_t);
 typedef int (*occupancy_fn)(int *blocks_per_sm);
 typedef void (*pack_launch_fn)(int64_t n_src, const double *, const double *, const double *,
-                               TileGeom *, void *, int32_t *, int n_tiles, cudaStream_t);
+                               TileGeom *, void *, int32_t *, float *src_lo, int n_tiles,
+                               cudaStream_t);
 
 typedef void (*batched_launch_fn)(const EvalArgs &, const BatchView &, int grid, cudaStream_t);
 typedef void (*batched_pack_fn)(const BatchView &, const double *, const double *, const double *,
-                                TileGeom *, void *, int32_t *, int max_tiles, cudaStream_t);
+                                TileGeom *, void *, int32_t *, float *src_lo, int max_tiles,
+                                cudaStream_t);
 
 // Upper bound on the tile configurations of one precision (host caches).
 constexpr int kMaxTileConfigs = 32;
@@ -2325,9 +2493,11 @@ int occupancy_f64_batched(int *b)
 
 template <int S, bool MIXED, bool VOFF, bool PAIR>
 void launch_pack_batched(const BatchView &b, const double *pos, const double *vel, const double *mass,
-                         TileGeom *geo, void *src, int32_t *flags, int max_tiles, cudaStream_t st)
+                         TileGeom *geo, void *src, int32_t *flags, float *src_lo, int max_tiles,
+                         cudaStream_t st)
 {
-    pack_tiles_batched_kernel<S, MIXED, VOFF, PAIR><<<max_tiles, S, 0, st>>>(b, pos, vel, mass, geo, src, flags);
+    pack_tiles_batched_kernel<S, MIXED, VOFF, PAIR><<<max_tiles, S, 0, st>>>(b, pos, vel, mass, geo, src,
+                                                                            flags, src_lo);
 }
 
 template <int NT, int S, bool POT, int MODE>
@@ -2344,13 +2514,15 @@ int occupancy_f64(int *b)
 
 template <int S, bool MIXED, bool VOFF, bool PAIR>
 void launch_pack(int64_t n_src, const double *pos, const double *vel, const double *mass,
-                 TileGeom *geo, void *src, int32_t *flags, int n_tiles, cudaStream_t st)
+                 TileGeom *geo, void *src, int32_t *flags, float *src_lo, int n_tiles, cudaStream_t st)
 {
-    pack_tiles_kernel<S, MIXED, VOFF, PAIR><<<n_tiles, S, 0, st>>>(n_src, pos, vel, mass, geo, src, flags);
+    pack_tiles_kernel<S, MIXED, VOFF, PAIR><<<n_tiles, S, 0, st>>>(n_src, pos, vel, mass, geo, src, flags,
+                                                                  src_lo);
 }
 
 // Defined in the per-precision translation units.
 const EvalConfig *mixed_configs(int *count);
+
 const EvalConfig *f64_configs(int *count);
 void launch_reduce(const EvalArgs &a, int32_t BT, bool pot, bool etrace, int64_t n_targets,
                    cudaStream_t st);

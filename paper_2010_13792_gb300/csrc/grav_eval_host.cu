@@ -110,7 +110,7 @@ void set_box(EvalArgs &a, double box)
     float tie = (float)(box * (0.5 - 0x1p-20));
     if ((double)tie > box * (0.5 - 0x1p-20)) tie = std::nextafter(tie, 0.0f);
     a.box_tie_f = box > 0.0 ? tie : 0.0f;
-    a.pad2 = 0.0f;
+    a.box_lo_f = box > 0.0 ? (float)(box - (double)a.box_f) : 0.0f;
 }
 
 int grid_for(const EvalConfig *c, int index, int mode, bool pot, int *grid)
@@ -139,7 +139,7 @@ int grid_for(const EvalConfig *c, int index, int mode, bool pot, int *grid)
 
 struct Layout {
     int64_t n_tiles;
-    int64_t geo_off, src_off, part_off, total;
+    int64_t geo_off, src_off, lo_off, part_off, total;
     int64_t part_cap_rows;
     int64_t hz_off, geo_h_off;     // adaptive softening only (else 0)
     int32_t max_split;
@@ -159,7 +159,9 @@ int make_layout(const grav_params *p, const EvalConfig *c, int64_t n_src, int64_
     L->n_tiles = (n_src + S - 1) / S;
     L->geo_off = 0;
     L->src_off = round_up(L->n_tiles * (int64_t)sizeof(TileGeom), 256);
-    L->part_off = L->src_off + round_up(L->n_tiles * 2 * S * elem, 256);
+    L->lo_off = L->src_off + round_up(L->n_tiles * 2 * S * elem, 256);
+    const int64_t lo_bytes = (c->precision == GRAV_MIXED) ? L->n_tiles * kLoPlanes * S * 4 : 0;
+    L->part_off = L->lo_off + round_up(lo_bytes, 256);
     const int64_t n_tb_max = (n_idx_max + BT - 1) / BT;
     int64_t blocks = 0;
     if (L->max_split > 1 && L->n_tiles > 1)
@@ -286,6 +288,8 @@ int eval_single(const char *who, const grav_params *p, bool soft, int64_t n_src,
     a.pad0 = 0;
     a.part = reinterpret_cast<double *>(ws + L.part_off);
     a.part_cap_rows = L.part_cap_rows;
+    a.src_lo = c->precision == GRAV_MIXED ? reinterpret_cast<const float *>(ws + L.lo_off) : nullptr;
+
     a.pos = pos;
     a.vel = vel;
     a.mass = mass;
@@ -315,7 +319,7 @@ int eval_single(const char *who, const grav_params *p, bool soft, int64_t n_src,
 
     cudaStream_t st = as_stream(stream);
     c->pack(n_src, pos, vel, mass, const_cast<TileGeom *>(a.geo), const_cast<void *>(a.src), flags_dev,
-            (int)L.n_tiles, st);
+            const_cast<float *>(a.src_lo), (int)L.n_tiles, st);
     rc = check_launch("grav_eval/pack");
     if (rc) return rc;
     if (soft) {
@@ -339,6 +343,7 @@ int eval_single(const char *who, const grav_params *p, bool soft, int64_t n_src,
         rc = check_launch("grav_eval/reduce");
         if (rc) return rc;
     }
+
     return GRAV_OK;
 }
 
@@ -493,7 +498,7 @@ batch_plan_kernel(BatchView b, const int32_t *__restrict__ idx, const int32_t *n
 }
 
 struct BatchLayout {
-    int64_t hdr, tile_off, idx_lo, idx_hi, ntb, order, item_off, geo, src, total;
+    int64_t hdr, tile_off, idx_lo, idx_hi, ntb, order, item_off, geo, src, lo, total;
     int64_t max_tiles;
 };
 
@@ -522,6 +527,8 @@ BatchLayout batch_layout(const EvalConfig *c, int32_t n_sys, int64_t n_total)
     o += round_up(L.max_tiles * (int64_t)sizeof(TileGeom), 256);
     L.src = o;
     o += round_up(L.max_tiles * 2 * S * elem, 256);
+    L.lo = o;
+    o += round_up((c->precision == GRAV_MIXED) ? L.max_tiles * kLoPlanes * S * 4 : 0, 256);
     L.total = o;
     return L;
 }
@@ -615,6 +622,7 @@ extern "C" int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav
     a.n_idx_max = n_idx_max;
     a.geo = reinterpret_cast<const TileGeom *>(ws + L.geo);
     a.src = ws + L.src;
+    a.src_lo = c->precision == GRAV_MIXED ? reinterpret_cast<const float *>(ws + L.lo) : nullptr;
     a.n_tiles = 0;
     a.max_split = 1;
     a.grid = grid;
@@ -649,7 +657,7 @@ extern "C" int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav
     rc = check_launch("grav_eval_batched/plan");
     if (rc) return rc;
     c->pack_batched(b, pos, vel, mass, const_cast<TileGeom *>(a.geo), const_cast<void *>(a.src),
-                    flags_dev, (int)L.max_tiles, st);
+                    flags_dev, const_cast<float *>(a.src_lo), (int)L.max_tiles, st);
     rc = check_launch("grav_eval_batched/pack");
     if (rc) return rc;
     c->launch_batched[p->box > 0.0 ? 1 : 0][want_pot ? 1 : 0](a, b, grid, st);

@@ -6,7 +6,8 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from paper_2010_13792_gb300 import grav
+from oracle import oracle as O
+from paper_2010_13792_gb300 import grav, ics
 
 DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
 
@@ -53,11 +54,15 @@ def rel_err(gpu, ref):
 
 
 def errors(out, ref, rows):
-    """Error statistics of GPU rows `rows` against oracle slots 0..len(rows)."""
+    """Error statistics of GPU rows `rows` against oracle slots 0..len(rows):
+    (median, max) of |d|/|ref| per target (||dT||_F / ||T||_F for T)."""
     e = {}
     for k in ("acc", "jerk", "tidal", "pot", "dt_grav"):
         if k in out and k in ref and ref[k] is not None:
-            r = rel_err(out[k][rows], ref[k])
+            if k == "tidal":
+                r = tidal_norm(out[k][rows] - ref[k]) / tidal_norm(ref[k])
+            else:
+                r = rel_err(out[k][rows], ref[k])
             e[k] = (float(np.median(r)), float(np.max(r)))
     return e
 
@@ -82,3 +87,72 @@ def assert_mixed(e):
     assert e["tidal"][1] <= MIXED_MAX, ("tidal max", e["tidal"])
     if "pot" in e:
         assert e["pot"][1] <= MIXED_MAX, ("pot max", e["pot"])
+
+
+def tidal_norm(t6):
+    """||T||_F of [n, 6] tidal tensors (off-diagonal components twice)."""
+    t6 = np.asarray(t6)
+    return np.sqrt((t6[:, :3] ** 2).sum(1) + 2.0 * (t6[:, 3:] ** 2).sum(1))
+
+
+def tree_accel_norm(pos, vel, mass, h):
+    """|a_i| of every element from the oracle's oct-tree (Theta = 0.5), a
+    cheap estimate used only to rank candidates for the worst-conditioned
+    targets (the conditioning's |a_i| is small where |a_i| is)."""
+    return np.linalg.norm(O.tree_eval(pos, vel, mass, None, h=h, theta=0.5, leaf_size=8,
+                                      want_pot=False)["acc"], axis=1)
+
+
+def stratified_rows(pos, vel, mass, idx, h, a_est, *, seed, worst=512, total=4096, pool=2048,
+                    box=0.0):
+    """Rows of a full-size parity check, stratified on the conditioning
+    kappa_i = sum_j |a_ij| / |a_i| (the error metric's conditioning): the
+    `worst` targets of idx with the largest kappa among the `pool` targets of
+    idx with the smallest estimated |a_i| (a_est, by element), plus targets
+    drawn at random from the rest of idx up to `total`.  Returns (rows,
+    ref, kappa): sorted element indices, the oracle at those rows and, per
+    row, kappa of a, j and T (sums of pair magnitudes over |a|, |j|, ||T||)."""
+    idx = np.asarray(idx, np.int64)
+    if idx.size <= total:
+        rows = idx.astype(np.int32)
+    else:
+        cand = np.sort(idx[np.argsort(a_est[idx], kind="stable")[:pool]]).astype(np.int32)
+        ref_c = O.eval_active(pos, vel, mass, cand, h=h, box=box)
+        kap_c = O.conditioning(pos, vel, mass, cand, h=h, box=box)[:, 0] / \
+            np.linalg.norm(ref_c["acc"], axis=1)
+        hard = cand[np.argsort(kap_c, kind="stable")[-worst:]]
+        rest = np.setdiff1d(idx, hard)
+        rnd = ics.rng(seed).choice(rest, size=total - hard.size, replace=False)
+        rows = np.sort(np.concatenate([hard, rnd])).astype(np.int32)
+    ref = O.eval_active(pos, vel, mass, rows, h=h, box=box)
+    cond = O.conditioning(pos, vel, mass, rows, h=h, box=box)
+    kappa = np.stack([cond[:, 0] / np.linalg.norm(ref["acc"], axis=1),
+                      cond[:, 1] / np.linalg.norm(ref["jerk"], axis=1),
+                      cond[:, 2] / tidal_norm(ref["tidal"])], axis=1)
+    return rows, ref, kappa
+
+
+def error_table(out, ref, rows, kappa):
+    """Per quantity: median and max relative error over the rows, with the
+    conditioning kappa of the row of the max and the largest kappa."""
+    tab = {}
+    for k, col in (("acc", 0), ("jerk", 1), ("tidal", 2)):
+        if k == "tidal":
+            r = tidal_norm(out[k][rows] - ref[k]) / tidal_norm(ref[k])
+        else:
+            r = rel_err(out[k][rows], ref[k])
+        w = int(np.argmax(r))
+        tab[k] = {"median": float(np.median(r)), "max": float(r.max()),
+                  "kappa_at_max": float(kappa[w, col]), "kappa_max": float(kappa[:, col].max())}
+    return tab
+
+
+def assert_table(tab, precision):
+    """The stated bounds on an error_table."""
+    if precision == grav.F64:
+        for k, v in tab.items():
+            assert v["max"] <= F64_TOL, (k, v)
+        return
+    assert tab["acc"]["median"] <= MIXED_A_MEDIAN, ("acc median", tab["acc"])
+    for k, v in tab.items():
+        assert v["max"] <= MIXED_MAX, (k, v)

@@ -7,7 +7,8 @@ several tiles with a partial last tile and last target block, every tile
 configuration, the source-split path (few targets), device-resident counts,
 degenerate inputs (one element, two bodies, coincident elements, everything
 softened), device flags, and full-size Plummer and turbulent-cloud inputs
-compared on sampled targets.
+compared on 4096 targets stratified on the conditioning (the 512 hardest
+plus 3584 at random).
 """
 import numpy as np
 import pytest
@@ -16,7 +17,8 @@ import torch
 from oracle import oracle as O
 from paper_2010_13792_gb300 import grav, ics
 
-from gpu_util import (DEV, T, assert_f64, assert_mixed, errors, run_eval)  # noqa: E402
+from gpu_util import (DEV, T, assert_f64, assert_mixed, assert_table, error_table,  # noqa: E402
+                      errors, run_eval, stratified_rows, tree_accel_norm)
 
 pytestmark = pytest.mark.gpu
 
@@ -169,64 +171,81 @@ def test_zero_targets_device_count():
     del idx
 
 
-# ---- full-size inputs, sampled targets ------------------------------------
+# ---- full-size inputs: 4096 targets, stratified on the conditioning ---------
+#
+# The rows compared at full size are the 512 worst-conditioned targets
+# (largest kappa_i = sum_j |a_ij| / |a_i| among the 2048 with the smallest
+# oracle-tree estimate of |a_i|, where FP32 cancellation bites) plus 3584
+# drawn at random; every row is checked at the stated bounds.
 
 
 @pytest.fixture(scope="module")
 def plummer_2e17():
-    return ics.plummer(1 << 17, seed=ics.BASE_SEED + 1)
+    pos, vel, mass = ics.plummer(1 << 17, seed=ics.BASE_SEED + 1)
+    return pos, vel, mass, tree_accel_norm(pos, vel, mass, 1e-3)
 
 
 @pytest.fixture(scope="module")
 def cloud_2e20():
-    return ics.turbulent_cloud(1 << 20, seed=ics.BASE_SEED + 2)
+    pos, vel, mass = ics.turbulent_cloud(1 << 20, seed=ics.BASE_SEED + 2)
+    return pos, vel, mass, tree_accel_norm(pos, vel, mass, 2e-3)
 
 
-def _sample(n, k, seed):
-    return np.sort(ics.rng(seed).choice(n, size=k, replace=False)).astype(np.int32)
+_ROWS = {}
+
+
+def _rows(key, pos, vel, mass, idx, h, a_est, seed):
+    """Stratified rows and their oracle values, shared by the tests of one
+    workload and active set."""
+    if key not in _ROWS:
+        _ROWS[key] = stratified_rows(pos, vel, mass, idx, h, a_est, seed=seed)
+    return _ROWS[key]
 
 
 @pytest.mark.parametrize("precision", [grav.F64, grav.MIXED])
-def test_plummer_2e17_all_active_sampled(plummer_2e17, precision):
-    pos, vel, mass = plummer_2e17
+def test_plummer_2e17_all_active_stratified(plummer_2e17, precision):
+    pos, vel, mass, a_est = plummer_2e17
     n = mass.size
     out = run_eval(pos, vel, mass, None, h=1e-3, precision=precision)
-    rows = _sample(n, 192, 31)
-    ref = O.eval_active(pos, vel, mass, rows, h=1e-3)
-    e = errors(out, ref, rows)
-    (assert_f64 if precision == grav.F64 else assert_mixed)(e)
+    rows, ref, kappa = _rows("plummer", pos, vel, mass, np.arange(n), 1e-3, a_est, 31)
+    assert rows.size == 4096
+    assert_table(error_table(out, ref, rows, kappa), precision)
+
+
+def _cloud_active(n, fraction):
+    return ics.active_subset(n, fraction, 40 + int(fraction * 100))
 
 
 @pytest.mark.parametrize("fraction", [0.01, 0.1, 1.0])
-def test_cloud_2e20_mixed_sampled(cloud_2e20, fraction):
-    pos, vel, mass = cloud_2e20
+def test_cloud_2e20_mixed_stratified(cloud_2e20, fraction):
+    pos, vel, mass, a_est = cloud_2e20
     n = mass.size
-    idx = ics.active_subset(n, fraction, 40 + int(fraction * 100))
+    idx = _cloud_active(n, fraction)
     out = run_eval(pos, vel, mass, idx, h=2e-3, precision=grav.MIXED)
-    rows = np.sort(ics.rng(41).choice(idx, size=160, replace=False)).astype(np.int32)
-    ref = O.eval_active(pos, vel, mass, rows, h=2e-3)
-    assert_mixed(errors(out, ref, rows))
+    rows, ref, kappa = _rows(("cloud", fraction), pos, vel, mass, idx, 2e-3, a_est, 41)
+    assert rows.size == 4096 and np.all(np.isin(rows, idx))
+    tab = error_table(out, ref, rows, kappa)
+    assert tab["acc"]["kappa_max"] > 50.0, tab        # the hard targets are in the sample
+    assert_table(tab, grav.MIXED)
 
 
-def test_cloud_2e20_f64_sampled(cloud_2e20):
-    pos, vel, mass = cloud_2e20
+def test_cloud_2e20_f64_stratified(cloud_2e20):
+    pos, vel, mass, a_est = cloud_2e20
     n = mass.size
-    idx = ics.active_subset(n, 0.01, 41)
+    idx = _cloud_active(n, 0.01)
     out = run_eval(pos, vel, mass, idx, h=2e-3, precision=grav.F64)
-    rows = np.sort(ics.rng(42).choice(idx, size=96, replace=False)).astype(np.int32)
-    ref = O.eval_active(pos, vel, mass, rows, h=2e-3)
-    assert_f64(errors(out, ref, rows))
+    rows, ref, kappa = _rows(("cloud", 0.01), pos, vel, mass, idx, 2e-3, a_est, 41)
+    assert_table(error_table(out, ref, rows, kappa), grav.F64)
 
 
 @pytest.mark.parametrize("cfg", range(24))
 def test_cloud_2e20_every_mixed_config(cloud_2e20, cfg):
+    """Every tile configuration on the stratified rows of the 1% set."""
     if cfg >= grav.lib().grav_tile_config_count(grav.MIXED):
         pytest.skip("no such tile configuration")
-    pos, vel, mass = cloud_2e20
+    pos, vel, mass, a_est = cloud_2e20
     n = mass.size
-    idx = ics.active_subset(n, 0.02, 77)
-    out = run_eval(pos, vel, mass, idx, h=2e-3, precision=grav.MIXED, tile_config=cfg,
-                   want_pot=False)
-    rows = np.sort(ics.rng(78).choice(idx, size=64, replace=False)).astype(np.int32)
-    ref = O.eval_active(pos, vel, mass, rows, h=2e-3, want_pot=False)
-    assert_mixed(errors(out, ref, rows))
+    idx = _cloud_active(n, 0.01)
+    out = run_eval(pos, vel, mass, idx, h=2e-3, precision=grav.MIXED, tile_config=cfg)
+    rows, ref, kappa = _rows(("cloud", 0.01), pos, vel, mass, idx, 2e-3, a_est, 41)
+    assert_table(error_table(out, ref, rows, kappa), grav.MIXED)
