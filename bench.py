@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -42,11 +43,11 @@ BWD_FLOPS_PER_INTERACTION = 31  # the adjoint's Newtonian pair body, counted the
 WORKLOAD = "turbulent_cloud_N1048576_h2e-3"
 METRIC = "acc+jerk+tidal interactions/s at N=2^20 (mixed precision)"
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of one force-kernel launch from an ncu capture of
-# the tile configuration the library picks for this workload (17) on the
-# turbulent cloud with N = 2^18, all active
-# (profiles/eval_mixed_kernel_768x1_warp_release_turbulent_cloud_N262144.md).
-# The traffic is the sources and targets streamed once, so it scales with N.
+# DRAM bytes (read + write, dram__bytes_read.sum + dram__bytes_write.sum) of
+# one force-kernel launch, from an ncu capture of the tile configuration the
+# library picks for this workload (17) on the turbulent cloud with N = 2^18,
+# all active.  The traffic is the sources and targets streamed once, so it
+# scales with N.
 TRAFFIC_CAPTURE = {"tile_config": 17, "n": 262144, "bytes": 21778176 + 14417152}
 
 
@@ -62,6 +63,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="headline steps only (no sweeps, FP64 path, e2e, CPU baseline)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--clocks-csv", default=None,
+                    help="also copy the nvidia-smi clock samples of the timed region here")
     ap.add_argument("--predict-only", action="store_true",
                     help="time only the predictor (grav_predict) on --n elements, all active, "
                          "none due, and print its bandwidth")
@@ -125,15 +128,16 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, keep: str | None = None):
         self.gpu = gpu_index
+        self.keep = keep    # where to copy the samples' CSV afterwards (None: nowhere)
         self.proc = None
         self.path = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{self.gpu}.csv")
+            self.dir = tempfile.mkdtemp(prefix="grav_clocks_")
+            self.path = os.path.join(self.dir, f"clocks_gpu{self.gpu}.csv")
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
@@ -151,6 +155,10 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
             self.fh.close()
+            if self.keep:
+                import shutil
+                os.makedirs(os.path.dirname(os.path.abspath(self.keep)), exist_ok=True)
+                shutil.copyfile(self.path, self.keep)
 
     def summary(self):
         if self.proc is None or not self.path or not os.path.exists(self.path):
@@ -262,7 +270,7 @@ def run_ours(args, rank, local, ws):
                for _ in range(args.steps)]
     barrier(ws)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_csv if rank == 0 else None) as clk:
         wall0 = time.perf_counter()
         for k in range(args.steps):
             l2_flush(flush)

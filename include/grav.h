@@ -172,7 +172,11 @@ GRAV_API int grav_compact_active(int64_t n, const uint8_t *flags, int32_t *idx_o
  *    GRAV_EINVAL before anything is launched.
  *  - The first call on a device looks up the array's device address (once per
  *    device, with that device current); make that first call before any
- *    stream capture.
+ *    stream capture.  The address is kept per device ordinal until the
+ *    process exits and is not looked up again: after cudaDeviceReset on a
+ *    device (which ends its primary context) the kept address may no longer
+ *    be valid there, so do not call this entry point on a device after
+ *    resetting it.
  *  - All calls share the array.  Each call writes every scratch element it
  *    reads, so nothing needs clearing between calls, but calls whose kernels
  *    overlap on the GPU (other streams, other threads) race on it: serialise

@@ -3,8 +3,9 @@
 Times every tile configuration libgrav offers (threads per CTA, targets per
 thread, sources per tile, accumulator placement, unroll depth) on the
 caller's own inputs with CUDA events, and remembers the fastest per device,
-precision, launch kind (single system or batched) and size class in a JSON
-cache next to the built library.  Only timing happens here; every
+precision, boundary mode (open or periodic box), potential on or off, launch
+kind (single system or batched) and size class in a JSON cache next to the
+built library.  Only timing happens here; every
 configuration computes the same sums.
 """
 from __future__ import annotations
@@ -39,12 +40,17 @@ def _store(cache):
     os.replace(tmp, CACHE)
 
 
-def shape_key(precision: int, kind: str, n_src: int, n_targets: int, device=None) -> str:
-    """Device, precision, launch kind and log2 size classes of sources and targets."""
+def shape_key(precision: int, kind: str, n_src: int, n_targets: int, device=None, *,
+              periodic: bool = False, pot: bool = False) -> str:
+    """Device, precision, boundary mode, potential, launch kind and log2 size
+    classes of sources and targets (the periodic and potential kernels are
+    separate instantiations with their own timings)."""
     name = torch.cuda.get_device_name(device)
     ls = int(math.log2(max(n_src, 1)))
     lt = int(math.log2(max(n_targets, 1)))
-    return f"{name}|{'mixed' if precision == grav.MIXED else 'f64'}|{kind}|src2^{ls}|tgt2^{lt}"
+    mode = "periodic" if periodic else "open"
+    return (f"{name}|{'mixed' if precision == grav.MIXED else 'f64'}|{mode}|"
+            f"{'pot' if pot else 'nopot'}|{kind}|src2^{ls}|tgt2^{lt}")
 
 
 def _time(fn, reps: int) -> float:
@@ -67,7 +73,8 @@ def tune_eval(params: grav.Params, pos, vel, mass, idx, n_idx: int, *, systems=N
     """Fastest tile configuration for this workload; returns (index, {index: ms})."""
     precision = params.precision
     kind = "batched" if systems is not None else "single"
-    key = shape_key(precision, kind, mass.numel(), n_idx, pos.device)
+    key = shape_key(precision, kind, mass.numel(), n_idx, pos.device, periodic=params.box > 0.0,
+                    pot=bool(params.want_pot))
     if use_cache:
         with _lock:
             hit = _load().get(key)

@@ -101,7 +101,7 @@ def test_predictor_variants_ablation():
     predictor, the linear polynomial through the last two evaluations and the
     jerk, ordered jerk < polynomial < none in predicted-acceleration error.
     (When close encounters dominate, or the update gaps are long, only the
-    jerk helps; tests/predictor_ablation.py and bench.py report those cases.)
+    jerk helps; test_gpu_predictor_ablation.py and bench.py cover those cases.)
     The graph replays the poly loop exactly."""
     n = 1 << 12
     pos, vel, mass = ics.plummer(n, seed=ics.BASE_SEED + 1)

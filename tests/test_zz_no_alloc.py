@@ -58,3 +58,17 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                        ctypes.c_void_p(8), ctypes.c_void_p(cnt.data_ptr()), None)
     assert rc == grav.GRAV_EINVAL
     assert b"outside" in L.grav_last_error_string()
+
+
+@pytest.mark.parametrize("n", [grav.COMPACT_NOALLOC_MAX_N - 1, grav.COMPACT_NOALLOC_MAX_N])
+def test_noalloc_at_its_size_limit(n):
+    """n = 2^26 (16384 blocks of 4096 flags: every scratch element, one
+    single-CTA scan over all of them) and one flag below it (a ragged last
+    block)."""
+    dev = torch.device("cuda:0")
+    flags = (ics.rng(901 + n % 7).uniform(size=n) < 0.25).astype(np.uint8)
+    flags[-1] = 1
+    ia, ca, ib, cb = _compact_both(flags, dev)
+    assert ca == cb == int(flags.astype(bool).sum())
+    assert np.array_equal(ia, ib)
+    assert ib[cb - 1] == n - 1
