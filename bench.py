@@ -695,7 +695,7 @@ def batched_extra(dev, flush):
     inter = float(sum(a.size * int(s) for a, s in zip(act, sizes)))
     f64 = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
     P, V, M = f64(pos), f64(vel), f64(mass)
-    systems = torch.as_tensor(np.stack([offsets, sizes], 1), dtype=torch.int64, device=dev)
+    systems = grav.systems_table(np.stack([offsets, sizes], 1), device=dev)
     idx = torch.as_tensor(idx_np, device=dev)
     acc = torch.empty(n, 3, dtype=torch.float64, device=dev)
     jerk, tid = torch.empty_like(acc), torch.empty(n, 6, dtype=torch.float64, device=dev)

@@ -91,11 +91,13 @@ typedef struct grav_tile_info {
 } grav_tile_info;
 
 /* One independent system of a batched launch: elements [offset, offset + n)
- * of the packed arrays.  Systems are given in ascending, non-overlapping
- * order. */
+ * of the packed arrays, softened with support h (Eq. 4 per system; h = 0:
+ * the call's grav_params h).  Systems are given in ascending,
+ * non-overlapping order. */
 typedef struct grav_system {
     int64_t offset;
     int64_t n;
+    double h;
 } grav_system;
 
 GRAV_API const char *grav_last_error_string(void);
@@ -292,12 +294,40 @@ GRAV_API int grav_eval_backward(const grav_params *p, int64_t n, const double *p
                        void *workspace, int64_t workspace_bytes, void *stream);
 
 /*
+ * grav_eval_backward_batched -- grav_eval_backward over many independent
+ * systems in one persistent launch (the batched form of the adjoint above,
+ * as grav_eval_batched is of the force evaluation).  systems [n_sys] is the
+ * DEVICE array of grav_eval_batched ({offset, n, h}, h = 0: p->h); every
+ * element of a system is a target, and its sums run over its own system's
+ * elements only, with its system's support h.  Work items are (system,
+ * target block) pairs taken longest system first through an atomic ticket;
+ * each element's sums are formed by one CTA over its system's tiles in a
+ * fixed order, so a system's results equal grav_eval_backward on that system
+ * alone with max_split = 1, bit for bit.  Elements of no system, and of a
+ * system that is skipped (out of range, overlapping, bad h: see
+ * grav_eval_batched; GRAV_FLAG_BADINDEX), are not written, except that with
+ * a_bar == NULL the elementwise potential-energy terms are written at every
+ * element of [0, n_total).  Open boundaries only (p->box = 0).
+ * workspace: >= grav_backward_batched_workspace_bytes(p, n_sys, n_total).
+ */
+GRAV_API int64_t grav_backward_batched_workspace_bytes(const grav_params *p, int32_t n_sys,
+                                                       int64_t n_total);
+GRAV_API int grav_eval_backward_batched(const grav_params *p, int32_t n_sys, const grav_system *systems,
+                                        int64_t n_total, const double *pos, const double *mass,
+                                        const double *a_bar, double w_bar, const double *acc,
+                                        const double *tidal, const double *pot, double *pos_bar,
+                                        double *mass_bar, int32_t *flags_dev, void *workspace,
+                                        int64_t workspace_bytes, void *stream);
+
+/*
  * grav_eval_batched -- grav_eval_active over many independent systems in one
  * persistent launch (pattern (2) of the batched workloads; the paper's method
  * per system is unchanged).  systems [n_sys] is a DEVICE array of
- * {offset, n} describing systems packed back to back in pos/vel/mass
+ * {offset, n, h} describing systems packed back to back in pos/vel/mass
  * (ascending, non-overlapping, inside [0, n_total)); the sources of a target
- * are the elements of its own system only.  idx[0..c) are GLOBAL target
+ * are the elements of its own system only, and its sums use its system's
+ * support h (p->h where h = 0), rounded to FP32 exactly as the host rounds
+ * p->h, so a system's results do not depend on how h reached the kernel.  idx[0..c) are GLOBAL target
  * indices in ascending order (for example grav_compact_active over the
  * packed due flags), c = *n_idx_dev or n_idx_max; each system's targets are
  * found on the device by binary search, so counts never visit the host and
@@ -308,9 +338,9 @@ GRAV_API int grav_eval_backward(const grav_params *p, int64_t n, const double *p
  * atomic ticket; each target's sum is formed by one CTA over its system's
  * tiles in a fixed order, so results do not depend on scheduling and equal
  * grav_eval_active on that system alone with max_split = 1.
- * A system that is out of range or overlaps its predecessor is skipped and
- * sets GRAV_FLAG_BADINDEX; targets that belong to no system are not
- * evaluated.
+ * A system that is out of range, overlaps its predecessor or has an h that
+ * is neither 0 nor finite and positive is skipped and sets
+ * GRAV_FLAG_BADINDEX; targets that belong to no system are not evaluated.
  * n_sys <= GRAV_BATCH_MAX_SYSTEMS.
  * workspace: >= grav_batched_workspace_bytes(p, n_sys, n_total) bytes.
  */

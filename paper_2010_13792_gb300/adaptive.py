@@ -31,6 +31,7 @@ class AdaptiveIntegrator:
         """predictor: "jerk" (Eq. jerkupdate), "poly" (first-order polynomial
         through the last two logged evaluations, Section 2.2) or "none" (keep the
         last evaluated acceleration).  systems: optional [n_sys, 2] (offset, n)
+        or a grav.systems_table (offset, n, h)
         of independent systems packed back to back; their forces come from one
         batched launch per tick."""
         device = device or torch.device("cuda", torch.cuda.current_device())
@@ -48,8 +49,7 @@ class AdaptiveIntegrator:
             raise ValueError(f"unknown predictor {predictor!r}")
         self.predictor = predictor
         self.params = grav.params(G=G, h=h, eta=eta, precision=precision, tile_config=tile_config)
-        self.systems = None if systems is None else \
-            torch.as_tensor(systems, dtype=torch.int64, device=device).contiguous()
+        self.systems = None if systems is None else grav.systems_table(systems, device=device)
         self.acc = torch.zeros(n, 3, dtype=torch.float64, device=device)
         self.jerk = torch.zeros_like(self.acc)
         self.tidal = torch.zeros(n, 6, dtype=torch.float64, device=device)

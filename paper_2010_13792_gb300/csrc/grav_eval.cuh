@@ -1569,6 +1569,35 @@ struct BatchView {
     int32_t pad;
 };
 
+// A system's softening h in a copy of the launch's arguments, with the
+// roundings the host applies to grav_params.h: FP32 h and 1/h to nearest,
+// h^2 in FP64 then to FP32 rounded up.
+__device__ __forceinline__ void softening_f(double h, float &h2f_up, float &hinvf)
+{
+    const double h2 = __dmul_rn(h, h);
+    float h2f = __double2float_rn(h2);
+    if ((double)h2f < h2) h2f = nextafterf(h2f, __int_as_float(0x7f800000));
+    h2f_up = h2f;
+    hinvf = __double2float_rn(__ddiv_rn(1.0, h));
+}
+
+__device__ __forceinline__ void set_softening(EvalArgs &a, double h)
+{
+    a.h = h;
+    a.hf = __double2float_rn(h);
+    softening_f(h, a.h2f_up, a.hinvf);
+}
+
+// The plan of a batched launch (grav_eval_host.cu): per-system tiles and
+// target ranges (idx == NULL: every element of a system is a target), the
+// longest-first order of the systems, the work-item offsets; resets the
+// ticket.  Systems that are out of range, overlap, or have an h that is
+// neither 0 nor finite, positive and (box > 0) under half the box are
+// skipped with GRAV_FLAG_BADINDEX.
+int launch_batch_plan(const BatchView &b, const int32_t *idx, const int32_t *n_idx_dev,
+                      int64_t n_idx_max, int64_t n_total, int32_t S, int32_t BT, double box,
+                      int32_t *flags, cudaStream_t st);
+
 // Rank r such that item_off[r] <= ticket < item_off[r + 1].
 __device__ __forceinline__ int item_rank(const BatchView &b, int64_t ticket)
 {
@@ -2095,11 +2124,20 @@ eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
     constexpr int BT = Sm::BT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
+    __shared__ EvalArgs sa;   // the launch's arguments with the item's system's softening
+    if (threadIdx.x == 0) sa = a;
     init_mixed_ring(sm);
     Ring ring{0u, 0u};
     const int64_t total = b.hdr->total_items;
     for (;;) {
-        if (threadIdx.x == 0) sm.ticket = (long long)atomicAdd(&b.hdr->ticket, 1ULL);
+        if (threadIdx.x == 0) {
+            const long long tk = (long long)atomicAdd(&b.hdr->ticket, 1ULL);
+            sm.ticket = tk;
+            if (tk < total) {
+                const double hs = b.sys[b.order[item_rank(b, tk)]].h;
+                set_softening(sa, hs > 0.0 ? hs : a.h);
+            }
+        }
         __syncthreads();
         const int64_t ticket = sm.ticket;
         __syncthreads();
@@ -2119,7 +2157,7 @@ eval_mixed_batched_kernel(const EvalArgs a, const BatchView b)
         it.rows = 0;
         it.tile0 = b.tile_off[s];
         it.pad = 0;
-        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, MODE>(a, sm, ring, it)) break;
+        if (!mixed_item<NT, KT, S, U, POT, SACC, PAIR, MODE>(sa, sm, ring, it)) break;
         __syncthreads();
     }
     drain_mixed_ring(sm, ring, a.flags);
@@ -2333,11 +2371,20 @@ __global__ void __launch_bounds__(NT, 2)
 eval_f64_batched_kernel(const EvalArgs a, const BatchView b)
 {
     __shared__ __align__(128) F64Smem<S> sm;
+    __shared__ EvalArgs sa;   // the launch's arguments with the item's system's softening
+    if (threadIdx.x == 0) sa = a;
     init_ring(sm);
     Ring ring{0u, 0u};
     const int64_t total = b.hdr->total_items;
     for (;;) {
-        if (threadIdx.x == 0) sm.ticket = (long long)atomicAdd(&b.hdr->ticket, 1ULL);
+        if (threadIdx.x == 0) {
+            const long long tk = (long long)atomicAdd(&b.hdr->ticket, 1ULL);
+            sm.ticket = tk;
+            if (tk < total) {
+                const double hs = b.sys[b.order[item_rank(b, tk)]].h;
+                set_softening(sa, hs > 0.0 ? hs : a.h);
+            }
+        }
         __syncthreads();
         const int64_t ticket = sm.ticket;
         __syncthreads();
@@ -2357,7 +2404,7 @@ eval_f64_batched_kernel(const EvalArgs a, const BatchView b)
         it.rows = 0;
         it.tile0 = b.tile_off[s];
         it.pad = 0;
-        if (!f64_item<NT, S, POT, MODE>(a, sm, ring, it)) break;
+        if (!f64_item<NT, S, POT, MODE>(sa, sm, ring, it)) break;
         __syncthreads();
     }
     drain_ring<2>(sm.bar, ring, a.flags);

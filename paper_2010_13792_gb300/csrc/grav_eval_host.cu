@@ -453,7 +453,8 @@ __device__ void cta_exclusive_scan(const TIn *vals, TOut *out, int n)
 // resets the ticket counter.
 __global__ void __launch_bounds__(kPlanThreads)
 batch_plan_kernel(BatchView b, const int32_t *__restrict__ idx, const int32_t *n_idx_dev,
-                  int64_t n_idx_max, int64_t n_total, int32_t S, int32_t BT, int32_t *flags)
+                  int64_t n_idx_max, int64_t n_total, int32_t S, int32_t BT, double box,
+                  int32_t *flags)
 {
     const int n = b.n_sys;
     int64_t count = n_idx_max;
@@ -463,11 +464,14 @@ batch_plan_kernel(BatchView b, const int32_t *__restrict__ idx, const int32_t *n
     }
     for (int s = threadIdx.x; s < n; s += kPlanThreads) {
         const int64_t off = b.sys[s].offset, len = b.sys[s].n;
+        const double h = b.sys[s].h;   // 0: the call's h
         bool ok = off >= 0 && len >= 0 && off + len <= n_total;
         if (ok && s > 0) ok = off >= b.sys[s - 1].offset + b.sys[s - 1].n;
+        if (ok && h != 0.0) ok = h > 0.0 && isfinite(h) && (box == 0.0 || 2.0 * h < box);
         if (!ok) flag_or(flags, GRAV_FLAG_BADINDEX);
-        const int64_t lo = ok ? lower_bound_i32(idx, count, off) : 0;
-        const int64_t hi = ok ? lower_bound_i32(idx, count, off + len) : 0;
+        // (no target list: every element is a target, slots are elements)
+        const int64_t lo = !ok ? 0 : idx ? lower_bound_i32(idx, count, off) : off;
+        const int64_t hi = !ok ? 0 : idx ? lower_bound_i32(idx, count, off + len) : off + len;
         b.idx_lo[s] = (int32_t)lo;
         b.idx_hi[s] = (int32_t)hi;
         b.ntb[s] = ok ? (int32_t)((hi - lo + BT - 1) / BT) : 0;
@@ -558,6 +562,16 @@ int batch_grid_for(const EvalConfig *c, int index, bool periodic, bool pot, int 
 }
 
 }  // namespace
+
+int launch_batch_plan(const BatchView &b, const int32_t *idx, const int32_t *n_idx_dev,
+                      int64_t n_idx_max, int64_t n_total, int32_t S, int32_t BT, double box,
+                      int32_t *flags, cudaStream_t st)
+{
+    batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(b, idx, n_idx_dev, n_idx_max, n_total, S, BT, box,
+                                                   flags);
+    return check_launch("batch plan");
+}
+
 }  // namespace grav
 
 extern "C" int64_t grav_batched_workspace_bytes(const grav_params *p, int32_t n_sys, int64_t n_total)
@@ -652,9 +666,7 @@ extern "C" int grav_eval_batched(const grav_params *p, int32_t n_sys, const grav
 
     cudaStream_t st = as_stream(stream);
     const int32_t BT = c->threads * c->kt;
-    batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(b, idx, n_idx_dev, n_idx_max, n_total, c->s, BT,
-                                                   flags_dev);
-    rc = check_launch("grav_eval_batched/plan");
+    rc = launch_batch_plan(b, idx, n_idx_dev, n_idx_max, n_total, c->s, BT, p->box, flags_dev, st);
     if (rc) return rc;
     c->pack_batched(b, pos, vel, mass, const_cast<TileGeom *>(a.geo), const_cast<void *>(a.src),
                     flags_dev, const_cast<float *>(a.src_lo), (int)L.max_tiles, st);

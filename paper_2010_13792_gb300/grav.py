@@ -122,6 +122,11 @@ _SIGS = {
     "grav_eval_backward": (ctypes.c_int, [ctypes.POINTER(Params), _c_i64, _c_ptr, _c_ptr, _c_ptr,
                                           _c_dbl, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                           _c_ptr, _c_i64, _c_ptr]),
+    "grav_backward_batched_workspace_bytes": (_c_i64, [ctypes.POINTER(Params), _c_i32, _c_i64]),
+    "grav_eval_backward_batched": (ctypes.c_int, [ctypes.POINTER(Params), _c_i32, _c_ptr, _c_i64,
+                                                  _c_ptr, _c_ptr, _c_ptr, _c_dbl, _c_ptr, _c_ptr,
+                                                  _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64,
+                                                  _c_ptr]),
     "grav_soft_workspace_bytes": (_c_i64, [_c_i64]),
     "grav_soft_solve": (ctypes.c_int, [ctypes.POINTER(SoftParams), _c_i64, _c_ptr, _c_ptr, _c_ptr,
                                        _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr]),
@@ -470,20 +475,40 @@ def batched_workspace_bytes(p: Params, n_sys: int, n_total: int) -> int:
     return r
 
 
+def systems_table(systems, h=None, device=None):
+    """The device array of grav_system {offset, n, h} for eval_batched, as an
+    int64 tensor [n_sys, 3] whose last column holds each h's FP64 bits.
+
+    systems: [n_sys, 2] (offset, n); h: None (every system takes the call's
+    grav_params h), one value, or one per system (0: the call's h).  A
+    tensor already in this form is returned unchanged."""
+    if torch.is_tensor(systems) and systems.dim() == 2 and systems.shape[1] == 3:
+        return systems
+    if device is None:
+        device = systems.device if torch.is_tensor(systems) else torch.device("cuda")
+    on = torch.as_tensor(systems, dtype=torch.int64).reshape(-1, 2).cpu()
+    hs = torch.zeros(on.shape[0], dtype=torch.float64)
+    if h is not None:
+        hs[:] = torch.as_tensor(h, dtype=torch.float64).cpu()
+    tab = torch.cat([on, hs.view(torch.int64)[:, None]], dim=1).contiguous()
+    return tab.to(device)
+
+
 def eval_batched(p: Params, systems, pos, vel, mass, idx, n_idx_dev, n_idx_max: int, acc, jerk,
                  tidal, pot=None, dt_grav=None, flags=None, workspace: Workspace | None = None,
                  stream=None):
     """Force evaluation over independent systems in one launch.
 
-    systems: int64 CUDA tensor [n_sys, 2] of (offset, n); idx: ascending
-    global target indices (int32), count *n_idx_dev or n_idx_max."""
+    systems: the int64 CUDA tensor [n_sys, 3] of systems_table (offset, n and
+    the bits of each system's h); idx: ascending global target indices
+    (int32), count *n_idx_dev or n_idx_max."""
     n = mass.numel()
     n_sys = systems.shape[0] if systems.dim() == 2 else 0
     dev = mass.device
     nb = batched_workspace_bytes(p, n_sys, n)
     buf = _ws(workspace, "batched", dev).get(nb, dev)
     rc = lib().grav_eval_batched(
-        ctypes.byref(p), n_sys, _ptr(systems, torch.int64, "systems", (n_sys, 2)), n,
+        ctypes.byref(p), n_sys, _ptr(systems, torch.int64, "systems", (n_sys, 3)), n,
         _ptr(pos, torch.float64, "pos", (n, 3)), _ptr(vel, torch.float64, "vel", (n, 3)),
         _ptr(mass, torch.float64, "mass", (n,)), _ptr(idx, torch.int32, "idx"),
         _ptr(n_idx_dev, torch.int32, "n_idx_dev", (1,), allow_none=True), int(n_idx_max),
@@ -521,6 +546,37 @@ def eval_backward(p: Params, pos, mass, a_bar, w_bar: float, acc, tidal, pot, po
         _ptr(flags, torch.int32, "flags", (1,), allow_none=True),
         ctypes.c_void_p(buf.data_ptr()), nb, _stream(stream))
     _err("grav_eval_backward", rc)
+
+
+def backward_batched_workspace_bytes(p: Params, n_sys: int, n_total: int) -> int:
+    r = lib().grav_backward_batched_workspace_bytes(ctypes.byref(p), int(n_sys), int(n_total))
+    if r < 0:
+        _err("grav_backward_batched_workspace_bytes", r)
+    return r
+
+
+def eval_backward_batched(p: Params, systems, pos, mass, a_bar, w_bar: float, acc, tidal, pot,
+                          pos_bar, mass_bar, flags=None, workspace: Workspace | None = None,
+                          stream=None):
+    """The adjoint over independent systems in one launch; systems: the
+    int64 CUDA tensor [n_sys, 3] of systems_table."""
+    n = mass.numel()
+    n_sys = systems.shape[0] if systems.dim() == 2 else 0
+    dev = mass.device
+    nb = backward_batched_workspace_bytes(p, n_sys, n)
+    buf = _ws(workspace, "backward_batched", dev).get(nb, dev)
+    rc = lib().grav_eval_backward_batched(
+        ctypes.byref(p), n_sys, _ptr(systems, torch.int64, "systems", (n_sys, 3)), n,
+        _ptr(pos, torch.float64, "pos", (n, 3)), _ptr(mass, torch.float64, "mass", (n,)),
+        _ptr(a_bar, torch.float64, "a_bar", (n, 3), allow_none=True), float(w_bar),
+        _ptr(acc, torch.float64, "acc", (n, 3), allow_none=True),
+        _ptr(tidal, torch.float64, "tidal", (n, 6), allow_none=True),
+        _ptr(pot, torch.float64, "pot", (n,), allow_none=True),
+        _ptr(pos_bar, torch.float64, "pos_bar", (n, 3)),
+        _ptr(mass_bar, torch.float64, "mass_bar", (n,)),
+        _ptr(flags, torch.int32, "flags", (1,), allow_none=True),
+        ctypes.c_void_p(buf.data_ptr()), nb, _stream(stream))
+    _err("grav_eval_backward_batched", rc)
 
 
 def measure_fma_peak(precision: int, seconds: float = 0.5, stream=None) -> float:

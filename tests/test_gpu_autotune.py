@@ -44,7 +44,8 @@ def _run(p, P, V, M, idx, systems=None):
     if systems is None:
         grav.eval_active(p, P, V, M, I, None, idx.size, *outs)
     else:
-        grav.eval_batched(p, T(systems, torch.int64), P, V, M, I, None, idx.size, *outs)
+        grav.eval_batched(p, grav.systems_table(systems, device=DEV), P, V, M, I, None, idx.size,
+                          *outs)
     torch.cuda.synchronize()
     return {k: t.cpu().numpy() for k, t in zip(("acc", "jerk", "tidal"), outs)}
 
@@ -62,7 +63,7 @@ def test_tune_eval_valid_cached_and_consistent(kind, precision, tmp_path, monkey
         h = 1e-3
     P, V, M = T(pos), T(vel), T(mass)
     p = grav.params(h=h, precision=precision)
-    sys_t = T(systems, torch.int64) if systems is not None else None
+    sys_t = grav.systems_table(systems, device=DEV) if systems is not None else None
     best, ms = autotune.tune_eval(p, P, V, M, T(idx, torch.int32), idx.size, systems=sys_t, reps=2)
     count = grav.lib().grav_tile_config_count(precision)
     assert 0 <= best < count

@@ -31,12 +31,13 @@ def _outputs(n):
 
 
 def run_batched(pos, vel, mass, systems, idx, h, precision, device_count=True, tile_config=-1,
-                flags=None):
+                flags=None, h_sys=None):
     n = mass.size
     acc, jerk, tid, pot, dtg = _outputs(n)
     p = grav.params(h=h, precision=precision, want_pot=True, tile_config=tile_config)
     cnt = T(np.array([idx.size]), torch.int32) if device_count else None
-    grav.eval_batched(p, T(systems, torch.int64), T(pos), T(vel), T(mass), T(idx, torch.int32), cnt,
+    grav.eval_batched(p, grav.systems_table(systems, h_sys, device=DEV), T(pos), T(vel), T(mass),
+                      T(idx, torch.int32), cnt,
                       idx.size, acc, jerk, tid, pot, dtg, flags=flags)
     torch.cuda.synchronize()
     return {"acc": acc.cpu().numpy(), "jerk": jerk.cpu().numpy(), "tidal": tid.cpu().numpy(),
@@ -106,8 +107,8 @@ def test_batched_device_count_from_compaction_and_configs():
     for cfg in range(grav.lib().grav_tile_config_count(grav.MIXED)):
         acc, jerk, tid, pot, dtg = _outputs(n)
         p = grav.params(h=0.02, precision=grav.MIXED, want_pot=True, tile_config=cfg)
-        grav.eval_batched(p, T(systems, torch.int64), T(pos), T(vel), T(mass), it, cnt, n, acc, jerk,
-                          tid, pot, dtg)
+        grav.eval_batched(p, grav.systems_table(systems, device=DEV), T(pos), T(vel), T(mass), it,
+                          cnt, n, acc, jerk, tid, pot, dtg)
         torch.cuda.synchronize()
         a = acc.cpu().numpy()
         assert np.all(np.isfinite(a[idx]))
@@ -125,3 +126,50 @@ def test_batched_rejects_overlapping_system():
     good = run_batched(pos, vel, mass, systems, idx, 0.02, grav.F64)
     rows = act[0] + systems[0, 0]
     assert np.array_equal(out["acc"][rows], good["acc"][rows])
+
+
+@pytest.mark.parametrize("precision", [grav.F64, grav.MIXED])
+def test_batched_per_system_softening(precision):
+    """Plummer systems at h = 1e-3 next to uniform spheres at h = 0.01 in one
+    launch (each system's own h from grav_system.h, the call's h = 0.05
+    unused but by the systems that give h = 0): bit for bit the per-system
+    grav_eval_active with that h, and the oracle on every system's targets."""
+    pos, vel, mass, systems, idx, act = _packed(20, 300, 6000, seed=95)
+    h_sys = np.where(np.arange(20) % 2 == 0, 1e-3, 0.01)
+    h_sys[5] = 0.0                       # this one takes the call's h
+    h_call = 0.05
+    out = run_batched(pos, vel, mass, systems, idx, h_call, precision, h_sys=h_sys)
+    P, V, M = T(pos), T(vel), T(mass)
+    errs = {k: [] for k in ("acc", "jerk", "tidal", "pot")}
+    for s, (off, ns) in enumerate(systems):
+        hs = h_sys[s] if h_sys[s] > 0 else h_call
+        sl = slice(off, off + ns)
+        acc, jerk, tid, pot, dtg = _outputs(int(ns))
+        p = grav.params(h=hs, precision=precision, want_pot=True, max_split=1)
+        grav.eval_active(p, P[sl].contiguous(), V[sl].contiguous(), M[sl].contiguous(),
+                         T(act[s], torch.int32), None, act[s].size, acc, jerk, tid, pot, dtg)
+        torch.cuda.synchronize()
+        rows = act[s] + off
+        for k, t in (("acc", acc), ("jerk", jerk), ("tidal", tid), ("pot", pot), ("dt_grav", dtg)):
+            assert np.array_equal(out[k][rows], t.cpu().numpy()[act[s]]), (s, k)
+        ref = O.eval_active(pos[sl], vel[sl], mass[sl], act[s].astype(np.int32), h=hs)
+        e = errors(out, ref, rows)
+        for k in errs:
+            errs[k].append(e[k])
+    agg = {k: (float(np.median([m for m, _ in v])), max(x for _, x in v)) for k, v in errs.items()}
+    (assert_f64 if precision == grav.F64 else assert_mixed)(agg)
+
+
+@pytest.mark.parametrize("bad_h", [-1e-3, float("nan"), float("inf")])
+def test_batched_rejects_bad_system_softening(bad_h):
+    pos, vel, mass, systems, idx, act = _packed(6, 200, 400, seed=96)
+    h_sys = np.zeros(6)
+    h_sys[2] = bad_h
+    flags = torch.zeros(1, dtype=torch.int32, device=DEV)
+    out = run_batched(pos, vel, mass, systems, idx, 0.02, grav.F64, flags=flags, h_sys=h_sys)
+    assert int(flags.item()) & grav.FLAG_BADINDEX
+    assert np.all(np.isnan(out["acc"][act[2] + systems[2, 0]]))
+    good = run_batched(pos, vel, mass, systems, idx, 0.02, grav.F64)
+    for s in (0, 1, 3, 4, 5):
+        rows = act[s] + systems[s, 0]
+        assert np.array_equal(out["acc"][rows], good["acc"][rows])

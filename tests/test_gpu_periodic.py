@@ -100,7 +100,7 @@ def test_batched_periodic_and_open_limit():
     acc = torch.zeros(n, 3, dtype=torch.float64, device=DEV)
     jerk, tid = torch.zeros_like(acc), torch.zeros(n, 6, dtype=torch.float64, device=DEV)
     p = grav.params(h=0.02, precision=grav.F64, box=1.0)
-    grav.eval_batched(p, T(systems, torch.int64), T(pos), T(vel), T(mass), T(idx, torch.int32), None,
+    grav.eval_batched(p, grav.systems_table(systems, device=DEV), T(pos), T(vel), T(mass), T(idx, torch.int32), None,
                       n, acc, jerk, tid)
     torch.cuda.synchronize()
     for off, ns in systems:
