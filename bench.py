@@ -330,8 +330,6 @@ def run_ours(args, rank, local, ws):
         # the other workloads and the oracle baseline at one GPU only (with
         # more ranks they would hold every GPU for minutes)
         result["extras"] = extras(args, path, dev, sms, peak32, flush)
-        result["extras"]["fp64_path"]["mixed_over_fp64"] = \
-            value / result["extras"]["fp64_path"]["interactions_per_s"]
         tree = result["extras"]["tree_N1048576"]
         if args.n == tree["n"] and args.fraction == 1.0:
             tree["speedup_over_mixed_direct"] = 1e3 * eval_s / tree["mixed"]["ms"]
@@ -375,15 +373,20 @@ def extras(args, path, dev, sms, peak32, flush):
         t = _time_eval(path, path.params, idx, cnt, idx_np.size, 3, flush)
         sweep[str(frac)] = {"interactions_per_s": idx_np.size * n / t, "eval_ms": 1e3 * t}
     out["mixed_fraction_sweep"] = sweep
-    # FP64 path on the 1% active set (all N sources)
-    idx_np = ics.active_subset(n, 0.01, ics.BASE_SEED + 5)
-    idx = torch.as_tensor(idx_np, device=dev)
-    cnt = torch.tensor([idx_np.size], dtype=torch.int32, device=dev)
+    # FP64 path on the 1% and 10% active sets (all N sources), and the mixed
+    # path's throughput over it at the same fraction
     p64 = grav.params(h=H, precision=grav.F64)
-    t64 = _time_eval(path, p64, idx, cnt, idx_np.size, 2, flush)
-    ips64 = idx_np.size * n / t64
-    out["fp64_path"] = {"interactions_per_s": ips64, "active_fraction": 0.01, "eval_ms": 1e3 * t64,
-                        "mixed_over_fp64": None}
+    f64 = {}
+    for frac in (0.01, 0.1):
+        idx_np = ics.active_subset(n, frac, ics.BASE_SEED + 5)
+        idx = torch.as_tensor(idx_np, device=dev)
+        cnt = torch.tensor([idx_np.size], dtype=torch.int32, device=dev)
+        t64 = _time_eval(path, p64, idx, cnt, idx_np.size, 2, flush)
+        ips = idx_np.size * n / t64
+        f64[str(frac)] = {"interactions_per_s": ips, "eval_ms": 1e3 * t64,
+                          "mixed_over_fp64": sweep[str(frac)]["interactions_per_s"] / ips}
+    ips64 = f64["0.1"]["interactions_per_s"]
+    out["fp64_path"] = f64
     # predictor (HBM-bound): all elements active, none due
     ones = torch.ones(n, dtype=torch.uint8, device=dev)
     zeros = torch.zeros(n, dtype=torch.uint8, device=dev)
@@ -409,12 +412,13 @@ def extras(args, path, dev, sms, peak32, flush):
     out["adaptive_plummer_131072"] = adaptive_extra(dev)
     try:
         f32 = grav.measure_fma_peak(grav.MIXED, 0.5)
-        f64 = grav.measure_fma_peak(grav.F64, 0.5)
+        f64p = grav.measure_fma_peak(grav.F64, 0.5)
         f32x2 = grav.measure_fma_peak(grav.PEAK_F32X2, 0.5)
         out["measured_fma_peak_tflops"] = {"fp32": f32 / 1e12, "fp32x2": f32x2 / 1e12,
-                                           "fp64": f64 / 1e12}
-        # the FP64 path against the measured FP64 FMA peak, same 56-flop tally
-        out["fp64_path"]["frac_of_measured_fp64_peak"] = FLOPS_PER_INTERACTION * ips64 / f64
+                                           "fp64": f64p / 1e12}
+        # the FP64 path (10% active) against the measured FP64 FMA peak, same
+        # 56-flop tally
+        out["fp64_path"]["frac_of_measured_fp64_peak_at_0.1"] = FLOPS_PER_INTERACTION * ips64 / f64p
     except grav.GravError as e:
         out["measured_fma_peak_tflops"] = {"error": str(e)}
     return out
@@ -735,34 +739,50 @@ def batched_extra(dev, flush):
 
 
 def adaptive_extra(dev):
-    """Plummer N = 2^17, h = 1e-3, k_max = 6: one 64-substep cycle of the
-    adaptive loop (q_f = 1/2, jerk predictor) against update-every-substep
-    (q_f = 0), both captured as CUDA graphs, mixed precision."""
+    """The adaptive update loop on a Plummer sphere of 2^17 (h = 1e-3,
+    k_max = 6, dt_max = 2^-4): one cycle of 64 substeps captured as a CUDA
+    graph.  q_f runs over {1/8, 1/4, 1/2, 1}, the paper's range, against
+    updating every active element at every substep (q_f = 0).  Both precisions
+    are run.  Per run: the cycle time, the work ratio (force evaluations over
+    those of q_f = 0), the relative energy change over the cycle and the
+    speedup over q_f = 0 of the same precision.  For q_f > 0 also: the jerk
+    predictor's error quantiles at the cycle's end, and the median distance
+    from the q_f = 0 positions."""
     import torch
 
     from paper_2010_13792_gb300 import grav, ics
     from paper_2010_13792_gb300.adaptive import AdaptiveIntegrator
     pos, vel, mass = ics.plummer(1 << 17, seed=ics.BASE_SEED + 1)
-    res = {}
-    runs = {}
-    for name, q_f in (("standard_qf0", 0.0), ("adaptive_qf0.5", 0.5)):
-        it = AdaptiveIntegrator(pos, vel, mass, h=1e-3, q_f=q_f, k_max=6, dt_max=2.0**-4,
-                                precision=grav.MIXED)
-        e0 = sum(it.energy())
-        it.start()
-        it.capture_cycle()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        it.replay(1)
-        b.record()
-        torch.cuda.synchronize()
-        e1 = sum(it.energy())
-        runs[name] = it
-        res[name] = {"ms_per_64_substeps": a.elapsed_time(b), "work_ratio": it.work_ratio(),
-                     "rel_energy_change": abs(e1 - e0) / abs(e0)}
-    s, ad = runs["standard_qf0"], runs["adaptive_qf0.5"]
-    res["speedup"] = res["standard_qf0"]["ms_per_64_substeps"] / res["adaptive_qf0.5"]["ms_per_64_substeps"]
-    res["median_position_difference"] = float((ad.pos - s.pos).norm(dim=1).median().item())
+    res = {"n": 1 << 17, "h": 1e-3, "k_max": 6, "dt_max": 2.0**-4, "substeps": 64}
+    for pname, prec in (("mixed", grav.MIXED), ("f64", grav.F64)):
+        runs, out = {}, {}
+        for q_f in (0.0, 0.125, 0.25, 0.5, 1.0):
+            it = AdaptiveIntegrator(pos, vel, mass, h=1e-3, q_f=q_f, k_max=6, dt_max=2.0**-4,
+                                    precision=prec)
+            e0 = sum(it.energy())
+            it.start()
+            it.capture_cycle()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            it.replay(1)
+            b.record()
+            torch.cuda.synchronize()
+            e1 = sum(it.energy())
+            rec = {"ms_per_64_substeps": a.elapsed_time(b), "work_ratio": it.work_ratio(),
+                   "rel_energy_change": abs(e1 - e0) / abs(e0)}
+            if q_f > 0:
+                rec["predicted_a_rel_error"] = it.predictor_error()["jerk"]
+            runs[q_f] = it
+            out[f"qf{q_f:g}"] = rec
+        std = out["qf0"]
+        for q_f, it in runs.items():
+            if q_f > 0:
+                r = out[f"qf{q_f:g}"]
+                r["speedup_over_qf0"] = std["ms_per_64_substeps"] / r["ms_per_64_substeps"]
+                r["median_position_difference"] = float((it.pos - runs[0.0].pos).norm(dim=1).median().item())
+        res[pname] = out
+    res["mixed_over_f64_qf0.5"] = (res["f64"]["qf0.5"]["ms_per_64_substeps"] /
+                                   res["mixed"]["qf0.5"]["ms_per_64_substeps"])
     # the paper's predictor ablation (q_f = 1/2): none, linear polynomial, jerk
     abl = {}
     for mode in ("none", "poly", "jerk"):
