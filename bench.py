@@ -48,7 +48,11 @@ L2_FLUSH_BYTES = 256 << 20
 # library picks for this workload (17) on the turbulent cloud with N = 2^18,
 # all active.  The traffic is the sources and targets streamed once, so it
 # scales with N.
-TRAFFIC_CAPTURE = {"tile_config": 17, "n": 262144, "bytes": 21778176 + 14417152}
+TRAFFIC_CAPTURE = {"tile_config": 17, "n": 262144, "bytes": 26454272 + 50545664}
+# DRAM bytes (read + write) of one predictor launch on 2^24 elements, all
+# active, none due, from an ncu capture of the same launch (82 B per element
+# algorithmic; some of the writes were still in L2 when the launch ended).
+PREDICT_TRAFFIC_CAPTURE = {"n": 16777216, "bytes": 973454080 + 381213696}
 
 
 def parse():
@@ -319,7 +323,7 @@ def run_ours(args, rank, local, ws):
         "achieved": achieved, "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32,
         "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
         "flops_per_interaction": FLOPS_PER_INTERACTION, "traffic": traffic,
-        "traffic_basis": "ncu dram bytes of the same kernel at N=2^18, scaled by N (see profiles/)",
+        "traffic_basis": "ncu dram bytes of the same kernel at N=2^18, scaled by N",
         "eval_ms_mean": 1e3 * eval_s,
     }
 
@@ -330,6 +334,15 @@ def run_ours(args, rank, local, ws):
         # the other workloads and the oracle baseline at one GPU only (with
         # more ranks they would hold every GPU for minutes)
         result["extras"] = extras(args, path, dev, sms, peak32, flush)
+        # the predictor (HBM-bound) against the measured copy bandwidth
+        pb = result["extras"]["predict_N16777216"]
+        hbm = measured_hbm_peak()
+        if hbm:
+            result["predictor_roofline"] = {
+                "bound": "hbm", "kernel": "predict_pair_kernel (grav_predict), 2^24 elements",
+                "achieved": pb["GB_per_s"], "peak": hbm, "unit": "GB/s", "frac": pb["GB_per_s"] / hbm,
+                "peak_basis": "measured copy bandwidth (burst)", "bytes_per_element": 82,
+                "traffic": PREDICT_TRAFFIC_CAPTURE["bytes"] * pb["n"] / PREDICT_TRAFFIC_CAPTURE["n"]}
         tree = result["extras"]["tree_N1048576"]
         if args.n == tree["n"] and args.fraction == 1.0:
             tree["speedup_over_mixed_direct"] = 1e3 * eval_s / tree["mixed"]["ms"]
