@@ -601,7 +601,6 @@ __device__ __forceinline__ bool bwd_pair_item(const BwdArgs &a, BwdPairSmem<S> &
     }
     // lo/hi become the warp's box; tiles are tested against it
     block_bbox<NT>(lo, hi, sm.blo, sm.bhi);
-    const float diag2_w = box_diag2(lo, hi);
     // pairs within 2h, listed per target for FP64
     int32_t nlist[KT][kBwdCloseList];
     int ncnt[KT];
@@ -638,7 +637,7 @@ __device__ __forceinline__ bool bwd_pair_item(const BwdArgs &a, BwdPairSmem<S> &
         // loop with two-part separations
         const float g2 = box_gap2(lo, hi, g);
         constexpr float kL = kLooseC / (1.0f - kLooseC);
-        const bool close = !(g2 >= h2) || g2 < (2.0f * kL * kL) * (diag2_w + box_diag2(g.lo, g.hi));
+        const bool close = !(g2 >= h2) || g2 < (kL * kL) * box_diag2(g.lo, g.hi);
         float tx[KT][3];
 #pragma unroll
         for (int q = 0; q < KT; ++q)

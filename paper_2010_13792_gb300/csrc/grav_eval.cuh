@@ -584,12 +584,15 @@ __device__ __forceinline__ double nearest_image_d(double xj, double xi, double b
 
 // Tiles whose FP32 position offsets (from the tile centre, rounded to half
 // an ulp) could make a separation wrong by more than about 8e-6 of itself:
-// a target within C (|t| + |e|) of the tile's box, t its offset from the
-// tile centre and e the box's half-diagonal, C = 2^-24 / 8e-6 ~ 1/128 --
-// over a warp, a box gap below C / (1 - C) (diagonal of the warp's box +
-// diagonal of the tile's).  Compact tiles meet it only next to the targets; a tile
-// that spans a jump of the element order (a core and a distant outskirt in
-// one Morton range) meets it wherever its members are.
+// the rounding is at most 2^-24 (|t| + |e|), t the target's offset from the
+// tile centre and e the box's half-diagonal, and |t| <= gap + e for a target
+// at distance gap from the box, so a separation (>= gap) can lose that much
+// only when gap < C (gap + 2e), C = 2^-24 / 8e-6 ~ 1/128, i.e. gap <
+// C / (1 - C) times the box's diagonal.  Over a warp the gap between the
+// warp's box and the tile's is a lower bound of every target's.  Compact
+// tiles meet it only next to the targets; a tile that spans a jump of the
+// element order (a core and a distant outskirt in one Morton range) meets it
+// wherever its members are.
 constexpr float kLooseC = 1.0f / 128.0f;
 
 // Per target and tile of the periodic box: bit 0 when the tile needs the
@@ -662,15 +665,13 @@ __device__ __forceinline__ float box_diag2(const float lo[3], const float hi[3])
 // close: the tile is summed by the close loops -- in a periodic box when it
 // comes within a target's close radius or the FP32 offsets' reach
 // (periodic_class), with open boundaries when it lies inside h of the warp's
-// box or within the offsets' reach over it, gap < C/(1-C) (diag_w + diag_t),
-// squared with (a+b)^2 <= 2 (a^2 + b^2) (diag2_w: the warp box's squared
-// diagonal).
+// box or within the offsets' reach, gap < C/(1-C) diag_t (kLooseC).
 template <int KT, int MODE>
 __device__ __forceinline__ void classify_tile(const EvalArgs &a, const TileGeom &g,
                                               const float tx[KT][3], const int64_t ti[KT],
                                               const float blo[3], const float bhi[3],
-                                              float diag2_w, const float rc2[KT], float h2_tile,
-                                              bool &near, bool &close)
+                                              const float rc2[KT], float h2_tile, bool &near,
+                                              bool &close)
 {
     close = false;
     if (MODE == kModePeriodic) {
@@ -683,7 +684,7 @@ __device__ __forceinline__ void classify_tile(const EvalArgs &a, const TileGeom 
         const float g2 = box_gap2(blo, bhi, g);
         near = !(g2 >= a.h2f_up);
         constexpr float kL = kLooseC / (1.0f - kLooseC);
-        close = near || g2 < (2.0f * kL * kL) * (diag2_w + box_diag2(g.lo, g.hi));
+        close = near || g2 < (kL * kL) * box_diag2(g.lo, g.hi);
     }
 }
 
@@ -866,8 +867,7 @@ __device__ __forceinline__ void periodic_loop_f(const float4 *__restrict__ stage
 // sum.  So every pair within 2h of its target (where a single pair can
 // dominate: inside the spline's support and just past it) is offered to
 // record(q, j) and, when taken, left out of the FP32 sums: it is summed in
-// FP64 after the item's tiles, its relative velocity formed from the FP64
-// velocities.
+// FP64 after the item's tiles, from the FP64 positions and velocities.
 template <int KT, int S, bool POT, bool PAIR, typename Record>
 __device__ __forceinline__ void near_loop_rec(const float4 *__restrict__ stage,
                                               const float *__restrict__ lo, const float tx[KT][3],
@@ -1760,8 +1760,6 @@ __device__ __forceinline__ bool mixed_item(
     // block's box when the targets are sparse
     const float blo_r[3] = {lo[0], lo[1], lo[2]};
     const float bhi_r[3] = {hi[0], hi[1], hi[2]};
-    // the warp's squared box diagonal (open boundaries: the close-tile test)
-    const float diag2_w = (MODE == kModeOpen) ? box_diag2(blo_r, bhi_r) : 0.0f;
 
     // adaptive softening: the targets' 1/h_i and zeta_i, the warp's largest
     // support
@@ -1922,7 +1920,7 @@ __device__ __forceinline__ bool mixed_item(
             h2_tile = __fmul_ru(hm, hm);
         }
         bool near, close;
-        classify_tile<KT, MODE>(a, g, tx, ti, blo_r, bhi_r, diag2_w, rc2, h2_tile, near, close);
+        classify_tile<KT, MODE>(a, g, tx, ti, blo_r, bhi_r, rc2, h2_tile, near, close);
         // next tile's geometry and offsets, computed ahead (FP64 latency)
         TileGeom gn = g;
         if (t + 1 < t_end) {
@@ -1969,8 +1967,7 @@ __device__ __forceinline__ bool mixed_item(
             for (int q = 0; q < KT; ++q) {
                 double x[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    x[c] = SACC ? sm.x[c * BT + q * NT + threadIdx.x] : xr[SACC ? 0 : q][c];
+                for (int c = 0; c < 3; ++c) x[c] = tpos(q, c);
                 target_low_parts(a, g, x, tx[q], false, tl[q]);
             }
             near_loop_rec<KT, S, POT, PAIR>(sm.stage[s],
