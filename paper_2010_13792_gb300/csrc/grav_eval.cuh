@@ -1967,7 +1967,8 @@ __device__ __forceinline__ bool mixed_item(
             for (int q = 0; q < KT; ++q) {
                 double x[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) x[c] = tpos(q, c);
+                for (int c = 0; c < 3; ++c)
+                    x[c] = SACC ? sm.x[c * BT + q * NT + threadIdx.x] : xr[SACC ? 0 : q][c];
                 target_low_parts(a, g, x, tx[q], false, tl[q]);
             }
             near_loop_rec<KT, S, POT, PAIR>(sm.stage[s],
