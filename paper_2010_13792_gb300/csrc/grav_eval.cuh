@@ -878,7 +878,7 @@ __device__ __forceinline__ void near_loop_rec(const float4 *__restrict__ stage,
     const float hinv3 = hinv * hinv * hinv;
     const float hinv5 = hinv3 * hinv * hinv;
     const float *tile = reinterpret_cast<const float *>(stage);
-#pragma unroll 2
+#pragma unroll 4
     for (int j = 0; j < S; ++j) {
         float x, y, z, m, wx, wy, wz;
         if (PAIR) {
@@ -908,7 +908,9 @@ __device__ __forceinline__ void near_loop_rec(const float4 *__restrict__ stage,
             const float dy = (y - tx[q][1]) + (yl - tl[q][1]);
             const float dz = (z - tx[q][2]) + (zl - tl[q][2]);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 < 4.0f * h2 && m != 0.0f && ti[q] >= 0 && jg != ti[q] && record(q, jg)) continue;
+            // (inactive lanes, ti < 0, may record too: their lists are never
+            // evaluated; padding sources lie far away)
+            if (r2 < 4.0f * h2 && jg != ti[q] && record(q, jg)) continue;
             const float ri = rsqrt_sfu(r2);
             const float ri2 = ri * ri;
             float mp = m * ri;
