@@ -48,7 +48,7 @@ L2_FLUSH_BYTES = 256 << 20
 # library picks for this workload (17) on the turbulent cloud with N = 2^18,
 # all active.  The traffic is the sources and targets streamed once, so it
 # scales with N.
-TRAFFIC_CAPTURE = {"tile_config": 17, "n": 262144, "bytes": 27209728 + 51135488}
+TRAFFIC_CAPTURE = {"tile_config": 17, "n": 262144, "bytes": 26887424 + 50837504}
 # DRAM bytes (read + write) of one predictor launch on 2^24 elements, all
 # active, none due, from an ncu capture of the same launch (82 B per element
 # algorithmic; some of the writes were still in L2 when the launch ended).
