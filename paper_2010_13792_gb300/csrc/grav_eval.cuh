@@ -2026,7 +2026,8 @@ __device__ __forceinline__ bool mixed_item(
             for (int c = 0; c < 3; ++c) tx[q][c] = tx_next[q][c];
     }
 
-    // the listed pairs in FP64 (each lane its own list; only targets list)
+    // the listed pairs in FP64 (each lane its own list; an inactive lane's
+    // list is skipped)
     if constexpr (listed) {
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
