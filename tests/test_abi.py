@@ -170,3 +170,56 @@ def test_default_tile_config_choice(libgrav):
     ti = grav.TileInfo()
     assert L.grav_tile_config(grav.MIXED, -1, ctypes.byref(ti)) == grav.GRAV_OK
     assert ti.threads == small["threads"]
+
+
+def test_batched_argument_checks(libgrav):
+    """Host-side checks of the batched force evaluation and the batched
+    adjoint (no launch happens for any of these)."""
+    from paper_2010_13792_gb300 import grav
+    L = grav.lib()
+    p = grav.params(h=0.01)
+    fwd = lambda n_sys, n_total, nmax: L.grav_eval_batched(
+        ctypes.byref(p), n_sys, None, n_total, None, None, None, None, None, nmax, None, None,
+        None, None, None, None, None, 0, None)
+    assert fwd(-1, 10, 10) == grav.GRAV_EINVAL
+    assert fwd(16385, 10, 10) == grav.GRAV_EINVAL          # past GRAV_BATCH_MAX_SYSTEMS
+    assert fwd(2, 10, 11) == grav.GRAV_EINVAL              # n_idx_max > n_total
+    assert fwd(0, 10, 10) == grav.GRAV_OK                  # no systems: nothing to do
+    assert fwd(2, 10, 10) == grav.GRAV_EINVAL              # null arrays
+    bwd = lambda pp, n_sys, n_total, w: L.grav_eval_backward_batched(
+        ctypes.byref(pp), n_sys, None, n_total, None, None, None, w, None, None, None, None, None,
+        None, None, 0, None)
+    assert bwd(p, -1, 10, 0.0) == grav.GRAV_EINVAL
+    assert bwd(p, 16385, 10, 0.0) == grav.GRAV_EINVAL
+    assert bwd(p, 2, -1, 0.0) == grav.GRAV_EINVAL
+    assert bwd(p, 2, 10, float("nan")) == grav.GRAV_EINVAL
+    assert bwd(p, 0, 10, 0.0) == grav.GRAV_OK
+    assert bwd(p, 2, 10, 0.0) == grav.GRAV_EINVAL          # null arrays
+    assert bwd(grav.params(h=0.01, box=1.0), 2, 10, 0.0) == grav.GRAV_EINVAL   # open boundaries only
+    assert L.grav_backward_batched_workspace_bytes(ctypes.byref(p), -1, 10) == grav.GRAV_EINVAL
+    assert L.grav_backward_batched_workspace_bytes(ctypes.byref(p), 4, 1 << 20) > (1 << 20) * 16
+
+
+def test_systems_table_layout():
+    """grav.systems_table: int64 [n_sys, 3] of (offset, n, bits of h), the
+    layout of grav_system {int64 offset; int64 n; double h;}."""
+    import numpy as np
+    import torch
+
+    from paper_2010_13792_gb300 import grav
+
+    class GravSystem(ctypes.Structure):
+        _fields_ = [("offset", ctypes.c_int64), ("n", ctypes.c_int64), ("h", ctypes.c_double)]
+
+    assert ctypes.sizeof(GravSystem) == 24
+    t = grav.systems_table([[0, 10], [10, 5], [15, 7]], h=[1e-3, 0.0, 0.25], device="cpu")
+    assert t.dtype == torch.int64 and tuple(t.shape) == (3, 3)
+    raw = bytes(t.contiguous().numpy().tobytes())
+    recs = (GravSystem * 3).from_buffer_copy(raw)
+    assert [(r.offset, r.n, r.h) for r in recs] == [(0, 10, 1e-3), (10, 5, 0.0), (15, 7, 0.25)]
+    # no h: every system takes the call's h (0); one h: broadcast
+    assert torch.equal(grav.systems_table(np.array([[0, 4]]), device="cpu")[:, 2], torch.zeros(1, dtype=torch.int64))
+    t2 = grav.systems_table(torch.tensor([[0, 4], [4, 4]]), h=0.5, device="cpu")
+    assert t2[:, 2].clone().view(torch.float64).tolist() == [0.5, 0.5]
+    # a table already in this form passes through unchanged
+    assert grav.systems_table(t) is t
